@@ -1,0 +1,243 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test compares the oracle with something other than itself: the PDE of
+Eqs. (1)-(3) differentiated symbolically, closed-form solutions printed in the
+paper (Stoker dam break, Section 2.1; Thacker bowl, Section 2.2; Manning
+normal flow, Section 2.3), the Synolakis runup law of a solitary wave on a
+plane beach, and invariants of the scheme (lake at rest, conservation of h,
+mirror and transpose symmetry, zero mass flux through walls).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests import analytic as A
+
+
+# ------------------------------------------------------------ spatial operator
+def _smooth_fields():
+    sp = pytest.importorskip("sympy")
+    x, y = sp.symbols("x y")
+    tp = 2 * sp.pi
+    h = 2 + sp.Rational(1, 5) * sp.sin(tp * x) * sp.cos(tp * y) + sp.Rational(1, 10) * sp.cos(tp * (x + 2 * y))
+    hu = sp.Rational(3, 10) * sp.cos(tp * x) * sp.sin(tp * y) + sp.Rational(1, 5)
+    hv = sp.Rational(1, 4) * sp.sin(tp * (x - y)) - sp.Rational(1, 10)
+    b = sp.Rational(3, 10) * sp.cos(tp * x) * sp.cos(tp * y) - 1
+    return sp, x, y, (h, hu, hv, b)
+
+
+def _pde_rhs(nm, g=9.81):
+    """Right-hand side -dF/dx - dG/dy + S of Eqs. (1)-(3) (y-source with db/dy)."""
+    sp, x, y, (h, hu, hv, b) = _smooth_fields()
+    F = [hu, hu ** 2 / h + g * (h ** 2 - b ** 2) / 2, hu * hv / h]
+    Gf = [hv, hu * hv / h, hv ** 2 / h + g * (h ** 2 - b ** 2) / 2]
+    q = sp.sqrt(hu ** 2 + hv ** 2)
+    fr = g * nm ** 2 * q / h ** sp.Rational(7, 3)
+    S = [0, -g * (h + b) * sp.diff(b, x) - fr * hu, -g * (h + b) * sp.diff(b, y) - fr * hv]
+    rhs = [sp.lambdify((x, y), -sp.diff(F[m], x) - sp.diff(Gf[m], y) + S[m], "numpy") for m in range(3)]
+    fields = [sp.lambdify((x, y), e, "numpy") for e in (h, hu, hv, b)]
+    return rhs, fields
+
+
+def _operator_error(N, nm=0.0):
+    rhs, fields = _pde_rhs(nm)
+    d = 1.0 / N
+    c = (np.arange(N) + 0.5) * d
+    X, Y = np.meshgrid(c, c)
+    H, HU, HV, B = (f(X, Y) * np.ones_like(X) for f in fields)
+    sc = W.Scenario("smooth", d, d, B, H, HU, HV, bc=(W.PERIODIC,) * 4, manning_n=nm)
+    L = oracle.operator(sc)[:3]
+    return max(float(np.abs(L[m] - rhs[m](X, Y)).max()) for m in range(3))
+
+
+def test_operator_converges_at_fifth_order_to_the_pde():
+    e = [_operator_error(N) for N in (128, 256, 512)]
+    assert e[0] > e[1] > e[2]
+    order = math.log2(e[1] / e[2])
+    assert order >= 4.5, (e, order)
+    assert e[2] < 1e-5
+
+
+def test_friction_term_is_explicit_manning_with_cap():
+    sc = W.planar_beach(nx=64, ny=4, manning_n=0.0)
+    rng = np.random.default_rng(7)
+    sc.h = 1.0 + rng.uniform(0, 1, sc.h.shape)
+    sc.b = np.full_like(sc.b, -5.0)
+    sc.hu = rng.normal(size=sc.h.shape)
+    sc.hv = rng.normal(size=sc.h.shape)
+    L0 = oracle.operator(sc)
+    n = 0.05
+    L1 = oracle.operator(sc.copy(manning_n=n))
+    kappa = 9.81 * n * n * np.sqrt(sc.hu ** 2 + sc.hv ** 2) / sc.h ** (7.0 / 3.0)
+    assert np.allclose(L1[1] - L0[1], -kappa * sc.hu, rtol=1e-12, atol=1e-14)
+    assert np.allclose(L1[2] - L0[2], -kappa * sc.hv, rtol=1e-12, atol=1e-14)
+    assert np.array_equal(L1[0], L0[0])
+    dt = 0.5 / kappa.max()  # the largest rates are capped at 1/dt
+    L2 = oracle.operator(sc.copy(manning_n=n), dt=dt)
+    kc = np.minimum(kappa, 1.0 / dt)
+    assert np.allclose(L2[1] - L0[1], -kc * sc.hu, rtol=1e-12, atol=1e-14)
+
+
+def test_walls_pass_no_mass():
+    rng = np.random.default_rng(3)
+    sc = W.gaussian_hump(n=24)
+    sc.hu = rng.normal(scale=0.1, size=sc.h.shape)
+    sc.hv = rng.normal(scale=0.1, size=sc.h.shape)
+    *_, edge = oracle.operator(sc)
+    assert edge == 0.0
+
+
+# ------------------------------------------------------------- lake at rest
+def test_lake_at_rest_at_any_level_in_the_sea():
+    # still water 0.5 m above the datum z_ref = 0 over a rough bed: the
+    # weighted bed reconstruction must cancel the pressure flux to round-off
+    sc = W.lake_at_rest(32, 32, eta0=0.5, depth=10.0, rms=2.0)
+    sc.z_ref = 0.0
+    assert sc.h.min() > 1.0
+    L = oracle.operator(sc)
+    assert max(np.abs(L[m]).max() for m in range(3)) < 1e-12
+    sim = oracle.Simulation(sc)
+    sim.step(1000)
+    assert np.abs(sim.h + sc.b - 0.5).max() <= 1e-12
+    assert np.abs(sim.hu).max() <= 1e-11 and np.abs(sim.hv).max() <= 1e-11
+
+
+def test_lake_at_rest_with_dry_islands_is_exact():
+    sc = W.lake_at_rest(32, 32, eta0=0.5, depth=10.0, rms=2.0, islands=True)
+    assert (sc.h == 0).sum() > 4
+    sim = oracle.Simulation(sc)
+    sim.step(300)
+    wet = sc.h > 0
+    # exact up to round-off of the RK combinations (3/4 h + 1/4 h != h)
+    assert np.abs((sim.h + sc.b - 0.5)[wet]).max() <= 1e-12
+    assert sim.h[~wet].max() <= 1e-12
+    assert np.abs(sim.hu).max() <= 1e-11 and np.abs(sim.hv).max() <= 1e-11
+    assert sim.diag()["clamp_mass"] <= 1e-12 * sim.diag()["mass"]
+
+
+# ----------------------------------------------------------- conservation
+def test_mass_conserved_with_walls():
+    sc = W.gaussian_hump()
+    m0 = sc.h.sum() * sc.dx * sc.dy
+    sim = oracle.Simulation(sc)
+    sim.step(200)
+    assert abs(sim.diag()["mass"] - m0) / m0 <= 1e-13
+    assert sim.diag()["clamp_mass"] == 0.0
+
+
+def test_mass_budget_with_wet_dry_equals_clamp():
+    sc = W.parabolic_bowl()
+    m0 = sc.h.sum() * sc.dx * sc.dy
+    sim = oracle.Simulation(sc)
+    sim.step(600)
+    d = sim.diag()
+    assert d["clamp_mass"] > 0
+    assert abs(d["mass"] - m0 - d["clamp_mass"]) / m0 <= 1e-12
+
+
+def test_mass_budget_with_inflow_equals_edge_flux():
+    sc = W.coastal_dem(n=64, dx=200.0, t0=500.0)
+    m0 = sc.h.sum() * sc.dx * sc.dy
+    sim = oracle.Simulation(sc)
+    sim.step(60)
+    d = sim.diag()
+    assert abs(d["boundary_mass"]) > 1e-6 * m0
+    assert abs(d["mass"] - m0 - d["boundary_mass"] - d["clamp_mass"]) / m0 <= 1e-12
+
+
+# --------------------------------------------------------------- symmetry
+def test_hump_keeps_mirror_and_transpose_symmetry():
+    sc = W.gaussian_hump(n=64, sigma_cells=5.0)
+    sim = oracle.Simulation(sc)
+    sim.step(60)
+    h = sim.h
+    tol = 1e-14 * np.abs(h).max()
+    assert np.abs(h - h[:, ::-1]).max() <= tol
+    assert np.abs(h - h[::-1, :]).max() <= tol
+    assert np.abs(h - h.T).max() <= tol
+    assert np.abs(sim.hu + sim.hu[:, ::-1]).max() <= tol
+    assert np.abs(sim.hu - sim.hv.T).max() <= tol
+
+
+def test_x_and_y_sweeps_agree_under_transposition():
+    rng = np.random.default_rng(5)
+    sc = W.lake_at_rest(24, 40, eta0=0.0, depth=5.0, rms=1.0, seed=9)
+    sc.h = sc.h + 0.05 * rng.uniform(size=sc.h.shape)
+    sc.hu = 0.1 * rng.normal(size=sc.h.shape)
+    sc.hv = 0.1 * rng.normal(size=sc.h.shape)
+    sc.manning_n = 0.03
+    tr = sc.copy(b=sc.b.T.copy(), h=sc.h.T.copy(), hu=sc.hv.T.copy(), hv=sc.hu.T.copy())
+    a, b = oracle.Simulation(sc), oracle.Simulation(tr)
+    a.step(20)
+    b.step(20)
+    assert np.abs(a.h - b.h.T).max() <= 1e-13
+    assert np.abs(a.hu - b.hv.T).max() <= 1e-13
+
+
+# ------------------------------------------------------ closed-form solutions
+def test_stoker_dam_break():
+    errs = {}
+    for nx in (200, 400):
+        sc = W.dam_break(nx=nx)
+        sim = oracle.Simulation(sc)
+        x = (np.arange(nx) + 0.5) * sc.dx
+        for t in (2.5, 9.0):
+            sim.run_until(t)
+            ha, x3 = A.stoker(x, t, 50.0, 2.0, 1.0)
+            keep = np.abs(x - x3) > 5 * sc.dx  # away from the shock front
+            hc = sim.h[0]
+            errs[(nx, t)] = A.rel_l2(hc[keep], ha[keep])
+            hm = 0.5 * (A.stoker_cm(2.0, 1.0) ** 2 / 9.81 + 1.0)
+            x_num = x[np.where(hc > hm)[0].max()]
+            assert abs(x_num - x3) <= 2 * sc.dx
+            assert np.all(sim.h == sim.h[0])  # stays one-dimensional
+    for t in (2.5, 9.0):
+        assert errs[(400, t)] <= 2e-2
+        assert errs[(400, t)] < errs[(200, t)]
+
+
+def test_thacker_planar_bowl():
+    sc = W.parabolic_bowl()
+    sim = oracle.Simulation(sc)
+    x = (np.arange(sc.nx) + 0.5) * sc.dx
+    om = math.sqrt(2 * 9.81 * 1.0) / 100.0
+    for t in (3.5, 12.5, 2 * math.pi / om):
+        sim.run_until(t)
+        ha, ua = A.thacker(x, t, 400.0, 100.0, 1.0)
+        assert A.rel_l2(sim.h[0], ha) <= 1e-2
+        wet_num = x[sim.h[0] > 1e-3]
+        wet_ana = x[ha > 1e-3]
+        assert abs(wet_num.min() - wet_ana.min()) <= 2 * sc.dx
+        assert abs(wet_num.max() - wet_ana.max()) <= 2 * sc.dx
+
+
+@pytest.mark.parametrize("frac", [1.0, 0.8])
+def test_manning_normal_flow(frac):
+    qn = A.manning_normal_discharge(0.5, 1.0 / 20.0, 0.033)
+    sc = W.manning_slope(q=frac * qn)
+    sim = oracle.Simulation(sc)
+    sim.run_until(200.0)
+    assert np.abs(sim.hu - qn).max() / qn <= 1e-10
+    assert np.abs(sim.h - 0.5).max() <= 1e-10
+
+
+def test_inflow_wave_peak_and_quiet_start():
+    sc = W.coastal_dem(n=32, dx=100.0)
+    ts = np.linspace(0, 2.0 * sc.inflow_period, 20001)
+    e = np.array([oracle.inflow_eta(sc, t) for t in ts])
+    assert e.max() == pytest.approx(sc.inflow_amp, rel=1e-6)
+    assert abs(e[0]) < 1e-6 * sc.inflow_amp and abs(e[-1]) < 1e-6 * sc.inflow_amp
+    assert ts[np.argmax(e)] < ts[np.argmin(e)]  # the crest leads, the trough follows
+
+
+def test_solitary_wave_runup_follows_synolakis_law():
+    # frictionless variant of the 2048-cell planar beach (1-D in 2-D)
+    sc = W.planar_beach(ny=4, manning_n=0.0)
+    sim = oracle.Simulation(sc)
+    sim.run_until(70.0)
+    R = sim.diag()["runup_max"]
+    law = A.synolakis_runup(0.02, 20.0, 10.0)
+    assert abs(R - law) / law <= 0.10, (R, law)
