@@ -1,0 +1,289 @@
+"""Benchmark: cell-updates/s of the WENO5-LF / SSP-RK3 shallow-water step on
+one GB300, on the synthetic coastal DEM (4096 x 4096, dx = 5 m, N-wave
+inflow, FP32 state with FP64 reductions).
+
+One "step" is one full RK3 time step (three fused stage kernels) over the
+whole grid: 16.8 M cell-updates.  Inputs are resident in HBM and larger than
+L2 (ten 64 MB planes), so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun), each rank runs an independent replica of the same
+workload (the single-scenario path does not shard: replicas only) and the
+value is the sum over ranks of cell-updates divided by the slowest rank's
+time.  ``--impl reference`` times the FP64 CPU oracle on the host cores on a
+bounded window of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s/GPU FP32 vs FP64 (oracle-matched), %HBM roofline; p50/p99 solve ms"
+WORKLOAD = "synthetic coastal DEM 4096x4096, dx=5 m, shelf ramp -200 m to 0 + fractal noise (slope -2, 3 m rms), " \
+           "land to +20 m, N-wave inflow 4 m / 600 s, Manning n=0.025, FP32 state, FP64 dt/mass reductions"
+
+# Algorithmic work per cell and RK stage (see the design notes for the
+# derivation): FP32 flops counting an FMA as two, and HBM bytes per stage.
+FLOPS_PER_CELL_STAGE = 1007.0
+BYTES_PER_CELL_STAGE = {1: 28.0, 2: 40.0, 3: 40.0}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop/FMA x max SM clock
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        try:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+        except Exception:
+            pass
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(sc, budget_s: float = 12.0):
+    """The FP64 oracle on the host cores, on a bounded window of the same
+    workload: whole RK3 steps of the full grid until the budget is spent."""
+    import oracle
+    sim = oracle.Simulation(sc)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 3:
+        sim.step(1)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": sc.cells * steps / el, "unit": "cell-updates/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": "%d RK3 step(s) of the full %dx%d grid (FP64, %d threads)"
+            % (steps, sc.nx, sc.ny, oracle.num_threads())}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle on the host cores, each step one
+    RK3 step of a 512 x 512 window (the inflow edge) of the coastal DEM."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import workloads as W
+    oracle.build()
+    full = W.coastal_dem()
+    win = 512
+    sc = full.copy(b=full.b[:win, :win].copy(), h=full.h[:win, :win].copy(), hu=full.hu[:win, :win].copy(),
+                   hv=full.hv[:win, :win].copy())
+    sim = oracle.Simulation(sc)
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    el = time.perf_counter() - t0
+    v = sc.cells * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "512x512 window at the inflow edge per step"},
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": v,
+                             "unit": "cell-updates/s",
+                             "sample": "one RK3 step of a 512x512 window of the 4096x4096 coastal DEM per step"},
+            "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=4096, help="grid size of the coastal DEM")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2301_12010_gb300 as swe
+    import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sc = W.coastal_dem(n=args.n)
+    stream = torch.cuda.current_stream()
+    solver = swe.Solver(sc, precision=swe.F32, stream=stream.cuda_stream, tile=args.tile)
+    solver.step(args.warmup)
+    solver.sync()
+
+    clocks = ClockSampler(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    solver.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    solver.sync()
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    cells = sc.cells
+    value = cells * args.steps * ws / (ms_max / 1e3)
+
+    # per-stage kernel durations (CUDA events on the launching stream)
+    nst = 30
+    tot, st3 = solver.time_stages(nst)
+    stage_ms = [x / nst for x in st3]
+    dom = int(np.argmax(stage_ms)) + 1
+    pk, pk_kind = peaks()
+    dom_s = stage_ms[dom - 1] / 1e3
+    achieved_tf = FLOPS_PER_CELL_STAGE * cells / dom_s / 1e12
+    achieved_gbs = BYTES_PER_CELL_STAGE[dom] * cells / dom_s / 1e9
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    diag = solver.diagnostics()
+
+    # end to end through the public API: pinned host FP64 state in, one step,
+    # state out (bytes counted from the arrays copied)
+    pin = [torch.empty((sc.ny, sc.nx), dtype=torch.float64, pin_memory=True) for _ in range(6)]
+    for a, src in zip(pin[:3], (sc.h, sc.hu, sc.hv)):
+        a.numpy()[...] = src
+    hin = [a.numpy() for a in pin[:3]]
+    hout = tuple(a.numpy() for a in pin[3:])
+    solver.set_state(*hin)
+    solver.step(1)
+    solver.get_state(hout)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        solver.set_state(*hin)
+        solver.step(1)
+        solver.get_state(hout)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_v = cells * ws / e2e_s
+    solver.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": sc.nx, "ny": sc.ny, "cells": cells,
+                       "l2": "inputs larger than L2 (10 planes x %.0f MB)" % (cells * 4 / 1e6),
+                       "parallelism": "replicas" if ws > 1 else "single", "tile": diag["tile"]},
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "stage_kernel<float> RK stage %d" % dom,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                         "flops_per_cell_stage": FLOPS_PER_CELL_STAGE},
+            "hbm_roofline": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": achieved_gbs / hbm_peak, "peak_source": pk_kind,
+                             "bytes_per_cell_stage": BYTES_PER_CELL_STAGE[dom],
+                             "step_frac": (108.0 * cells * args.steps * ws / (ms_max / 1e3) / 1e9) / hbm_peak},
+            "stage_ms": stage_ms,
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk,
+            "e2e": {"value": e2e_v, "unit": "cell-updates/s", "h2d_bytes_per_step": 3 * 8 * cells,
+                    "d2h_bytes_per_step": 3 * 8 * cells,
+                    "how": "swe_set_state(pinned FP64 host) + swe_step(1) + swe_get_state(pinned FP64 host)"},
+            "sim": {"t": diag["t"], "steps": diag["steps"], "last_dt": diag["last_dt"]},
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(sc)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * swe.h -- C ABI of the GB300 (sm_103a) shallow-water solver.
+ *
+ * The solver advances the 2-D nonlinear shallow-water equations of the paper
+ * (Madden, Marras & Suckale, arXiv:2301.12010, "Numerical approximation",
+ * Eqs. (1)-(3)) with fifth-order WENO reconstruction and global
+ * Lax-Friedrichs flux splitting in x and y (Eqs. (5)-(6)), the well-balanced
+ * bed source term and explicit Manning friction, advanced by the TVD
+ * (SSP) Runge-Kutta scheme of Eq. (8).  The caller supplies bathymetry and an
+ * initial state, the library advances it, and the caller gathers results:
+ * the division of labour of the paper's "TPU implementation" (host
+ * initialises, device steps, host gathers).
+ *
+ * Conventions (all calls):
+ *  - Arrays are row-major [ny][nx] with x fastest, SI units (m, m^2/s).
+ *  - Host arrays passed to the library are FP64 and are copied; the caller
+ *    keeps ownership.  Device arrays (the *_device calls) are contiguous
+ *    [ny][nx] of the handle's precision (float for SWE_F32, double for
+ *    SWE_F64) and stay owned by the caller.
+ *  - Every call returns an SWE_* status.  No call aborts and no device code
+ *    traps.  Errors raised by asynchronous work (swe_step) surface at the next
+ *    synchronising call (swe_get_state, swe_mass, swe_runup, swe_get_time,
+ *    swe_diagnostics, swe_sync) or at swe_status.
+ *  - A handle is not thread-safe: one host thread at a time.
+ *  - Grids need nx >= 3 and ny >= 3 (the WENO5 ghost width).
+ */
+#ifndef SWE_H
+#define SWE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+  SWE_OK = 0,
+  SWE_EINVAL = 1,     /* invalid argument, or CFL time step undefined (fully dry, still domain) */
+  SWE_ENOMEM = 2,     /* device or host allocation failed */
+  SWE_ECUDA = 3,      /* a CUDA call failed (kernel launch, copy, graph) */
+  SWE_ENONFINITE = 4, /* NaN/Inf met in a reduction; later stages were skipped */
+  SWE_ETIMEOUT = 5,   /* a bounded device-side wait expired (persistent batch barrier) */
+  SWE_EBUDGET = 6,    /* admission would exceed the batch's HBM budget */
+  SWE_EFULL = 7       /* no free batch slot */
+};
+
+typedef enum { SWE_F32 = 0, SWE_F64 = 1 } swe_precision;
+
+/* Boundary types, per side.  WALL: free-slip, no-penetration wall (the
+ * tsunami runs of "Validation for tsunami simulations": ghost cells mirror
+ * depth, bed and tangential momentum and negate normal momentum).  INFLOW
+ * (x- side only): ghost cells carry the Carrier N-wave of Eq. (20) in time
+ * with amplitude inflow_amp (peak elevation), period inflow_period and
+ * offshore depth inflow_depth, as an incoming long wave.  PERIODIC (tests):
+ * wrap-around, with the bed offset b_jump_x/y added across the seam. */
+typedef enum { SWE_BC_WALL = 0, SWE_BC_INFLOW = 1, SWE_BC_PERIODIC = 2 } swe_bc;
+
+typedef struct {
+  int32_t nx, ny; /* interior cells along x and y */
+} swe_grid;
+
+typedef struct {
+  double g;             /* gravity, 9.81 m s^-2 (Eqs. (1)-(3)) */
+  double manning_n;     /* Manning n of Eqs. (2)-(3); 0 disables friction */
+  double h_dry;         /* depth below which a cell is dry (compared in FP64); 1e-5 m */
+  double h_wet;         /* depth from which a land cell (b > 0) counts for runup; 1e-3 m */
+  double weno_eps;      /* WENO5 epsilon; 1e-6 */
+  double fixed_dt;      /* > 0: fixed time step (the paper's runs use 5e-3 s); else CFL */
+  double z_ref;         /* still-water level of the bed splitting; 0 m */
+  double b_jump_x;      /* PERIODIC x: b(i + nx) = b(i) + b_jump_x */
+  double b_jump_y;      /* PERIODIC y: b(j + ny) = b(j) + b_jump_y */
+  double inflow_amp;    /* INFLOW: peak surface elevation (m) */
+  double inflow_period; /* INFLOW: N-wave period T (s) */
+  double inflow_depth;  /* INFLOW: offshore depth d0 (m) */
+  int32_t bc[4];        /* sides x-, x+, y-, y+ (swe_bc) */
+  int32_t precision;    /* swe_precision of state and arithmetic */
+  int32_t tile;         /* 0: autotuned/default tile shape; k > 0: compiled shape k */
+  void *stream;         /* cudaStream_t to run on (e.g. torch.cuda.Stream().cuda_stream); NULL = legacy default */
+} swe_params;
+
+typedef struct {
+  double t;             /* simulated time of the current state */
+  int64_t steps;        /* RK3 steps taken since the last swe_set_time/swe_create */
+  double last_dt;       /* time step of the last step */
+  double alpha_x;       /* global max |u| + sqrt(g h) of the current state */
+  double alpha_y;       /* global max |v| + sqrt(g h) of the current state */
+  double clamp_mass;    /* mass added by the h < 0 clamp, RK-weighted (m^3) */
+  double boundary_mass; /* mass that entered through the edges, RK-weighted (m^3) */
+  double runup_now;     /* max h+b over land cells (b > 0) with h >= h_wet; -inf if none */
+  double runup_max;     /* running maximum of runup_now */
+  int32_t status;       /* SWE_* status of the device work so far */
+  int32_t tile;         /* tile shape in use */
+} swe_diag;
+
+typedef struct swe_handle swe_handle; /* opaque; owns its device memory */
+
+/* Fill *p with the defaults listed above (walls on all sides, FP32). */
+void swe_params_default(swe_params *p);
+
+/* Create a solver for grid *grid with spacings dx, dy (m) over the host FP64
+ * bathymetry b[ny][nx] (m, positive up).  Allocates all device memory the
+ * stepping needs; no later call allocates.  The state is zero until
+ * swe_set_state.  *out receives the handle, or NULL on error. */
+int swe_create(const swe_grid *grid, double dx, double dy, const double *bathymetry,
+               const swe_params *params, swe_handle **out);
+
+/* Copy a host FP64 state h, hu, hv [ny][nx] to the device (converted to the
+ * handle's precision), and evaluate the wave speeds and runup of that
+ * state.  Synchronous. */
+int swe_set_state(swe_handle *s, const double *h, const double *hu, const double *hv);
+
+/* Same from device arrays of the handle's precision (contiguous [ny][nx],
+ * owned by the caller, read on the handle's stream). */
+int swe_set_state_device(swe_handle *s, const void *h, const void *hu, const void *hv);
+
+/* Enqueue n RK3 steps (Eq. (8)) on the handle's stream.  Each step runs three
+ * stage kernels; the time step is dt = cfl / (alpha_x/dx + alpha_y/dy) from
+ * the step's first stage (ignored if fixed_dt > 0).  Asynchronous: no host
+ * synchronisation; steps are replayed from a captured CUDA graph. */
+int swe_step(swe_handle *s, int32_t n, double cfl);
+
+/* Wait for the handle's stream and report the device status. */
+int swe_sync(swe_handle *s);
+
+/* Copy the current state to host FP64 arrays [ny][nx].  Synchronises. */
+int swe_get_state(swe_handle *s, double *h, double *hu, double *hv);
+
+/* Copy the current state into caller device arrays of the handle's
+ * precision (contiguous [ny][nx]).  Synchronises. */
+int swe_get_state_device(swe_handle *s, void *h, void *hu, void *hv);
+
+/* Total water volume sum(h) dx dy (FP64, fixed summation order) and the
+ * clamp-added volume.  Synchronises. */
+int swe_mass(swe_handle *s, double *mass, double *clamp_mass);
+
+/* Runup: running maximum and current value (m; -inf if no wet land cell).
+ * Synchronises. */
+int swe_runup(swe_handle *s, double *runup_max, double *runup_now);
+
+/* Simulated time and step count.  Synchronises. */
+int swe_get_time(swe_handle *s, double *t, int64_t *steps);
+
+/* Set the simulated time (resume from a checkpoint); resets the step count. */
+int swe_set_time(swe_handle *s, double t);
+
+/* All diagnostics at once.  Synchronises. */
+int swe_diagnostics(swe_handle *s, swe_diag *d);
+
+/* Status of the device work so far, without waiting for it. */
+int swe_status(swe_handle *s);
+
+/* Static text for a status code. */
+const char *swe_strerror(int code);
+
+/* Free the handle and its device memory.  NULL-safe; returns SWE_OK. */
+int swe_destroy(swe_handle *s);
+
+/* Number of compiled tile shapes and the shape of entry k (1-based). */
+int swe_tile_count(void);
+int swe_tile_shape(int k, int32_t *tx, int32_t *ty, int32_t *threads);
+
+/* Timing helper for benchmarks: enqueue n steps as individual stage launches
+ * (not the graph) with a CUDA event recorded on the handle's stream around
+ * each stage kernel, wait, and return the summed milliseconds of whole steps
+ * (*ms_total) and of each stage kernel (ms_stage[3], may be NULL). */
+int swe_time_stages(swe_handle *s, int32_t n, double cfl, double *ms_total, double *ms_stage);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWE_H */

@@ -1,0 +1,241 @@
+"""GB300 (sm_103a) solver for the 2-D nonlinear shallow-water equations with
+WENO5 / global Lax-Friedrichs flux splitting and SSP-RK3 (the method of
+arXiv:2301.12010, "Numerical approximation").
+
+This module is a thin ctypes binding over the C ABI of ``libswe.so``
+(declared in ``include/swe.h``): it marshals arguments and nothing else.
+Every step of the solver runs in the library's CUDA kernels; there is no
+CPU fallback.  If the library is missing the import fails loudly; build it
+with ``python -c "import __graft_entry__ as g; g.build()"``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional, Sequence, Tuple
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libswe.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EBUDGET, EFULL = range(8)
+F32, F64 = 0, 1
+WALL, INFLOW, PERIODIC = 0, 1, 2
+
+
+class SweError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = _strerror(code)
+        super().__init__("%s: %s (status %d)" % (what, msg, code) if what else "%s (status %d)" % (msg, code))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("g", ctypes.c_double), ("manning_n", ctypes.c_double), ("h_dry", ctypes.c_double),
+        ("h_wet", ctypes.c_double), ("weno_eps", ctypes.c_double), ("fixed_dt", ctypes.c_double),
+        ("z_ref", ctypes.c_double), ("b_jump_x", ctypes.c_double), ("b_jump_y", ctypes.c_double),
+        ("inflow_amp", ctypes.c_double), ("inflow_period", ctypes.c_double), ("inflow_depth", ctypes.c_double),
+        ("bc", ctypes.c_int32 * 4), ("precision", ctypes.c_int32), ("tile", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_double), ("steps", ctypes.c_int64), ("last_dt", ctypes.c_double),
+        ("alpha_x", ctypes.c_double), ("alpha_y", ctypes.c_double), ("clamp_mass", ctypes.c_double),
+        ("boundary_mass", ctypes.c_double), ("runup_now", ctypes.c_double), ("runup_max", ctypes.c_double),
+        ("status", ctypes.c_int32), ("tile", ctypes.c_int32),
+    ]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libswe.so is not built (%s); run __graft_entry__.build() on a machine with nvcc"
+                          % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    H = ctypes.c_void_p
+    sig = {
+        "swe_params_default": (None, [ctypes.POINTER(Params)]),
+        "swe_create": (ip, [ctypes.POINTER(Grid), ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(Params),
+                            ctypes.POINTER(H)]),
+        "swe_set_state": (ip, [H, dp, dp, dp]),
+        "swe_set_state_device": (ip, [H, vp, vp, vp]),
+        "swe_step": (ip, [H, ctypes.c_int32, ctypes.c_double]),
+        "swe_sync": (ip, [H]),
+        "swe_get_state": (ip, [H, dp, dp, dp]),
+        "swe_get_state_device": (ip, [H, vp, vp, vp]),
+        "swe_mass": (ip, [H, dp, dp]),
+        "swe_runup": (ip, [H, dp, dp]),
+        "swe_get_time": (ip, [H, dp, ctypes.POINTER(ctypes.c_int64)]),
+        "swe_set_time": (ip, [H, ctypes.c_double]),
+        "swe_diagnostics": (ip, [H, ctypes.POINTER(Diag)]),
+        "swe_status": (ip, [H]),
+        "swe_strerror": (ctypes.c_char_p, [ip]),
+        "swe_destroy": (ip, [H]),
+        "swe_tile_count": (ip, []),
+        "swe_tile_shape": (ip, [ip, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_int32)]),
+        "swe_time_stages": (ip, [H, ctypes.c_int32, ctypes.c_double, dp, dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _strerror(code: int) -> str:
+    return lib.swe_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str = "") -> None:
+    if rc != OK:
+        raise SweError(rc, what)
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def tile_shapes() -> Sequence[Tuple[int, int, int]]:
+    out = []
+    for k in range(1, lib.swe_tile_count() + 1):
+        tx, ty, nt = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.swe_tile_shape(k, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(nt)))
+        out.append((tx.value, ty.value, nt.value))
+    return out
+
+
+def params_for(sc, precision: int = F32, stream: Optional[int] = None, tile: int = 0) -> Params:
+    """swe_params from a workload description (any object with the fields)."""
+    p = Params()
+    lib.swe_params_default(ctypes.byref(p))
+    p.g, p.manning_n, p.h_dry, p.h_wet = sc.g, sc.manning_n, sc.h_dry, sc.h_wet
+    p.weno_eps, p.fixed_dt, p.z_ref = sc.weno_eps, sc.fixed_dt, sc.z_ref
+    p.b_jump_x, p.b_jump_y = sc.b_jump_x, sc.b_jump_y
+    p.inflow_amp, p.inflow_period, p.inflow_depth = sc.inflow_amp, sc.inflow_period, sc.inflow_depth
+    for k in range(4):
+        p.bc[k] = int(sc.bc[k])
+    p.precision = int(precision)
+    p.tile = int(tile)
+    p.stream = stream
+    return p
+
+
+class Solver:
+    """One scenario on the GPU, driven through the C ABI."""
+
+    def __init__(self, sc, precision: int = F32, stream: Optional[int] = None, tile: int = 0,
+                 set_state: bool = True):
+        self.sc = sc
+        self.precision = precision
+        self.nx, self.ny = sc.nx, sc.ny
+        self._h = ctypes.c_void_p()
+        b = np.ascontiguousarray(sc.b, dtype=np.float64)
+        g = Grid(sc.nx, sc.ny)
+        self.params = params_for(sc, precision, stream, tile)
+        _check(lib.swe_create(ctypes.byref(g), float(sc.dx), float(sc.dy), _dp(b), ctypes.byref(self.params),
+                              ctypes.byref(self._h)), "swe_create")
+        if sc.t0:
+            _check(lib.swe_set_time(self._h, float(sc.t0)), "swe_set_time")
+        if set_state:
+            self.set_state(sc.h, sc.hu, sc.hv)
+
+    # -- life cycle
+    def close(self) -> None:
+        if self._h:
+            lib.swe_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- state
+    def set_state(self, h, hu, hv) -> None:
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (h, hu, hv)]
+        _check(lib.swe_set_state(self._h, *[_dp(x) for x in a]), "swe_set_state")
+
+    def set_state_device(self, h, hu, hv) -> None:
+        """From device tensors (torch) of the solver's precision, contiguous [ny][nx]."""
+        _check(lib.swe_set_state_device(self._h, h.data_ptr(), hu.data_ptr(), hv.data_ptr()),
+               "swe_set_state_device")
+
+    def get_state(self, out=None) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+        if out is None:
+            out = tuple(np.empty((self.ny, self.nx), dtype=np.float64) for _ in range(3))
+        _check(lib.swe_get_state(self._h, *[_dp(x) for x in out]), "swe_get_state")
+        return out
+
+    def get_state_device(self, h, hu, hv) -> None:
+        _check(lib.swe_get_state_device(self._h, h.data_ptr(), hu.data_ptr(), hv.data_ptr()),
+               "swe_get_state_device")
+
+    # -- stepping
+    def step(self, n: int, cfl: Optional[float] = None) -> None:
+        c = self.sc.cfl if cfl is None else cfl
+        _check(lib.swe_step(self._h, int(n), float(c)), "swe_step")
+
+    def sync(self) -> None:
+        _check(lib.swe_sync(self._h), "swe_sync")
+
+    def status(self) -> int:
+        return int(lib.swe_status(self._h))
+
+    def set_time(self, t: float) -> None:
+        _check(lib.swe_set_time(self._h, float(t)), "swe_set_time")
+
+    # -- diagnostics
+    def diagnostics(self, check: bool = True) -> Dict[str, float]:
+        d = Diag()
+        rc = lib.swe_diagnostics(self._h, ctypes.byref(d))
+        if check:
+            _check(rc, "swe_diagnostics")
+        return dict(t=d.t, steps=int(d.steps), last_dt=d.last_dt, alpha_x=d.alpha_x, alpha_y=d.alpha_y,
+                    clamp_mass=d.clamp_mass, boundary_mass=d.boundary_mass, runup_now=d.runup_now,
+                    runup_max=d.runup_max, status=int(d.status), tile=int(d.tile))
+
+    def mass(self) -> Tuple[float, float]:
+        m, c = ctypes.c_double(), ctypes.c_double()
+        _check(lib.swe_mass(self._h, ctypes.byref(m), ctypes.byref(c)), "swe_mass")
+        return m.value, c.value
+
+    def runup(self) -> Tuple[float, float]:
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib.swe_runup(self._h, ctypes.byref(a), ctypes.byref(b)), "swe_runup")
+        return a.value, b.value
+
+    def time(self) -> Tuple[float, int]:
+        t, n = ctypes.c_double(), ctypes.c_int64()
+        _check(lib.swe_get_time(self._h, ctypes.byref(t), ctypes.byref(n)), "swe_get_time")
+        return t.value, int(n.value)
+
+    def time_stages(self, n: int, cfl: Optional[float] = None) -> Tuple[float, Tuple[float, float, float]]:
+        c = self.sc.cfl if cfl is None else cfl
+        tot = ctypes.c_double()
+        st = (ctypes.c_double * 3)()
+        _check(lib.swe_time_stages(self._h, int(n), float(c), ctypes.byref(tot), st), "swe_time_stages")
+        return tot.value, (st[0], st[1], st[2])

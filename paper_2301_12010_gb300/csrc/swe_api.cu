@@ -1,0 +1,617 @@
+// swe_api.cu -- C ABI of the single-scenario solver (include/swe.h): handle
+// life cycle, host/device transfers, the CUDA-graph step loop, diagnostics
+// and the small helper kernels (format conversion, state statistics, mass).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/swe.h"
+#include "swe_launch.h"
+
+using namespace swe;
+
+namespace {
+
+// ---------------------------------------------------------------- kernels
+template <typename T>
+__global__ void k_from_f64(const double *__restrict__ src, T *__restrict__ dst, int nx, int ny, int pitch) {
+  const size_t n = (size_t)nx * ny;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = q / nx, i = q - j * nx;
+    dst[j * pitch + i] = (T)src[q];
+  }
+}
+
+template <typename T>
+__global__ void k_to_f64(const T *__restrict__ src, double *__restrict__ dst, int nx, int ny, int pitch) {
+  const size_t n = (size_t)nx * ny;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = q / nx, i = q - j * nx;
+    dst[q] = (double)src[j * pitch + i];
+  }
+}
+
+__global__ void k_set_cfl(DevScalars *sc, double cfl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc->cfl = cfl;
+}
+
+__global__ void k_reset(DevScalars *sc, double t, double cfl, double t_end) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    for (int s = 0; s < 3; ++s) sc->alpha[s][0] = sc->alpha[s][1] = 0ull;
+    sc->dt = 0.0;
+    sc->t = t;
+    sc->t_step = t;
+    sc->steps = 0;
+    sc->runup_now[0] = sc->runup_now[1] = 0ull;
+    sc->runup_max = 0ull;
+    sc->clamp_mass = 0.0;
+    sc->boundary_mass = 0.0;
+    sc->t_end = t_end;
+    sc->cfl = cfl;
+    sc->status = 0u;
+    sc->running = 0u;
+    sc->parity = 1u;  // runup_now of "step -1" lives at parity 1 (steps = 0 -> next writes parity 0)
+    sc->active = 1u;
+  }
+}
+
+// Wave speeds (slot 0) and runup of the current state U^n, with the same
+// in-precision arithmetic as the stage epilogue (so that a state written out
+// and set again gives the same time step as an uninterrupted run).
+template <typename T>
+__global__ void k_state_stats(Field<T> fd, Phys p, DevScalars *sc) {
+  __shared__ double sm[32][3];
+  __shared__ unsigned sbad;
+  if (threadIdx.x == 0) sbad = 0u;
+  __syncthreads();
+  T mx = T(0), my = T(0), ru = T(0);
+  bool bad = false;
+  const T g = T(p.g);
+  const size_t n = (size_t)fd.nx * fd.ny;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = q / fd.nx, i = q - j * fd.nx;
+    const size_t o = j * fd.pitch + i;
+    const T h = fd.h[0][o], hu = fd.hu[0][o], hv = fd.hv[0][o];
+    if (!(fabs(h) <= T(3.0e38)) || !(fabs(hu) <= T(3.0e38)) || !(fabs(hv) <= T(3.0e38))) { bad = true; continue; }
+    T u = T(0), v = T(0);
+    if (!Num<T>::below(h, p.h_dry32, p.h_dry)) { const T rr = Num<T>::rcp(h); u = hu * rr; v = hv * rr; }
+    const T cel = Num<T>::sqrt_(g * (h > T(0) ? h : T(0)));
+    const T sx = fabs(u) + cel, sy = fabs(v) + cel;
+    mx = sx > mx ? sx : mx;
+    my = sy > my ? sy : my;
+    const T b = fd.b[o];
+    if (!Num<T>::below(h, p.h_wet32, p.h_wet) && b > T(0)) { const T e = h + b; ru = e > ru ? e : ru; }
+  }
+  mx = warp_max(mx);
+  my = warp_max(my);
+  ru = warp_max(ru);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) sbad = 1u;
+  if ((threadIdx.x & 31) == 0) {
+    sm[threadIdx.x >> 5][0] = (double)mx;
+    sm[threadIdx.x >> 5][1] = (double)my;
+    sm[threadIdx.x >> 5][2] = (double)ru;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = sm[0][0], b = sm[0][1], r = sm[0][2];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      a = fmax(a, sm[w][0]);
+      b = fmax(b, sm[w][1]);
+      r = fmax(r, sm[w][2]);
+    }
+    atomicMax(&sc->alpha[0][0], (unsigned long long)__double_as_longlong(a));
+    atomicMax(&sc->alpha[0][1], (unsigned long long)__double_as_longlong(b));
+    if (r > 0.0) {
+      atomicMax(&sc->runup_now[1], (unsigned long long)__double_as_longlong(r));
+      atomicMax(&sc->runup_max, (unsigned long long)__double_as_longlong(r));
+    }
+    if (sbad) atomicOr(&sc->status, ST_NONFINITE);
+  }
+}
+
+// Mass, pass 1: per-block FP64 partial sums of h over rows, fixed order.
+template <typename T>
+__global__ void k_mass_partial(const T *__restrict__ h, int nx, int ny, int pitch, double *__restrict__ part) {
+  __shared__ double sm[32];
+  double s = 0.0;
+  const size_t n = (size_t)nx * ny;
+  const size_t per = (n + gridDim.x - 1) / gridDim.x;
+  const size_t lo = blockIdx.x * per, hi = lo + per < n ? lo + per : n;
+  for (size_t q = lo + threadIdx.x; q < hi; q += blockDim.x) {
+    const size_t j = q / nx, i = q - j * nx;
+    s += (double)h[j * pitch + i];
+  }
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// Mass, pass 2: one block sums the partials in a fixed tree order.
+__global__ void k_mass_final(const double *__restrict__ part, int n, double area, double *__restrict__ out) {
+  __shared__ double sm[1024];
+  double s = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) s += part[q];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sm[0] * area;
+}
+
+constexpr int kMassBlocks = 1024;
+
+float thr32(double thr) {
+  // smallest float f with (double)f >= thr: comparing h < f in FP32 is the
+  // same predicate as (double)h < thr
+  float f = (float)thr;
+  if ((double)f < thr) f = std::nextafter(f, INFINITY);
+  while ((double)std::nextafter(f, -INFINITY) >= thr) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+
+}  // namespace
+
+struct swe_handle {
+  int nx = 0, ny = 0, pitch = 0;
+  double dx = 0, dy = 0;
+  swe_params prm{};
+  Phys phys{};
+  int prec = SWE_F32;
+  int tile = 1;
+  size_t elem = 4;
+  cudaStream_t stream = nullptr;  // caller's stream (may be the legacy default)
+  cudaStream_t cap = nullptr;     // private stream used for graph capture
+  void *mem = nullptr;            // one device allocation for all planes
+  void *b = nullptr;
+  void *h[3] = {}, *hu[3] = {}, *hv[3] = {};
+  double *staging = nullptr;      // ny*nx doubles: host-format transfers
+  DevScalars *sc = nullptr;
+  double *partials = nullptr;     // kMassBlocks + 1 (last: mass result)
+  cudaGraphExec_t graph = nullptr;
+  double cfl_dev = -1.0;          // CFL value last written to the device scalars
+  int sticky = SWE_OK;            // first host-visible error
+};
+
+namespace {
+
+int fail(swe_handle *s, int code) {
+  if (s && s->sticky == SWE_OK) s->sticky = code;
+  return code;
+}
+
+int cuda_check(swe_handle *s, cudaError_t e) {
+  if (e == cudaSuccess) return SWE_OK;
+  (void)cudaGetLastError();
+  return fail(s, e == cudaErrorMemoryAllocation ? SWE_ENOMEM : SWE_ECUDA);
+}
+
+template <typename T>
+Field<T> field_of(const swe_handle *s) {
+  Field<T> f;
+  f.b = (const T *)s->b;
+  for (int k = 0; k < 3; ++k) {
+    f.h[k] = (T *)s->h[k];
+    f.hu[k] = (T *)s->hu[k];
+    f.hv[k] = (T *)s->hv[k];
+  }
+  f.nx = s->nx;
+  f.ny = s->ny;
+  f.pitch = s->pitch;
+  return f;
+}
+
+int grid_blocks(size_t n, int threads) {
+  size_t b = (n + threads - 1) / threads;
+  if (b > 4096) b = 4096;
+  return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t enqueue_step(swe_handle *s, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
+    if (s->prec == SWE_F64) e = launch_stage<double>(s->tile, field_of<double>(s), s->phys, s->sc, stage, st);
+    else e = launch_stage<float>(s->tile, field_of<float>(s), s->phys, s->sc, stage, st);
+  }
+  return e;
+}
+
+int device_status(swe_handle *s) {
+  unsigned st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, &s->sc->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_check(s, e);
+  if (st & ST_TIMEOUT) return SWE_ETIMEOUT;
+  if (st & ST_NONFINITE) return SWE_ENONFINITE;
+  if (st & ST_DRY) return SWE_EINVAL;
+  return SWE_OK;
+}
+
+int upload_field(swe_handle *s, const double *src, void *dst) {
+  cudaError_t e = cudaMemcpyAsync(s->staging, src, sizeof(double) * (size_t)s->nx * s->ny, cudaMemcpyHostToDevice,
+                                  s->stream);
+  if (e != cudaSuccess) return cuda_check(s, e);
+  const size_t n = (size_t)s->nx * s->ny;
+  if (s->prec == SWE_F64) k_from_f64<double><<<grid_blocks(n, 256), 256, 0, s->stream>>>(s->staging, (double *)dst, s->nx, s->ny, s->pitch);
+  else k_from_f64<float><<<grid_blocks(n, 256), 256, 0, s->stream>>>(s->staging, (float *)dst, s->nx, s->ny, s->pitch);
+  return cuda_check(s, cudaGetLastError());
+}
+
+int download_field(swe_handle *s, const void *src, double *dst) {
+  const size_t n = (size_t)s->nx * s->ny;
+  if (s->prec == SWE_F64) k_to_f64<double><<<grid_blocks(n, 256), 256, 0, s->stream>>>((const double *)src, s->staging, s->nx, s->ny, s->pitch);
+  else k_to_f64<float><<<grid_blocks(n, 256), 256, 0, s->stream>>>((const float *)src, s->staging, s->nx, s->ny, s->pitch);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, s->staging, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream);
+  return cuda_check(s, e);
+}
+
+int after_state_change(swe_handle *s) {
+  // scalars: keep t, clear everything else; then wave speeds + runup of U^n
+  double t = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&t, &s->sc->t, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_check(s, e);
+  k_reset<<<1, 32, 0, s->stream>>>(s->sc, t, s->cfl_dev > 0 ? s->cfl_dev : 0.4, 0.0);
+  const size_t n = (size_t)s->nx * s->ny;
+  if (s->prec == SWE_F64) k_state_stats<double><<<grid_blocks(n, 256), 256, 0, s->stream>>>(field_of<double>(s), s->phys, s->sc);
+  else k_state_stats<float><<<grid_blocks(n, 256), 256, 0, s->stream>>>(field_of<float>(s), s->phys, s->sc);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (s->cfl_dev <= 0) s->cfl_dev = 0.4;
+  return cuda_check(s, e);
+}
+
+bool valid_params(const swe_params *p) {
+  if (!p) return false;
+  if (p->precision != SWE_F32 && p->precision != SWE_F64) return false;
+  for (int k = 0; k < 4; ++k)
+    if (p->bc[k] < SWE_BC_WALL || p->bc[k] > SWE_BC_PERIODIC) return false;
+  if ((p->bc[0] == SWE_BC_PERIODIC) != (p->bc[1] == SWE_BC_PERIODIC)) return false;
+  if ((p->bc[2] == SWE_BC_PERIODIC) != (p->bc[3] == SWE_BC_PERIODIC)) return false;
+  if (p->bc[1] == SWE_BC_INFLOW || p->bc[2] == SWE_BC_INFLOW || p->bc[3] == SWE_BC_INFLOW) return false;
+  if (p->bc[0] == SWE_BC_INFLOW && !(p->inflow_depth > 0.0 && p->inflow_period > 0.0)) return false;
+  if (!(p->g > 0.0) || !(p->manning_n >= 0.0) || !(p->h_dry >= 0.0) || !(p->h_wet >= 0.0) || !(p->weno_eps > 0.0))
+    return false;
+  if (!std::isfinite(p->z_ref) || !std::isfinite(p->fixed_dt)) return false;
+  if (p->tile < 0 || p->tile > num_shapes()) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void swe_params_default(swe_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->g = 9.81;
+  p->manning_n = 0.0;
+  p->h_dry = 1e-5;
+  p->h_wet = 1e-3;
+  p->weno_eps = 1e-6;
+  p->fixed_dt = 0.0;
+  p->z_ref = 0.0;
+  for (int k = 0; k < 4; ++k) p->bc[k] = SWE_BC_WALL;
+  p->precision = SWE_F32;
+  p->tile = 0;
+  p->stream = nullptr;
+}
+
+const char *swe_strerror(int code) {
+  switch (code) {
+    case SWE_OK: return "ok";
+    case SWE_EINVAL: return "invalid argument (or CFL time step undefined: dry, still domain)";
+    case SWE_ENOMEM: return "out of memory";
+    case SWE_ECUDA: return "CUDA error";
+    case SWE_ENONFINITE: return "non-finite value in the state";
+    case SWE_ETIMEOUT: return "bounded device wait expired";
+    case SWE_EBUDGET: return "HBM budget exceeded";
+    case SWE_EFULL: return "no free slot";
+  }
+  return "unknown status";
+}
+
+int swe_tile_count(void) { return num_shapes(); }
+
+int swe_tile_shape(int k, int32_t *tx, int32_t *ty, int32_t *threads) {
+  const TileShape *t = shape(k);
+  if (!t) return SWE_EINVAL;
+  if (tx) *tx = t->tx;
+  if (ty) *ty = t->ty;
+  if (threads) *threads = t->threads;
+  return SWE_OK;
+}
+
+int swe_create(const swe_grid *grid, double dx, double dy, const double *bathymetry, const swe_params *params,
+               swe_handle **out) {
+  if (out) *out = nullptr;
+  if (!grid || !out || !bathymetry || !valid_params(params)) return SWE_EINVAL;
+  if (grid->nx < 3 || grid->ny < 3 || !(dx > 0.0) || !(dy > 0.0)) return SWE_EINVAL;
+  if ((long long)grid->nx * grid->ny > (1ll << 31)) return SWE_EINVAL;
+  swe_handle *s = new (std::nothrow) swe_handle();
+  if (!s) return SWE_ENOMEM;
+  s->nx = grid->nx;
+  s->ny = grid->ny;
+  s->dx = dx;
+  s->dy = dy;
+  s->prm = *params;
+  s->prec = params->precision;
+  s->elem = s->prec == SWE_F64 ? 8 : 4;
+  s->tile = params->tile > 0 ? params->tile : 1;
+  s->stream = (cudaStream_t)params->stream;
+  const int align = 32;  // elements: 128 B rows in FP32, 256 B in FP64
+  s->pitch = ((s->nx + align - 1) / align) * align;
+
+  Phys &ph = s->phys;
+  ph.g = params->g;
+  ph.n2 = params->manning_n * params->manning_n;
+  ph.h_dry = params->h_dry;
+  ph.h_wet = params->h_wet;
+  ph.weno_eps = params->weno_eps;
+  ph.fixed_dt = params->fixed_dt;
+  ph.z_ref = params->z_ref;
+  ph.b_jump_x = params->b_jump_x;
+  ph.b_jump_y = params->b_jump_y;
+  ph.inflow_amp = params->inflow_amp;
+  ph.inflow_period = params->inflow_period;
+  ph.inflow_depth = params->inflow_depth;
+  ph.dx = dx;
+  ph.dy = dy;
+  ph.h_dry32 = thr32(params->h_dry);
+  ph.h_wet32 = thr32(params->h_wet);
+  for (int k = 0; k < 4; ++k) ph.bc[k] = params->bc[k];
+
+  const size_t plane = (size_t)s->pitch * s->ny * s->elem;
+  const size_t plane_al = (plane + 255) & ~(size_t)255;
+  const size_t stag = ((sizeof(double) * (size_t)s->nx * s->ny) + 255) & ~(size_t)255;
+  const size_t scal = (sizeof(DevScalars) + 255) & ~(size_t)255;
+  const size_t part = sizeof(double) * (kMassBlocks + 1);
+  const size_t total = plane_al * 10 + stag + scal + part;
+  cudaError_t e = cudaMalloc(&s->mem, total);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete s;
+    return e == cudaErrorMemoryAllocation ? SWE_ENOMEM : SWE_ECUDA;
+  }
+  char *q = (char *)s->mem;
+  s->b = q; q += plane_al;
+  for (int k = 0; k < 3; ++k) {
+    s->h[k] = q; q += plane_al;
+    s->hu[k] = q; q += plane_al;
+    s->hv[k] = q; q += plane_al;
+  }
+  s->staging = (double *)q; q += stag;
+  s->sc = (DevScalars *)q; q += scal;
+  s->partials = (double *)q;
+
+  int rc = SWE_OK;
+  if (cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) rc = SWE_ECUDA;
+  if (rc == SWE_OK) {
+    e = s->prec == SWE_F64 ? prepare_shape<double>(s->tile) : prepare_shape<float>(s->tile);
+    rc = cuda_check(s, e);
+  }
+  if (rc == SWE_OK) rc = cuda_check(s, cudaMemsetAsync(s->mem, 0, plane_al * 10, s->stream));
+  if (rc == SWE_OK) {
+    k_reset<<<1, 32, 0, s->stream>>>(s->sc, 0.0, 0.4, 0.0);
+    rc = cuda_check(s, cudaGetLastError());
+  }
+  if (rc == SWE_OK) rc = upload_field(s, bathymetry, s->b);
+  if (rc == SWE_OK) rc = cuda_check(s, cudaStreamSynchronize(s->stream));
+  if (rc != SWE_OK) {
+    swe_destroy(s);
+    return rc;
+  }
+  s->cfl_dev = 0.4;
+  *out = s;
+  return SWE_OK;
+}
+
+int swe_set_state(swe_handle *s, const double *h, const double *hu, const double *hv) {
+  if (!s || !h || !hu || !hv) return SWE_EINVAL;
+  int rc = upload_field(s, h, s->h[0]);
+  if (rc == SWE_OK) rc = upload_field(s, hu, s->hu[0]);
+  if (rc == SWE_OK) rc = upload_field(s, hv, s->hv[0]);
+  if (rc == SWE_OK) rc = after_state_change(s);
+  return rc;
+}
+
+int swe_set_state_device(swe_handle *s, const void *h, const void *hu, const void *hv) {
+  if (!s || !h || !hu || !hv) return SWE_EINVAL;
+  const size_t row = s->elem * (size_t)s->nx;
+  cudaError_t e = cudaMemcpy2DAsync(s->h[0], s->elem * s->pitch, h, row, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(s->hu[0], s->elem * s->pitch, hu, row, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(s->hv[0], s->elem * s->pitch, hv, row, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
+  if (e != cudaSuccess) return cuda_check(s, e);
+  return after_state_change(s);
+}
+
+int swe_step(swe_handle *s, int32_t n, double cfl) {
+  if (!s || n < 0) return SWE_EINVAL;
+  if (s->prm.fixed_dt <= 0.0 && !(cfl > 0.0 && std::isfinite(cfl))) return SWE_EINVAL;
+  if (n == 0) return SWE_OK;
+  cudaError_t e = cudaSuccess;
+  if (s->prm.fixed_dt <= 0.0 && cfl != s->cfl_dev) {
+    // ordered on the stream before the steps; the captured graph reads it
+    k_set_cfl<<<1, 32, 0, s->stream>>>(s->sc, cfl);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(s, e);
+    s->cfl_dev = cfl;
+  }
+  if (!s->graph) {
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t le = enqueue_step(s, s->cap);
+      e = cudaStreamEndCapture(s->cap, &g);
+      if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      s->graph = nullptr;
+      return cuda_check(s, e);
+    }
+  }
+  for (int32_t k = 0; k < n && e == cudaSuccess; ++k) e = cudaGraphLaunch(s->graph, s->stream);
+  return cuda_check(s, e);
+}
+
+int swe_sync(swe_handle *s) {
+  if (!s) return SWE_EINVAL;
+  if (s->sticky != SWE_OK) return s->sticky;
+  return device_status(s);
+}
+
+int swe_status(swe_handle *s) {
+  if (!s) return SWE_EINVAL;
+  if (s->sticky != SWE_OK) return s->sticky;
+  cudaError_t q = cudaStreamQuery(s->stream);
+  if (q == cudaErrorNotReady) return SWE_OK;
+  if (q != cudaSuccess) return cuda_check(s, q);
+  return device_status(s);
+}
+
+int swe_get_state(swe_handle *s, double *h, double *hu, double *hv) {
+  if (!s || !h || !hu || !hv) return SWE_EINVAL;
+  int rc = download_field(s, s->h[0], h);
+  if (rc == SWE_OK) rc = download_field(s, s->hu[0], hu);
+  if (rc == SWE_OK) rc = download_field(s, s->hv[0], hv);
+  if (rc == SWE_OK) rc = cuda_check(s, cudaStreamSynchronize(s->stream));
+  if (rc == SWE_OK) rc = swe_sync(s);
+  return rc;
+}
+
+int swe_get_state_device(swe_handle *s, void *h, void *hu, void *hv) {
+  if (!s || !h || !hu || !hv) return SWE_EINVAL;
+  const size_t row = s->elem * (size_t)s->nx;
+  cudaError_t e = cudaMemcpy2DAsync(h, row, s->h[0], s->elem * s->pitch, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(hu, row, s->hu[0], s->elem * s->pitch, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(hv, row, s->hv[0], s->elem * s->pitch, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_check(s, e);
+  return swe_sync(s);
+}
+
+int swe_mass(swe_handle *s, double *mass, double *clamp_mass) {
+  if (!s) return SWE_EINVAL;
+  if (s->prec == SWE_F64) k_mass_partial<double><<<kMassBlocks, 256, 0, s->stream>>>((const double *)s->h[0], s->nx, s->ny, s->pitch, s->partials);
+  else k_mass_partial<float><<<kMassBlocks, 256, 0, s->stream>>>((const float *)s->h[0], s->nx, s->ny, s->pitch, s->partials);
+  k_mass_final<<<1, 1024, 0, s->stream>>>(s->partials, kMassBlocks, s->dx * s->dy, s->partials + kMassBlocks);
+  cudaError_t e = cudaGetLastError();
+  double r[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&r[0], s->partials + kMassBlocks, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&r[1], &s->sc->clamp_mass, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_check(s, e);
+  if (mass) *mass = r[0];
+  if (clamp_mass) *clamp_mass = r[1];
+  return swe_sync(s);
+}
+
+int swe_diagnostics(swe_handle *s, swe_diag *d) {
+  if (!s || !d) return SWE_EINVAL;
+  DevScalars h;
+  cudaError_t e = cudaMemcpyAsync(&h, s->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_check(s, e);
+  auto dbl = [](unsigned long long u) { double x; std::memcpy(&x, &u, 8); return x; };
+  d->t = h.t;
+  d->steps = h.steps;
+  d->last_dt = h.dt;
+  d->alpha_x = dbl(h.alpha[0][0]);
+  d->alpha_y = dbl(h.alpha[0][1]);
+  d->clamp_mass = h.clamp_mass;
+  d->boundary_mass = h.boundary_mass;
+  const unsigned long long rn = h.runup_now[(h.steps + 1) & 1];
+  d->runup_now = rn ? dbl(rn) : -INFINITY;
+  d->runup_max = h.runup_max ? dbl(h.runup_max) : -INFINITY;
+  d->tile = s->tile;
+  d->status = SWE_OK;
+  if (h.status & ST_TIMEOUT) d->status = SWE_ETIMEOUT;
+  else if (h.status & ST_NONFINITE) d->status = SWE_ENONFINITE;
+  else if (h.status & ST_DRY) d->status = SWE_EINVAL;
+  if (s->sticky != SWE_OK) d->status = s->sticky;
+  return d->status;
+}
+
+int swe_runup(swe_handle *s, double *runup_max, double *runup_now) {
+  swe_diag d;
+  int rc = swe_diagnostics(s, &d);
+  if (!s) return SWE_EINVAL;
+  if (runup_max) *runup_max = d.runup_max;
+  if (runup_now) *runup_now = d.runup_now;
+  return rc;
+}
+
+int swe_get_time(swe_handle *s, double *t, int64_t *steps) {
+  swe_diag d;
+  int rc = swe_diagnostics(s, &d);
+  if (!s) return SWE_EINVAL;
+  if (t) *t = d.t;
+  if (steps) *steps = d.steps;
+  return rc;
+}
+
+int swe_set_time(swe_handle *s, double t) {
+  if (!s || !std::isfinite(t)) return SWE_EINVAL;
+  const long long zero = 0;
+  cudaError_t e = cudaMemcpyAsync(&s->sc->t, &t, sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&s->sc->t_step, &t, sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&s->sc->steps, &zero, sizeof(long long), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_check(s, e);
+}
+
+int swe_destroy(swe_handle *s) {
+  if (!s) return SWE_OK;
+  if (s->stream || s->mem) cudaStreamSynchronize(s->stream);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->cap) cudaStreamDestroy(s->cap);
+  if (s->mem) cudaFree(s->mem);
+  delete s;
+  return SWE_OK;
+}
+
+int swe_time_stages(swe_handle *s, int32_t n, double cfl, double *ms_total, double *ms_stage) {
+  if (!s || n <= 0) return SWE_EINVAL;
+  int rc = swe_step(s, 1, cfl);  // make sure cfl is on the device and the graph exists
+  if (rc != SWE_OK) return rc;
+  cudaEvent_t ev[4];
+  for (int k = 0; k < 4; ++k)
+    if (cudaEventCreate(&ev[k]) != cudaSuccess) return fail(s, SWE_ECUDA);
+  double acc[3] = {0, 0, 0}, tot = 0.0;
+  cudaError_t e = cudaSuccess;
+  for (int32_t it = 0; it < n && e == cudaSuccess; ++it) {
+    e = cudaEventRecord(ev[0], s->stream);
+    for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
+      if (s->prec == SWE_F64) e = launch_stage<double>(s->tile, field_of<double>(s), s->phys, s->sc, stage, s->stream);
+      else e = launch_stage<float>(s->tile, field_of<float>(s), s->phys, s->sc, stage, s->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[stage], s->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    float m;
+    for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
+      e = cudaEventElapsedTime(&m, ev[stage - 1], ev[stage]);
+      acc[stage - 1] += m;
+    }
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m, ev[0], ev[3]);
+    tot += m;
+  }
+  for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
+  if (e != cudaSuccess) return cuda_check(s, e);
+  if (ms_total) *ms_total = tot;
+  if (ms_stage)
+    for (int k = 0; k < 3; ++k) ms_stage[k] = acc[k];
+  return swe_sync(s);
+}
+
+}  // extern "C"

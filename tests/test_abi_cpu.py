@@ -1,0 +1,71 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/swe.h declares, and rejects invalid arguments before
+touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(swe_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def swe():
+    from paper_2301_12010_gb300 import _build
+    if not _build.up_to_date():
+        pytest.importorskip("shutil")
+        _build.build()
+    import paper_2301_12010_gb300 as m
+    return m
+
+
+def test_every_declared_symbol_is_exported(swe):
+    names = _declared("swe.h")
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(swe.lib, n), n
+
+
+def test_defaults_and_strerror(swe):
+    p = swe.Params()
+    swe.lib.swe_params_default(ctypes.byref(p))
+    assert p.g == 9.81 and p.h_dry == 1e-5 and p.weno_eps == 1e-6 and list(p.bc) == [0, 0, 0, 0]
+    for code in range(8):
+        assert swe.lib.swe_strerror(code)
+    assert swe.lib.swe_destroy(None) == swe.OK
+
+
+def test_invalid_arguments_rejected_without_gpu(swe):
+    p = swe.Params()
+    swe.lib.swe_params_default(ctypes.byref(p))
+    b = np.zeros((4, 4))
+    h = ctypes.c_void_p()
+    dp = b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert swe.lib.swe_create(ctypes.byref(swe.Grid(2, 4)), 1.0, 1.0, dp, ctypes.byref(p), ctypes.byref(h)) == swe.EINVAL
+    assert swe.lib.swe_create(ctypes.byref(swe.Grid(4, 4)), 0.0, 1.0, dp, ctypes.byref(p), ctypes.byref(h)) == swe.EINVAL
+    q = swe.Params.from_buffer_copy(p)
+    q.bc[1] = swe.INFLOW
+    assert swe.lib.swe_create(ctypes.byref(swe.Grid(4, 4)), 1.0, 1.0, dp, ctypes.byref(q), ctypes.byref(h)) == swe.EINVAL
+    q = swe.Params.from_buffer_copy(p)
+    q.bc[0] = swe.PERIODIC
+    assert swe.lib.swe_create(ctypes.byref(swe.Grid(4, 4)), 1.0, 1.0, dp, ctypes.byref(q), ctypes.byref(h)) == swe.EINVAL
+    q = swe.Params.from_buffer_copy(p)
+    q.precision = 7
+    assert swe.lib.swe_create(ctypes.byref(swe.Grid(4, 4)), 1.0, 1.0, dp, ctypes.byref(q), ctypes.byref(h)) == swe.EINVAL
+    assert not h.value
+    assert swe.lib.swe_step(None, 1, 0.4) == swe.EINVAL
+
+
+def test_tile_shapes(swe):
+    shapes = swe.tile_shapes()
+    assert len(shapes) >= 3
+    for tx, ty, nt in shapes:
+        assert (tx // 8) * ty == nt and (ty // 8) * tx == nt

@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Tolerances: FP64 GPU max |d eta| <= 1e-10 m; FP32 relative L2 of the surface
+anomaly eta~ (h+b on wet cells, 0 on dry) <= 1e-4 and runup error <= 1 cm.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2301_12010_gb300 as swe  # noqa: E402
+
+
+def stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def eta_tilde(h, b, h_dry=1e-5):
+    return np.where(h >= h_dry, h + b, 0.0)
+
+
+def rel_l2(a, ref):
+    return float(np.sqrt(((a - ref) ** 2).sum() / max((ref ** 2).sum(), 1e-300)))
+
+
+def run_gpu(sc, steps, precision, tile=0):
+    with swe.Solver(sc, precision=precision, stream=stream(), tile=tile) as s:
+        s.step(steps)
+        h, hu, hv = s.get_state()
+        d = s.diagnostics()
+        m = s.mass()
+    return h, hu, hv, d, m
+
+
+def run_oracle(sc, steps):
+    sim = oracle.Simulation(sc)
+    sim.step(steps)
+    return sim
+
+
+# ------------------------------------------------------------------ FP64
+@pytest.mark.parametrize("tile", [1, 2, 3])
+def test_fp64_hump_128(tile):
+    sc = W.gaussian_hump()
+    ref = run_oracle(sc, 200)
+    h, hu, hv, d, (m, cm) = run_gpu(sc, 200, swe.F64, tile)
+    assert np.abs(h - ref.h).max() <= 1e-10
+    assert np.abs(hu - ref.hu).max() <= 1e-10 and np.abs(hv - ref.hv).max() <= 1e-10
+    assert d["steps"] == 200 and d["t"] == pytest.approx(ref.t, rel=1e-12)
+    assert abs(m - ref.diag()["mass"]) <= 1e-11 * m
+
+
+@pytest.mark.parametrize("shape", [(77, 45), (3, 3), (37, 4), (130, 97)])
+@pytest.mark.parametrize("tile", [1, 2, 3])
+def test_fp64_ragged_random(shape, tile):
+    nx, ny = shape
+    rng = np.random.default_rng(nx * 1000 + ny)
+    sc = W.lake_at_rest(nx, ny, eta0=0.0, depth=4.0, rms=1.0, seed=nx + ny)
+    sc.h = sc.h + 0.2 * rng.uniform(size=sc.h.shape)
+    sc.hu = 0.3 * rng.normal(size=sc.h.shape)
+    sc.hv = 0.3 * rng.normal(size=sc.h.shape)
+    sc.manning_n = 0.03
+    ref = run_oracle(sc, 12)
+    h, hu, hv, d, _ = run_gpu(sc, 12, swe.F64, tile)
+    assert np.abs(h - ref.h).max() <= 1e-10
+    assert np.abs(hu - ref.hu).max() <= 1e-10 and np.abs(hv - ref.hv).max() <= 1e-10
+
+
+def test_fp64_wet_dry_bowl_and_clamp_mass():
+    sc = W.parabolic_bowl(nx=400, ny=8)
+    ref = run_oracle(sc, 300)
+    h, hu, hv, d, (m, cm) = run_gpu(sc, 300, swe.F64)
+    assert np.abs(h - ref.h).max() <= 1e-10
+    assert cm == pytest.approx(ref.diag()["clamp_mass"], rel=1e-9, abs=1e-12)
+
+
+def test_fp64_periodic_manning():
+    from tests.analytic import manning_normal_discharge
+    qn = manning_normal_discharge(0.5, 1 / 20, 0.033)
+    sc = W.manning_slope(nx=64, ny=8, q=0.8 * qn)
+    ref = run_oracle(sc, 300)
+    h, hu, hv, d, _ = run_gpu(sc, 300, swe.F64)
+    assert np.abs(hu - ref.hu).max() <= 1e-10 and np.abs(h - ref.h).max() <= 1e-10
+
+
+def test_fp64_inflow_and_boundary_mass():
+    sc = W.coastal_dem(n=96, dx=150.0, t0=500.0)
+    ref = run_oracle(sc, 40)
+    h, hu, hv, d, (m, cm) = run_gpu(sc, 40, swe.F64)
+    assert np.abs(h - ref.h).max() <= 1e-10
+    rd = ref.diag()
+    assert d["boundary_mass"] == pytest.approx(rd["boundary_mass"], rel=1e-9)
+    assert d["t"] == pytest.approx(rd["t"], rel=1e-13)
+
+
+def test_fp64_planar_beach_full_5000_steps():
+    # 2048 x 64 on the GPU; the y-uniform problem is row-for-row the same as
+    # the oracle's 2048 x 4 run (walls in y keep it exactly one-dimensional)
+    sc = W.planar_beach()
+    sc4 = W.planar_beach(ny=4)
+    ref = run_oracle(sc4, 5000)
+    h, hu, hv, d, _ = run_gpu(sc, 5000, swe.F64)
+    eta_ref = ref.h[0] + sc4.b[0]
+    assert np.abs(h + sc.b - eta_ref[None, :]).max() <= 1e-10
+    assert d["runup_max"] == pytest.approx(ref.diag()["runup_max"], abs=1e-10)
+
+
+# ------------------------------------------------------------------ FP32
+def test_fp32_hump_128():
+    sc = W.gaussian_hump()
+    ref = run_oracle(sc, 200)
+    h, hu, hv, d, _ = run_gpu(sc, 200, swe.F32)
+    e = rel_l2(eta_tilde(h, sc.b) - 0.0, eta_tilde(ref.h, sc.b))
+    assert e <= 1e-4
+
+
+def test_fp32_planar_beach_against_fp64_oracle():
+    sc = W.planar_beach()
+    sc4 = W.planar_beach(ny=4)
+    ref = oracle.Simulation(sc4)
+    with swe.Solver(sc, precision=swe.F32, stream=stream()) as s:
+        for target in (5000, 8000):  # 8000 steps covers the maximum runup
+            ref.step(target - ref.diag()["steps"])
+            s.step(target - s.diagnostics()["steps"])
+            h, hu, hv = s.get_state()
+            d = s.diagnostics()
+            et = eta_tilde(h, sc.b)
+            er = eta_tilde(ref.h, sc4.b)[0][None, :].repeat(sc.ny, axis=0)
+            assert rel_l2(et, er) <= 1e-4, target
+            assert abs(d["runup_max"] - ref.diag()["runup_max"]) <= 0.01, target
+
+
+def test_fp32_lake_at_rest_with_islands():
+    sc = W.lake_at_rest(96, 64, eta0=0.5, depth=10.0, rms=2.0, islands=True)
+    h, hu, hv, d, _ = run_gpu(sc, 500, swe.F32)
+    wet = sc.h > 0
+    assert np.abs((h + sc.b - 0.5)[wet]).max() <= 1e-5
+    assert np.abs(hu).max() <= 1e-4 and np.abs(hv).max() <= 1e-4
+
+
+def test_fp32_coastal_dem_full_size_two_steps():
+    sc = W.coastal_dem()
+    ref = run_oracle(sc, 2)
+    h, hu, hv, d, _ = run_gpu(sc, 2, swe.F32)
+    e = rel_l2(eta_tilde(h, sc.b), eta_tilde(ref.h, sc.b))
+    assert e <= 1e-4, e
+
+
+# ------------------------------------------------------------- edge cases
+def test_dry_still_domain_reports_einval():
+    sc = W.lake_at_rest(16, 16, eta0=-100.0, depth=10.0, rms=1.0)
+    assert sc.h.max() == 0.0
+    with swe.Solver(sc, precision=swe.F32, stream=stream()) as s:
+        s.step(1)
+        with pytest.raises(swe.SweError) as ei:
+            s.sync()
+        assert ei.value.code == swe.EINVAL
+
+
+def test_nonfinite_state_is_reported():
+    sc = W.gaussian_hump(n=32)
+    sc.h[5, 7] = np.nan
+    with swe.Solver(sc, precision=swe.F32, stream=stream()) as s:
+        with pytest.raises(swe.SweError) as ei:
+            s.step(2)
+            s.sync()
+        assert ei.value.code == swe.ENONFINITE
+
+
+def test_checkpoint_resume_is_bitwise():
+    sc = W.planar_beach(nx=256, ny=8, steps=0)
+    sc.manning_n = 0.025
+    with swe.Solver(sc, precision=swe.F32, stream=stream()) as a:
+        a.step(60)
+        ha, hua, hva = a.get_state()
+        ta, _ = a.time()
+    with swe.Solver(sc, precision=swe.F32, stream=stream()) as b:
+        b.step(25)
+        st = b.get_state()
+        t1, _ = b.time()
+    sc2 = sc.copy(h=st[0], hu=st[1], hv=st[2], t0=t1)
+    with swe.Solver(sc2, precision=swe.F32, stream=stream()) as c:
+        c.step(35)
+        hc, huc, hvc = c.get_state()
+        tc, _ = c.time()
+    assert np.array_equal(ha, hc) and np.array_equal(hua, huc) and np.array_equal(hva, hvc)
+    assert ta == tc
