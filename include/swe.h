@@ -101,8 +101,8 @@ void swe_params_default(swe_params *p);
 
 /* Create a solver for grid *grid with spacings dx, dy (m) over the host FP64
  * bathymetry b[ny][nx] (m, positive up).  Allocates all device memory the
- * stepping needs; no later call allocates.  The state is zero until
- * swe_set_state.  *out receives the handle, or NULL on error. */
+ * stepping needs; no later call allocates.  Until swe_set_state the state is
+ * still water at z_ref.  *out receives the handle, or NULL on error. */
 int swe_create(const swe_grid *grid, double dx, double dy, const double *bathymetry,
                const swe_params *params, swe_handle **out);
 

@@ -15,21 +15,30 @@ using namespace swe;
 namespace {
 
 // ---------------------------------------------------------------- kernels
-template <typename T>
-__global__ void k_from_f64(const double *__restrict__ src, T *__restrict__ dst, int nx, int ny, int pitch) {
+// Host-format FP64 [ny][nx] -> pitched planes.  With bed != nullptr the
+// field is a depth h stored as the anomaly ha = h - max(z_ref - b, 0).
+template <typename T, typename S>
+__global__ void k_import(const S *__restrict__ src, T *__restrict__ dst, const T *__restrict__ bed, double zref,
+                         int nx, int ny, int pitch) {
   const size_t n = (size_t)nx * ny;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
     const size_t j = q / nx, i = q - j * nx;
-    dst[j * pitch + i] = (T)src[q];
+    double v = (double)src[q];
+    if (bed) v -= fmax(zref - (double)bed[j * pitch + i], 0.0);
+    dst[j * pitch + i] = (T)v;
   }
 }
 
-template <typename T>
-__global__ void k_to_f64(const T *__restrict__ src, double *__restrict__ dst, int nx, int ny, int pitch) {
+// Pitched planes -> contiguous [ny][nx]; with bed != nullptr, h = ha + d.
+template <typename T, typename S>
+__global__ void k_export(const T *__restrict__ src, S *__restrict__ dst, const T *__restrict__ bed, double zref,
+                         int nx, int ny, int pitch) {
   const size_t n = (size_t)nx * ny;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
     const size_t j = q / nx, i = q - j * nx;
-    dst[q] = (double)src[j * pitch + i];
+    double v = (double)src[j * pitch + i];
+    if (bed) v += fmax(zref - (double)bed[j * pitch + i], 0.0);
+    dst[q] = (S)v;
   }
 }
 
@@ -73,7 +82,8 @@ __global__ void k_state_stats(Field<T> fd, Phys p, DevScalars *sc) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
     const size_t j = q / fd.nx, i = q - j * fd.nx;
     const size_t o = j * fd.pitch + i;
-    const T h = fd.h[0][o], hu = fd.hu[0][o], hv = fd.hv[0][o];
+    const T b = fd.b[o];
+    const T h = fd.h[0][o] + still_depth(b, T(p.z_ref)), hu = fd.hu[0][o], hv = fd.hv[0][o];
     if (!(fabs(h) <= T(3.0e38)) || !(fabs(hu) <= T(3.0e38)) || !(fabs(hv) <= T(3.0e38))) { bad = true; continue; }
     T u = T(0), v = T(0);
     if (!Num<T>::below(h, p.h_dry32, p.h_dry)) { const T rr = Num<T>::rcp(h); u = hu * rr; v = hv * rr; }
@@ -81,7 +91,6 @@ __global__ void k_state_stats(Field<T> fd, Phys p, DevScalars *sc) {
     const T sx = fabs(u) + cel, sy = fabs(v) + cel;
     mx = sx > mx ? sx : mx;
     my = sy > my ? sy : my;
-    const T b = fd.b[o];
     if (!Num<T>::below(h, p.h_wet32, p.h_wet) && b > T(0)) { const T e = h + b; ru = e > ru ? e : ru; }
   }
   mx = warp_max(mx);
@@ -113,7 +122,8 @@ __global__ void k_state_stats(Field<T> fd, Phys p, DevScalars *sc) {
 
 // Mass, pass 1: per-block FP64 partial sums of h over rows, fixed order.
 template <typename T>
-__global__ void k_mass_partial(const T *__restrict__ h, int nx, int ny, int pitch, double *__restrict__ part) {
+__global__ void k_mass_partial(const T *__restrict__ ha, const T *__restrict__ bed, double zref, int nx, int ny,
+                               int pitch, double *__restrict__ part) {
   __shared__ double sm[32];
   double s = 0.0;
   const size_t n = (size_t)nx * ny;
@@ -121,7 +131,8 @@ __global__ void k_mass_partial(const T *__restrict__ h, int nx, int ny, int pitc
   const size_t lo = blockIdx.x * per, hi = lo + per < n ? lo + per : n;
   for (size_t q = lo + threadIdx.x; q < hi; q += blockDim.x) {
     const size_t j = q / nx, i = q - j * nx;
-    s += (double)h[j * pitch + i];
+    const size_t o = j * pitch + i;
+    s += (double)ha[o] + fmax(zref - (double)bed[o], 0.0);
   }
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
@@ -235,23 +246,52 @@ int device_status(swe_handle *s) {
   return SWE_OK;
 }
 
-int upload_field(swe_handle *s, const double *src, void *dst) {
+// Host FP64 [ny][nx] -> device plane; depth fields (is_depth) are stored as
+// the anomaly ha (the bed must already be on the device).
+int upload_field(swe_handle *s, const double *src, void *dst, bool is_depth) {
   cudaError_t e = cudaMemcpyAsync(s->staging, src, sizeof(double) * (size_t)s->nx * s->ny, cudaMemcpyHostToDevice,
                                   s->stream);
   if (e != cudaSuccess) return cuda_check(s, e);
   const size_t n = (size_t)s->nx * s->ny;
-  if (s->prec == SWE_F64) k_from_f64<double><<<grid_blocks(n, 256), 256, 0, s->stream>>>(s->staging, (double *)dst, s->nx, s->ny, s->pitch);
-  else k_from_f64<float><<<grid_blocks(n, 256), 256, 0, s->stream>>>(s->staging, (float *)dst, s->nx, s->ny, s->pitch);
+  const int nb = grid_blocks(n, 256);
+  if (s->prec == SWE_F64)
+    k_import<double, double><<<nb, 256, 0, s->stream>>>(s->staging, (double *)dst, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
+  else
+    k_import<float, double><<<nb, 256, 0, s->stream>>>(s->staging, (float *)dst, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
   return cuda_check(s, cudaGetLastError());
 }
 
-int download_field(swe_handle *s, const void *src, double *dst) {
+int download_field(swe_handle *s, const void *src, double *dst, bool is_depth) {
   const size_t n = (size_t)s->nx * s->ny;
-  if (s->prec == SWE_F64) k_to_f64<double><<<grid_blocks(n, 256), 256, 0, s->stream>>>((const double *)src, s->staging, s->nx, s->ny, s->pitch);
-  else k_to_f64<float><<<grid_blocks(n, 256), 256, 0, s->stream>>>((const float *)src, s->staging, s->nx, s->ny, s->pitch);
+  const int nb = grid_blocks(n, 256);
+  if (s->prec == SWE_F64)
+    k_export<double, double><<<nb, 256, 0, s->stream>>>((const double *)src, s->staging, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
+  else
+    k_export<float, double><<<nb, 256, 0, s->stream>>>((const float *)src, s->staging, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(dst, s->staging, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream);
   return cuda_check(s, e);
+}
+
+// Caller device arrays (handle precision, contiguous) <-> planes.
+int import_device(swe_handle *s, const void *src, void *dst, bool is_depth) {
+  const size_t n = (size_t)s->nx * s->ny;
+  const int nb = grid_blocks(n, 256);
+  if (s->prec == SWE_F64)
+    k_import<double, double><<<nb, 256, 0, s->stream>>>((const double *)src, (double *)dst, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
+  else
+    k_import<float, float><<<nb, 256, 0, s->stream>>>((const float *)src, (float *)dst, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
+  return cuda_check(s, cudaGetLastError());
+}
+
+int export_device(swe_handle *s, const void *src, void *dst, bool is_depth) {
+  const size_t n = (size_t)s->nx * s->ny;
+  const int nb = grid_blocks(n, 256);
+  if (s->prec == SWE_F64)
+    k_export<double, double><<<nb, 256, 0, s->stream>>>((const double *)src, (double *)dst, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
+  else
+    k_export<float, float><<<nb, 256, 0, s->stream>>>((const float *)src, (float *)dst, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
+  return cuda_check(s, cudaGetLastError());
 }
 
 int after_state_change(swe_handle *s) {
@@ -404,7 +444,7 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
     k_reset<<<1, 32, 0, s->stream>>>(s->sc, 0.0, 0.4, 0.0);
     rc = cuda_check(s, cudaGetLastError());
   }
-  if (rc == SWE_OK) rc = upload_field(s, bathymetry, s->b);
+  if (rc == SWE_OK) rc = upload_field(s, bathymetry, s->b, false);
   if (rc == SWE_OK) rc = cuda_check(s, cudaStreamSynchronize(s->stream));
   if (rc != SWE_OK) {
     swe_destroy(s);
@@ -417,20 +457,19 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
 
 int swe_set_state(swe_handle *s, const double *h, const double *hu, const double *hv) {
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
-  int rc = upload_field(s, h, s->h[0]);
-  if (rc == SWE_OK) rc = upload_field(s, hu, s->hu[0]);
-  if (rc == SWE_OK) rc = upload_field(s, hv, s->hv[0]);
+  int rc = upload_field(s, h, s->h[0], true);
+  if (rc == SWE_OK) rc = upload_field(s, hu, s->hu[0], false);
+  if (rc == SWE_OK) rc = upload_field(s, hv, s->hv[0], false);
   if (rc == SWE_OK) rc = after_state_change(s);
   return rc;
 }
 
 int swe_set_state_device(swe_handle *s, const void *h, const void *hu, const void *hv) {
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
-  const size_t row = s->elem * (size_t)s->nx;
-  cudaError_t e = cudaMemcpy2DAsync(s->h[0], s->elem * s->pitch, h, row, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
-  if (e == cudaSuccess) e = cudaMemcpy2DAsync(s->hu[0], s->elem * s->pitch, hu, row, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
-  if (e == cudaSuccess) e = cudaMemcpy2DAsync(s->hv[0], s->elem * s->pitch, hv, row, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
-  if (e != cudaSuccess) return cuda_check(s, e);
+  int rc = import_device(s, h, s->h[0], true);
+  if (rc == SWE_OK) rc = import_device(s, hu, s->hu[0], false);
+  if (rc == SWE_OK) rc = import_device(s, hv, s->hv[0], false);
+  if (rc != SWE_OK) return rc;
   return after_state_change(s);
 }
 
@@ -482,9 +521,9 @@ int swe_status(swe_handle *s) {
 
 int swe_get_state(swe_handle *s, double *h, double *hu, double *hv) {
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
-  int rc = download_field(s, s->h[0], h);
-  if (rc == SWE_OK) rc = download_field(s, s->hu[0], hu);
-  if (rc == SWE_OK) rc = download_field(s, s->hv[0], hv);
+  int rc = download_field(s, s->h[0], h, true);
+  if (rc == SWE_OK) rc = download_field(s, s->hu[0], hu, false);
+  if (rc == SWE_OK) rc = download_field(s, s->hv[0], hv, false);
   if (rc == SWE_OK) rc = cuda_check(s, cudaStreamSynchronize(s->stream));
   if (rc == SWE_OK) rc = swe_sync(s);
   return rc;
@@ -492,19 +531,20 @@ int swe_get_state(swe_handle *s, double *h, double *hu, double *hv) {
 
 int swe_get_state_device(swe_handle *s, void *h, void *hu, void *hv) {
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
-  const size_t row = s->elem * (size_t)s->nx;
-  cudaError_t e = cudaMemcpy2DAsync(h, row, s->h[0], s->elem * s->pitch, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
-  if (e == cudaSuccess) e = cudaMemcpy2DAsync(hu, row, s->hu[0], s->elem * s->pitch, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
-  if (e == cudaSuccess) e = cudaMemcpy2DAsync(hv, row, s->hv[0], s->elem * s->pitch, row, s->ny, cudaMemcpyDeviceToDevice, s->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  if (e != cudaSuccess) return cuda_check(s, e);
+  int rc = export_device(s, s->h[0], h, true);
+  if (rc == SWE_OK) rc = export_device(s, s->hu[0], hu, false);
+  if (rc == SWE_OK) rc = export_device(s, s->hv[0], hv, false);
+  if (rc == SWE_OK) rc = cuda_check(s, cudaStreamSynchronize(s->stream));
+  if (rc != SWE_OK) return rc;
   return swe_sync(s);
 }
 
 int swe_mass(swe_handle *s, double *mass, double *clamp_mass) {
   if (!s) return SWE_EINVAL;
-  if (s->prec == SWE_F64) k_mass_partial<double><<<kMassBlocks, 256, 0, s->stream>>>((const double *)s->h[0], s->nx, s->ny, s->pitch, s->partials);
-  else k_mass_partial<float><<<kMassBlocks, 256, 0, s->stream>>>((const float *)s->h[0], s->nx, s->ny, s->pitch, s->partials);
+  if (s->prec == SWE_F64)
+    k_mass_partial<double><<<kMassBlocks, 256, 0, s->stream>>>((const double *)s->h[0], (const double *)s->b, s->phys.z_ref, s->nx, s->ny, s->pitch, s->partials);
+  else
+    k_mass_partial<float><<<kMassBlocks, 256, 0, s->stream>>>((const float *)s->h[0], (const float *)s->b, s->phys.z_ref, s->nx, s->ny, s->pitch, s->partials);
   k_mass_final<<<1, 1024, 0, s->stream>>>(s->partials, kMassBlocks, s->dx * s->dy, s->partials + kMassBlocks);
   cudaError_t e = cudaGetLastError();
   double r[2] = {0, 0};

@@ -20,9 +20,16 @@
 //   still-water depth d = max(z_ref - b, 0): pressure g (h^2 - d^2)/2, source
 //   -g (h - d) db/dx, mass viscosity on h - d.
 //
+// Storage: the depth is held as the still-water anomaly ha = h - d (= h + b -
+// z_ref at sea, = h on land), a change of variables that is exact in real
+// arithmetic and keeps full FP32 precision both for small waves over deep
+// water and for thin films on land; d is recomputed from b.  The RK
+// combinations are written in increment form U0 + w (U' - U0), whose weights
+// sum to one exactly in any precision.
+//
 // Shared-memory plan (per CTA): the bed over the halo box, one split-flux
 // buffer reused by the x pass and then the y pass, the x-pass result L_x, and
-// the surface anomaly h - d of the tile's own cells.
+// the anomaly ha of the tile's own cells.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -64,7 +71,7 @@ struct Phys {
 template <typename T>
 struct Field {
   const T *b;
-  T *h[3], *hu[3], *hv[3];  // planes of U^n, U1, U2
+  T *h[3], *hu[3], *hv[3];  // planes of U^n, U1, U2; h[] holds ha = h - d
   int nx, ny, pitch;
 };
 
@@ -145,64 +152,76 @@ __device__ __forceinline__ double inflow_eta(const Phys &p, double t) {
   return 2.0 * (a1 * exp(-k1 * q1 * q1) - a2 * exp(-k2 * q2 * q2));
 }
 
-// State of cell (i, j), where (i, j) may lie up to 3 cells outside the
-// interior in at most one direction (ghosts per boundary type).
-template <typename T>
-__device__ __forceinline__ void load_cell(const T *__restrict__ b, const T *__restrict__ h,
-                                          const T *__restrict__ hu, const T *__restrict__ hv, int nx, int ny,
-                                          int pitch, const Phys &p, T eta_in, T u_in, int i, int j, T &ch,
-                                          T &chu, T &chv, T &cb) {
-  int si = i, sj = j;
-  bool fu = false, fv = false, inflow = false;
-  T bshift = T(0);
-  if (i < 0) {
-    if (p.bc[0] == BC_PERIODIC) { si = i + nx; bshift = T(-p.b_jump_x); }
-    else { si = -1 - i; fu = true; inflow = (p.bc[0] == BC_INFLOW); }
-  } else if (i >= nx) {
-    if (p.bc[1] == BC_PERIODIC) { si = i - nx; bshift = T(p.b_jump_x); }
-    else { si = 2 * nx - 1 - i; fu = true; }
-  }
-  if (j < 0) {
-    if (p.bc[2] == BC_PERIODIC) { sj = j + ny; bshift = T(-p.b_jump_y); }
-    else { sj = -1 - j; fv = true; }
-  } else if (j >= ny) {
-    if (p.bc[3] == BC_PERIODIC) { sj = j - ny; bshift = T(p.b_jump_y); }
-    else { sj = 2 * ny - 1 - j; fv = true; }
-  }
-  const size_t o = (size_t)sj * pitch + si;
-  cb = b[o] + bshift;
-  if (inflow) {
-    T hg = eta_in - cb;
-    ch = hg > T(0) ? hg : T(0);
-    chu = ch * u_in;
-    chv = T(0);
-  } else {
-    ch = h[o];
-    chu = hu[o];
-    chv = hv[o];
-    if (fu) chu = -chu;
-    if (fv) chv = -chv;
-  }
-}
-
 template <typename T>
 __device__ __forceinline__ T still_depth(T b, T zref) {
   T d = zref - b;
   return d > T(0) ? d : T(0);
 }
 
-// Split fluxes of one cell along direction DIR (0: x with F, 1: y with G).
+// State (ha, hu, hv) and bed of cell (i, j), where (i, j) may lie up to 3
+// cells outside the interior in at most one direction (ghosts per boundary
+// type: mirrored walls, the inflow wave, or periodic wrap with bed offset).
+template <typename T>
+__device__ __forceinline__ void load_cell(const T *__restrict__ b, const T *__restrict__ ha,
+                                          const T *__restrict__ hu, const T *__restrict__ hv, int nx, int ny,
+                                          int pitch, const Phys &p, T zref, T eta_in, T u_in, int i, int j, T &ch,
+                                          T &chu, T &chv, T &cb) {
+  int si = i, sj = j;
+  bool fu = false, fv = false, inflow = false, seam = false;
+  T bshift = T(0);
+  if (i < 0) {
+    if (p.bc[0] == BC_PERIODIC) { si = i + nx; bshift = T(-p.b_jump_x); seam = true; }
+    else { si = -1 - i; fu = true; inflow = (p.bc[0] == BC_INFLOW); }
+  } else if (i >= nx) {
+    if (p.bc[1] == BC_PERIODIC) { si = i - nx; bshift = T(p.b_jump_x); seam = true; }
+    else { si = 2 * nx - 1 - i; fu = true; }
+  }
+  if (j < 0) {
+    if (p.bc[2] == BC_PERIODIC) { sj = j + ny; bshift = T(-p.b_jump_y); seam = true; }
+    else { sj = -1 - j; fv = true; }
+  } else if (j >= ny) {
+    if (p.bc[3] == BC_PERIODIC) { sj = j - ny; bshift = T(p.b_jump_y); seam = true; }
+    else { sj = 2 * ny - 1 - j; fv = true; }
+  }
+  const size_t o = (size_t)sj * pitch + si;
+  const T bs = b[o];
+  cb = bs + bshift;
+  if (inflow) {
+    // h = max(eta_in - b, 0), u = eta_in sqrt(g/d0), v = 0; in anomaly form
+    const T dg = still_depth(cb, zref);
+    if (cb < zref) {
+      const T a = eta_in - zref;
+      ch = a > -dg ? a : -dg;
+    } else {
+      const T hg = eta_in - cb;
+      ch = hg > T(0) ? hg : T(0);
+    }
+    chu = (ch + dg) * u_in;
+    chv = T(0);
+  } else {
+    ch = ha[o];
+    chu = hu[o];
+    chv = hv[o];
+    if (seam) ch = (ch + still_depth(bs, zref)) - still_depth(cb, zref);  // same h, new d
+    if (fu) chu = -chu;
+    if (fv) chv = -chv;
+  }
+}
+
+// Split fluxes of one cell along direction DIR (0: x with F, 1: y with G)
+// from the anomaly form: h = ha + d, pressure g ha (h + d)/2 = g (h^2-d^2)/2,
+// Q = (ha, hu, hv).
 template <typename T, int DIR>
-__device__ __forceinline__ void split_cell(T h, T hu, T hv, T b, T alpha, T g, T zref, const Phys &p, T fp[3],
+__device__ __forceinline__ void split_cell(T ha, T hu, T hv, T b, T alpha, T g, T zref, const Phys &p, T fp[3],
                                            T fm[3]) {
+  const T d = still_depth(b, zref);
+  const T h = ha + d;
   T u = T(0), v = T(0);
   if (!Num<T>::below(h, p.h_dry32, p.h_dry)) {
     const T r = Num<T>::rcp(h);
     u = hu * r;
     v = hv * r;
   }
-  const T d = still_depth(b, zref);
-  const T ha = h - d;
   const T pres = T(0.5) * g * ha * (h + d);
   T F0, F1, F2;
   if (DIR == 0) { F0 = hu; F1 = hu * u + pres; F2 = hv * u; }
@@ -336,7 +355,7 @@ __device__ void stage_tile(const Field<T> &fd, const Phys &p, DevScalars *sc, in
 
   T *sb = smem;               // bed over the halo box
   T *spl = sb + G::NB;        // 6 split components
-  T *sha = spl + 6 * G::SPL;  // h - d of own cells
+  T *sha = spl + 6 * G::SPL;  // ha of own cells
   T *sL = sha + G::NC;        // L_x, 3 components
 
   // ---- stage scalars and the skip decision (uniform over the CTA)
@@ -389,7 +408,7 @@ __device__ void stage_tile(const Field<T> &fd, const Phys &p, DevScalars *sc, in
   const T g = T(p.g), zref = T(p.z_ref), eps12 = T(12.0 * p.weno_eps);
   const T alx = T(ax), aly = T(ay);
 
-  // ---- phase A: bed box, x-split fluxes (own rows, halo columns), h - d
+  // ---- phase A: bed box, x-split fluxes (own rows, halo columns), ha of own cells
   for (int idx = tid; idx < G::NB; idx += NT) {
     const int r = idx / G::BW, c = idx - r * G::BW;
     const int i = i0 - 3 + c, j = j0 - 3 + r;
@@ -399,7 +418,7 @@ __device__ void stage_tile(const Field<T> &fd, const Phys &p, DevScalars *sc, in
     T cb = T(0);
     if ((ix && yin) || (jy && xin)) {
       T ch, chu, chv;
-      load_cell<T>(bb, hin, huin, hvin, nx, ny, pitch, p, eta_in, u_in, i, j, ch, chu, chv, cb);
+      load_cell<T>(bb, hin, huin, hvin, nx, ny, pitch, p, zref, eta_in, u_in, i, j, ch, chu, chv, cb);
       if (own_row) {
         T fp[3], fm[3];
         if (jy) split_cell<T, 0>(ch, chu, chv, cb, alx, g, zref, p, fp, fm);
@@ -407,7 +426,7 @@ __device__ void stage_tile(const Field<T> &fd, const Phys &p, DevScalars *sc, in
         const int o = (r - 3) * G::XP + c;
 #pragma unroll
         for (int m = 0; m < 3; ++m) { spl[m * G::SPL + o] = fp[m]; spl[(3 + m) * G::SPL + o] = fm[m]; }
-        if (c >= 3 && c < TX + 3) sha[(r - 3) * TX + (c - 3)] = ch - still_depth(cb, zref);
+        if (c >= 3 && c < TX + 3) sha[(r - 3) * TX + (c - 3)] = ch;
       }
     } else if (own_row) {
       const int o = (r - 3) * G::XP + c;
@@ -456,7 +475,7 @@ __device__ void stage_tile(const Field<T> &fd, const Phys &p, DevScalars *sc, in
     T fp[3], fm[3];
     if (i < nx && j >= -3 && j < ny + 3) {
       T ch, chu, chv, cb;
-      load_cell<T>(bb, hin, huin, hvin, nx, ny, pitch, p, eta_in, u_in, i, j, ch, chu, chv, cb);
+      load_cell<T>(bb, hin, huin, hvin, nx, ny, pitch, p, zref, eta_in, u_in, i, j, ch, chu, chv, cb);
       split_cell<T, 1>(ch, chu, chv, cb, aly, g, zref, p, fp, fm);
     } else {
       fp[0] = fp[1] = fp[2] = fm[0] = fm[1] = fm[2] = T(0);
@@ -497,7 +516,10 @@ __device__ void stage_tile(const Field<T> &fd, const Phys &p, DevScalars *sc, in
       if (i < nx && j < ny) {
         const int o = (r0 + k) * TX + c;
         const size_t go = (size_t)j * pitch + i;
-        const T h = hin[go], hu = huin[go], hv = hvin[go];
+        const T ha = hin[go], hu = huin[go], hv = hvin[go];
+        const T bc = bb[go];
+        const T d = still_depth(bc, zref);
+        const T h = ha + d;
         T Lh = sL[o] - dG[0][k] * inv6dy;
         T Lhu = sL[G::NC + o] - dG[1][k] * inv6dy;
         T Lhv = sL[2 * G::NC + o] - dG[2][k] * inv6dy - g12dy * sha[o] * db[k];
@@ -508,29 +530,22 @@ __device__ void stage_tile(const Field<T> &fd, const Phys &p, DevScalars *sc, in
           Lhu -= kap * hu;
           Lhv -= kap * hv;
         }
-        T nh, nhu, nhv;
-        if (STAGE == 1) {
-          nh = h + tdt * Lh;
-          nhu = hu + tdt * Lhu;
-          nhv = hv + tdt * Lhv;
-        } else {
-          const T h0 = fd.h[0][go], hu0 = fd.hu[0][go], hv0 = fd.hv[0][go];
-          if (STAGE == 2) {
-            nh = T(0.75) * h0 + T(0.25) * (h + tdt * Lh);
-            nhu = T(0.75) * hu0 + T(0.25) * (hu + tdt * Lhu);
-            nhv = T(0.75) * hv0 + T(0.25) * (hv + tdt * Lhv);
-          } else {
-            nh = h0 / T(3) + T(2.0 / 3.0) * (h + tdt * Lh);
-            nhu = hu0 / T(3) + T(2.0 / 3.0) * (hu + tdt * Lhu);
-            nhv = hv0 / T(3) + T(2.0 / 3.0) * (hv + tdt * Lhv);
-          }
+        // RK combination in increment form: U0 + w (U + dt L - U0)
+        T nha = ha + tdt * Lh, nhu = hu + tdt * Lhu, nhv = hv + tdt * Lhv;
+        if (STAGE != 1) {
+          const T w = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
+          const T ha0 = fd.h[0][go], hu0 = fd.hu[0][go], hv0 = fd.hv[0][go];
+          nha = ha0 + w * (nha - ha0);
+          nhu = hu0 + w * (nhu - hu0);
+          nhv = hv0 + w * (nhv - hv0);
         }
         // post-stage rule: clamp negative depth (counted), dry cells at rest
-        if (nh < T(0)) { deficit -= (double)nh; nh = T(0); }
+        if (nha < -d) { deficit -= (double)(nha + d); nha = -d; }
+        const T nh = nha + d;
         T u = T(0), v = T(0);
         if (Num<T>::below(nh, p.h_dry32, p.h_dry)) { nhu = T(0); nhv = T(0); }
         else { const T rr = Num<T>::rcp(nh); u = nhu * rr; v = nhv * rr; }
-        fd.h[OUTB][go] = nh;
+        fd.h[OUTB][go] = nha;
         fd.hu[OUTB][go] = nhu;
         fd.hv[OUTB][go] = nhv;
         const T cel = Num<T>::sqrt_(g * nh);
@@ -539,8 +554,8 @@ __device__ void stage_tile(const Field<T> &fd, const Phys &p, DevScalars *sc, in
           bad = true;
         amax_x = sx > amax_x ? sx : amax_x;
         amax_y = sy > amax_y ? sy : amax_y;
-        if (STAGE == 3 && !Num<T>::below(nh, p.h_wet32, p.h_wet) && bb[go] > T(0)) {
-          const T e = nh + bb[go];
+        if (STAGE == 3 && !Num<T>::below(nh, p.h_wet32, p.h_wet) && bc > T(0)) {
+          const T e = nh + bc;
           runup = e > runup ? e : runup;
         }
       }

@@ -19,10 +19,10 @@ def _declared(header):
 
 @pytest.fixture(scope="module")
 def swe():
-    from paper_2301_12010_gb300 import _build
-    if not _build.up_to_date():
-        pytest.importorskip("shutil")
-        _build.build()
+    import __graft_entry__
+    b = __graft_entry__._build_module()
+    if not b.up_to_date():
+        b.build()
     import paper_2301_12010_gb300 as m
     return m
 
