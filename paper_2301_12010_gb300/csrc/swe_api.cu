@@ -434,7 +434,18 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   s->partials = (double *)q;
 
   int rc = SWE_OK;
-  if (cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) rc = SWE_ECUDA;
+  {
+    // the tile shape must fit in the opt-in shared memory of this device
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      (void)cudaGetLastError();
+      rc = SWE_ECUDA;
+    } else if (shape_smem(s->tile, (int)s->elem) + sizeof(RedSmem) > (size_t)optin) {
+      rc = SWE_EINVAL;
+    }
+  }
+  if (rc == SWE_OK && cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) rc = SWE_ECUDA;
   if (rc == SWE_OK) {
     e = s->prec == SWE_F64 ? prepare_shape<double>(s->tile) : prepare_shape<float>(s->tile);
     rc = cuda_check(s, e);

@@ -232,60 +232,6 @@ __device__ __forceinline__ void split_cell(T ha, T hu, T hv, T b, T alpha, T g, 
   fp[2] = T(0.5) * (F2 + q2); fm[2] = T(0.5) * (F2 - q2);
 }
 
-// Strip of S cells along a line: faces k = 0..S lie at the left of cell
-// c0+k (face c0+k-1/2).  sp points at the f+ value of component 0 for the
-// cell c0-3; cells along the line are `st` apart, components `cs` apart and
-// f- sits `pm` after f+.  bl points at b of cell c0-3 (stride bst).
-// For each cell k of the strip: dF[m][k] = 6*(Fhat_{k+1/2} - Fhat_{k-1/2}),
-// db[k] = 6*(bhat_{k+1/2} - bhat_{k-1/2}) * 2 (bhat of b/2, scaled), and the
-// first/last face values of component 0 (edge mass flux).
-template <typename T, int S, int MOM>
-__device__ __forceinline__ void sweep_strip(const T *__restrict__ sp, int st, int cs, int pm,
-                                            const T *__restrict__ bl, int bst, T eps12, T dF[3][S], T db[S],
-                                            T Fface0[S + 1]) {
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    const T *fpp = sp + m * cs;
-    const T *fmm = fpp + pm;
-    T wp[6], wm[6], wb[6];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      wp[q] = fpp[q * st];
-      wm[q] = fmm[q * st];
-      if (m == MOM) wb[q] = bl[q * bst];
-    }
-    T prevF = T(0), prevB = T(0);
-#pragma unroll
-    for (int k = 0; k <= S; ++k) {
-      // window: cells c0-3+k .. c0+2+k at wp[0..5]
-      wp[5] = fpp[(k + 5) * st];
-      wm[5] = fmm[(k + 5) * st];
-      if (m == MOM) wb[5] = bl[(k + 5) * bst];
-      T a0, a1, a2, rp, c0, c1, c2, rm;
-      const T Fp = weno5x6<T>(wp[0], wp[1], wp[2], wp[3], wp[4], eps12, a0, a1, a2, rp);
-      const T Fm = weno5x6<T>(wm[5], wm[4], wm[3], wm[2], wm[1], eps12, c0, c1, c2, rm);
-      const T F = Fp + Fm;
-      T B = T(0);
-      if (m == MOM)
-        B = weighted6<T>(wb[0], wb[1], wb[2], wb[3], wb[4], a0, a1, a2, rp) +
-            weighted6<T>(wb[5], wb[4], wb[3], wb[2], wb[1], c0, c1, c2, rm);
-      if (m == 0) Fface0[k] = F;
-      if (k > 0) {
-        dF[m][k - 1] = F - prevF;
-        if (m == MOM) db[k - 1] = B - prevB;
-      }
-      prevF = F;
-      prevB = B;
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        wp[q] = wp[q + 1];
-        wm[q] = wm[q + 1];
-        if (m == MOM) wb[q] = wb[q + 1];
-      }
-    }
-  }
-}
-
 template <typename T> __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -300,18 +246,30 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Shared-memory footprint of one tile (elements of T).
-template <int TX, int TY>
+// ------------------------------------------------------- asynchronous copies
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Shared-memory geometry of one tile.
+template <typename T, int TX, int TY>
 struct TileGeom {
-  static constexpr int BW = TX + 6;                    // halo box width
-  static constexpr int BH = TY + 6;                    // halo box height
-  static constexpr int XP = ((TX + 6 + 7) / 8) * 8 + 1;  // x-pass row pitch: = 1 mod 8 (bank spread)
-  static constexpr int XS = TY * XP;                   // one x-split component
-  static constexpr int YS = BH * TX;                   // one y-split component
-  static constexpr int SPL = (XS > YS ? XS : YS);      // split buffer per component
-  static constexpr int NB = BH * BW;                   // bed box
-  static constexpr int NC = TX * TY;                   // own cells
-  static constexpr int ELEMS = NB + 6 * SPL + NC + 3 * NC;
+  static constexpr int BW = TX + 6;  // halo box width (cells i0-3 .. i0+TX+2)
+  static constexpr int BH = TY + 6;  // halo box height
+  // row pitch: = 1 mod 8 floats (x-pass lanes on 8 rows x 4 strips hit distinct banks)
+  static constexpr int P = ((BW + 7) / 8) * 8 + 1;
+  static constexpr int FIELD = BH * P;  // one field of the box
+  static constexpr int BOX = 4 * FIELD; // ha, hu, hv, b
+  static constexpr int NC = TX * TY;
+  static constexpr int ELEMS = 2 * BOX + 3 * NC;  // two boxes (double buffer) + L_x
+  static constexpr size_t BYTES = sizeof(T) * (size_t)ELEMS;
 };
 
 // Reduction scratch in shared memory (per CTA).
@@ -320,292 +278,445 @@ struct RedSmem {
   double s[32][2];
   double r[32];
   double dt;
-  double eta_in;
+  double eta_in[3];
   unsigned bad;
   unsigned skip;
 };
 
-// One RK3 stage (Eq. (8), Shu-Osher form) over the tile whose first cell is
-// (i0, j0):
+// The state planes a stage reads and writes.
+template <typename T>
+struct StageIO {
+  const T *b;
+  const T *ha, *hu, *hv;     // stage input (halo reads)
+  const T *ha0, *hu0, *hv0;  // U^n (own cells, stages 2 and 3)
+  T *oha, *ohu, *ohv;        // stage output
+  int nx, ny, pitch;
+};
+
+// Issue the asynchronous copies of the halo box of tile (i0, j0) into box:
+// interior cells only; ghost positions are patched after arrival.
+template <typename T, int TX, int TY, int NT>
+__device__ __forceinline__ void issue_box(const StageIO<T> &io, int i0, int j0, T *box) {
+  using G = TileGeom<T, TX, TY>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T *src[4] = {io.ha, io.hu, io.hv, io.b};
+  for (int r = warp; r < G::BH; r += NT / 32) {
+    const int j = j0 - 3 + r;
+    if (j < 0 || j >= io.ny) continue;
+#pragma unroll
+    for (int c = lane; c < ((G::BW + 31) / 32) * 32; c += 32) {
+      const int i = i0 - 3 + c;
+      if (c < G::BW && i >= 0 && i < io.nx) {
+        const size_t go = (size_t)j * io.pitch + i;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          if (sizeof(T) == 4) cp_async4(box + f * G::FIELD + r * G::P + c, src[f] + go);
+          else cp_async8(box + f * G::FIELD + r * G::P + c, src[f] + go);
+        }
+      }
+    }
+  }
+}
+
+// Fill every box position outside the domain (tiles whose box crosses the
+// domain edge): cells within 3 of the edge along one axis get ghost values,
+// all others (beyond the ghosts, or outside along both axes) are zeroed and
+// never read by a valid cell.  Walls mirror cells of the same box; inflow
+// ghosts carry the N-wave; periodic ghosts are read across the seam.
+template <typename T, int TX, int TY, int NT>
+__device__ __forceinline__ void patch_box(const StageIO<T> &io, const Phys &p, int i0, int j0, T *box, T zref,
+                                          T eta_in, T u_in) {
+  using G = TileGeom<T, TX, TY>;
+  const int nx = io.nx, ny = io.ny;
+  T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
+  for (int q = threadIdx.x; q < G::BH * G::BW; q += NT) {
+    const int r = q / G::BW, c = q - r * G::BW;
+    const int i = i0 - 3 + c, j = j0 - 3 + r;
+    const bool in_i = i >= 0 && i < nx, in_j = j >= 0 && j < ny;
+    if (in_i && in_j) continue;  // a real cell, already loaded
+    const int o = r * G::P + c;
+    const bool xg = !in_i && in_j && i >= -3 && i < nx + 3;  // x ghost
+    const bool yg = in_i && !in_j && j >= -3 && j < ny + 3;  // y ghost
+    if (!xg && !yg) {
+      bha[o] = bhu[o] = bhv[o] = bb[o] = T(0);
+      continue;
+    }
+    const int side = xg ? (i < 0 ? 0 : 1) : (j < 0 ? 2 : 3);
+    const int bc = p.bc[side];
+    if (bc == BC_PERIODIC) {
+      int si = i, sj = j;
+      T shift;
+      if (xg) { si = i < 0 ? i + nx : i - nx; shift = T(i < 0 ? -p.b_jump_x : p.b_jump_x); }
+      else { sj = j < 0 ? j + ny : j - ny; shift = T(j < 0 ? -p.b_jump_y : p.b_jump_y); }
+      const size_t go = (size_t)sj * io.pitch + si;
+      const T bs = io.b[go], cb = bs + shift;
+      bb[o] = cb;
+      bha[o] = (io.ha[go] + still_depth(bs, zref)) - still_depth(cb, zref);
+      bhu[o] = io.hu[go];
+      bhv[o] = io.hv[go];
+      continue;
+    }
+    // mirror source: a real cell of the same box
+    int mc = c, mr = r;
+    if (xg) mc = (i < 0 ? (-1 - i) : (2 * nx - 1 - i)) - (i0 - 3);
+    else mr = (j < 0 ? (-1 - j) : (2 * ny - 1 - j)) - (j0 - 3);
+    const int m = mr * G::P + mc;
+    const T cb = bb[m];
+    bb[o] = cb;
+    if (bc == BC_INFLOW) {
+      const T dg = still_depth(cb, zref);
+      T a;
+      if (cb < zref) { a = eta_in - zref; a = a > -dg ? a : -dg; }
+      else { a = eta_in - cb; a = a > T(0) ? a : T(0); }
+      bha[o] = a;
+      bhu[o] = (a + dg) * u_in;
+      bhv[o] = T(0);
+    } else {
+      bha[o] = bha[m];
+      bhu[o] = xg ? -bhu[m] : bhu[m];
+      bhv[o] = xg ? bhv[m] : -bhv[m];
+    }
+  }
+}
+
+// Sliding WENO5 window over one line of the box.  For faces k = 0..S (face k
+// at the left of strip cell k), with split fluxes computed on the fly from
+// the raw box: F6[m] = 6 Fhat_m, B12 = 12 bhat (normal-momentum weights).
+template <typename T, int DIR>
+struct Window {
+  T fp[3][6], fm[3][6], bw[6];
+  __device__ __forceinline__ void put(int q, const T *bha, const T *bhu, const T *bhv, const T *bb, int o, T alpha,
+                                      T g, T zref, const Phys &p) {
+    T a[3], m[3];
+    const T b = bb[o];
+    split_cell<T, DIR>(bha[o], bhu[o], bhv[o], b, alpha, g, zref, p, a, m);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { fp[c][q] = a[c]; fm[c][q] = m[c]; }
+    bw[q] = b;
+  }
+  __device__ __forceinline__ void shift() {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { fp[c][q] = fp[c][q + 1]; fm[c][q] = fm[c][q + 1]; }
+      bw[q] = bw[q + 1];
+    }
+  }
+  // face between window cells 2 and 3
+  __device__ __forceinline__ void face(T eps12, T F6[3], T &B12) const {
+    constexpr int MOM = DIR == 0 ? 1 : 2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T a0, a1, a2, rp, c0, c1, c2, rm;
+      const T Fp = weno5x6<T>(fp[c][0], fp[c][1], fp[c][2], fp[c][3], fp[c][4], eps12, a0, a1, a2, rp);
+      const T Fm = weno5x6<T>(fm[c][5], fm[c][4], fm[c][3], fm[c][2], fm[c][1], eps12, c0, c1, c2, rm);
+      F6[c] = Fp + Fm;
+      if (c == MOM)
+        B12 = weighted6<T>(bw[0], bw[1], bw[2], bw[3], bw[4], a0, a1, a2, rp) +
+              weighted6<T>(bw[5], bw[4], bw[3], bw[2], bw[1], c0, c1, c2, rm);
+    }
+  }
+};
+
+// Per-CTA accumulators carried across the tiles of one launch.
+template <typename T>
+struct Acc {
+  T ax = T(0), ay = T(0), ru = T(0), chk = T(0);
+  double deficit = 0.0, edge = 0.0;
+};
+
+// One RK3 stage (Eq. (8), Shu-Osher form, increment form) on one tile whose
+// halo box is resident in shared memory:
 //   stage 1: U1 = U^n + dt L(U^n)
-//   stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
-//   stage 3: U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2))   (written over U^n)
-// followed by the post-stage rule, with L of Eq. (7).  NT threads; strips of
-// S cells.  `lead` marks the one tile per scenario that does the per-step
-// bookkeeping (dt, time, step count, slot resets).
-//
-// Stage s reads the wave speeds of its input from slot s-1, publishes those
-// of its output to slot s mod 3 and clears slot (s+1) mod 3, which nothing
-// reads or writes during stage s.
+//   stage 2: U2 = U^n + 1/4 (U1 + dt L(U1) - U^n)
+//   stage 3: U^{n+1} = U^n + 2/3 (U2 + dt L(U2) - U^n)   (written over U^n)
+// followed by the post-stage rule, with L of Eq. (7).
 template <typename T, int TX, int TY, int NT, int S, int STAGE>
-__device__ void stage_tile(const Field<T> &fd, const Phys &p, DevScalars *sc, int i0, int j0, T *smem,
-                           RedSmem &red, bool lead) {
-  using G = TileGeom<TX, TY>;
+__device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p, int i0, int j0, const T *box,
+                                             T *sL, double dt, T alx, T aly, Acc<T> &acc) {
+  using G = TileGeom<T, TX, TY>;
   static_assert(TX % S == 0 && TY % S == 0, "strip length must divide the tile");
   static_assert((TX / S) * TY == NT && (TY / S) * TX == NT, "one strip per thread in both passes");
   static_assert(TY % 8 == 0 && (TX / S) % 4 == 0, "x-pass warp covers 8 rows x 4 strips");
   const int tid = threadIdx.x;
-  const int nx = fd.nx, ny = fd.ny, pitch = fd.pitch;
-  constexpr int IN = STAGE - 1;         // U^n, U1, U2 as stage input
-  constexpr int OUTB = STAGE % 3;       // U1, U2, U^n as stage output
-  const T *__restrict__ bb = fd.b;
-  const T *__restrict__ hin = fd.h[IN];
-  const T *__restrict__ huin = fd.hu[IN];
-  const T *__restrict__ hvin = fd.hv[IN];
-
-  T *sb = smem;               // bed over the halo box
-  T *spl = sb + G::NB;        // 6 split components
-  T *sha = spl + 6 * G::SPL;  // ha of own cells
-  T *sL = sha + G::NC;        // L_x, 3 components
-
-  // ---- stage scalars and the skip decision (uniform over the CTA)
-  const double ax = bitsd(sc->alpha[STAGE - 1][0]);
-  const double ay = bitsd(sc->alpha[STAGE - 1][1]);
-  if (tid == 0) {
-    double dt = 0.0;
-    unsigned skip = sc->status != 0u;
-    if (STAGE == 1) {
-      const double t = sc->t;
-      if (sc->t_end > 0.0 && t >= sc->t_end) skip = 1;
-      if (p.fixed_dt > 0.0) dt = p.fixed_dt;
-      else {
-        const double den = ax / p.dx + ay / p.dy;
-        if (den > 0.0) dt = sc->cfl / den;
-        else if (!skip) { skip = 1; atomicOr(&sc->status, ST_DRY); }
-      }
-      if (sc->t_end > 0.0 && t + dt > sc->t_end) dt = sc->t_end - t;
-      if (lead) {
-        sc->running = skip ? 0u : 1u;
-        if (!skip) {
-          sc->dt = dt;
-          sc->t_step = t;
-          sc->parity = (unsigned)(sc->steps & 1);
-          sc->runup_now[sc->steps & 1] = 0ull;
-          sc->alpha[2][0] = 0ull;
-          sc->alpha[2][1] = 0ull;
-        }
-      }
-    } else {
-      if (!sc->running) skip = 1;
-      dt = sc->dt;
-      if (lead && !skip) {
-        sc->alpha[STAGE == 2 ? 0 : 1][0] = 0ull;
-        sc->alpha[STAGE == 2 ? 0 : 1][1] = 0ull;
-      }
-    }
-    red.skip = skip;
-    red.bad = 0u;
-    red.dt = dt;
-    const double tst = (STAGE == 1) ? sc->t : sc->t_step;
-    const double ts = (STAGE == 1) ? tst : (STAGE == 2 ? tst + dt : tst + 0.5 * dt);
-    red.eta_in = (p.bc[0] == BC_INFLOW && i0 == 0) ? inflow_eta(p, ts) : 0.0;
-  }
-  __syncthreads();
-  if (red.skip) return;
-  const double dt = red.dt;
-  const T eta_in = T(red.eta_in);
-  const T u_in = (p.bc[0] == BC_INFLOW) ? T(red.eta_in * sqrt(p.g / p.inflow_depth)) : T(0);
+  const int nx = io.nx, ny = io.ny;
+  const T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
   const T g = T(p.g), zref = T(p.z_ref), eps12 = T(12.0 * p.weno_eps);
-  const T alx = T(ax), aly = T(ay);
 
-  // ---- phase A: bed box, x-split fluxes (own rows, halo columns), ha of own cells
-  for (int idx = tid; idx < G::NB; idx += NT) {
-    const int r = idx / G::BW, c = idx - r * G::BW;
-    const int i = i0 - 3 + c, j = j0 - 3 + r;
-    const bool xin = (i >= -3 && i < nx + 3), yin = (j >= -3 && j < ny + 3);
-    const bool ix = (i >= 0 && i < nx), jy = (j >= 0 && j < ny);
-    const bool own_row = (r >= 3 && r < TY + 3);
-    T cb = T(0);
-    if ((ix && yin) || (jy && xin)) {
-      T ch, chu, chv;
-      load_cell<T>(bb, hin, huin, hvin, nx, ny, pitch, p, zref, eta_in, u_in, i, j, ch, chu, chv, cb);
-      if (own_row) {
-        T fp[3], fm[3];
-        if (jy) split_cell<T, 0>(ch, chu, chv, cb, alx, g, zref, p, fp, fm);
-        else { fp[0] = fp[1] = fp[2] = fm[0] = fm[1] = fm[2] = T(0); }
-        const int o = (r - 3) * G::XP + c;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) { spl[m * G::SPL + o] = fp[m]; spl[(3 + m) * G::SPL + o] = fm[m]; }
-        if (c >= 3 && c < TX + 3) sha[(r - 3) * TX + (c - 3)] = ch;
-      }
-    } else if (own_row) {
-      const int o = (r - 3) * G::XP + c;
-#pragma unroll
-      for (int m = 0; m < 6; ++m) spl[m * G::SPL + o] = T(0);
-      if (c >= 3 && c < TX + 3) sha[(r - 3) * TX + (c - 3)] = T(0);
-    }
-    sb[idx] = cb;
-  }
-  __syncthreads();
-
-  T fsum_edge = T(0);  // 6 x (mass flux into the domain through its edges), per unit length in y
-  // ---- phase B: x pass.  Lane l of warp w covers row 8*(w % (TY/8)) + l/4 and
-  // strip 4*(w / (TY/8)) + l%4 (8 rows x 4 strips: conflict-free with XP = 1 mod 8).
+  // ---- x pass: lane l of warp w: row 8*(w % (TY/8)) + l/4, strip 4*(w / (TY/8)) + l%4
   {
     const int w = tid >> 5, l = tid & 31;
     const int r = 8 * (w % (TY / 8)) + (l >> 2);
     const int c0 = (4 * (w / (TY / 8)) + (l & 3)) * S;
-    T dF[3][S], db[S], Ff[S + 1];
-    sweep_strip<T, S, 1>(spl + r * G::XP + c0, 1, G::SPL, 3 * G::SPL, sb + (r + 3) * G::BW + c0, 1, eps12, dF,
-                         db, Ff);
+    const int row = (r + 3) * G::P;
+    Window<T, 0> win;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) win.put(q, bha, bhu, bhv, bb, row + c0 + q, alx, g, zref, p);
     const T inv6dx = T(1.0 / (6.0 * p.dx));
     const T g12dx = T(p.g / (12.0 * p.dx));
+    T prevF[3], prevB = T(0);
+    const bool edge_row = (j0 + r < ny);
+    const int ia = i0 + c0;
 #pragma unroll
-    for (int k = 0; k < S; ++k) {
-      const int o = r * TX + c0 + k;
-      sL[o] = -dF[0][k] * inv6dx;
-      sL[G::NC + o] = -dF[1][k] * inv6dx - g12dx * sha[o] * db[k];
-      sL[2 * G::NC + o] = -dF[2][k] * inv6dx;
-    }
-    if (j0 + r < ny) {
-      const int ia = i0 + c0;  // global index of the strip's first cell
-      if (ia == 0) fsum_edge += Ff[0];
-      const int kk = nx - ia;  // face nx-1/2 is face kk of the strip
+    for (int k = 0; k <= S; ++k) {
+      win.put(5, bha, bhu, bhv, bb, row + c0 + k + 5, alx, g, zref, p);
+      T F6[3], B12 = T(0);
+      win.face(eps12, F6, B12);
+      if (k > 0) {
+        const int o = r * TX + c0 + k - 1;
+        const T ha = bha[row + c0 + k + 2];
+        sL[o] = -(F6[0] - prevF[0]) * inv6dx;
+        sL[G::NC + o] = -(F6[1] - prevF[1]) * inv6dx - g12dx * ha * (B12 - prevB);
+        sL[2 * G::NC + o] = -(F6[2] - prevF[2]) * inv6dx;
+      }
+      // faces -1/2 (k = 0 of the first strip) and nx-1/2 (k >= 1 of the strip holding cell nx-1)
+      if (edge_row && ((k == 0 && ia == 0) || (k > 0 && ia + k == nx)))
+        acc.edge += (ia + k == 0) ? (double)F6[0] : -(double)F6[0];
 #pragma unroll
-      for (int k = 1; k <= S; ++k)
-        if (k == kk) fsum_edge -= Ff[k];
+      for (int c = 0; c < 3; ++c) prevF[c] = F6[c];
+      prevB = B12;
+      win.shift();
     }
   }
   __syncthreads();
 
-  // ---- phase B': y-split fluxes (halo rows, own columns) into the same buffer
-  for (int idx = tid; idx < G::BH * TX; idx += NT) {
-    const int r = idx / TX, c = idx - r * TX;
-    const int i = i0 + c, j = j0 - 3 + r;
-    T fp[3], fm[3];
-    if (i < nx && j >= -3 && j < ny + 3) {
-      T ch, chu, chv, cb;
-      load_cell<T>(bb, hin, huin, hvin, nx, ny, pitch, p, zref, eta_in, u_in, i, j, ch, chu, chv, cb);
-      split_cell<T, 1>(ch, chu, chv, cb, aly, g, zref, p, fp, fm);
-    } else {
-      fp[0] = fp[1] = fp[2] = fm[0] = fm[1] = fm[2] = T(0);
-    }
-#pragma unroll
-    for (int m = 0; m < 3; ++m) { spl[m * G::SPL + idx] = fp[m]; spl[(3 + m) * G::SPL + idx] = fm[m]; }
-  }
-  __syncthreads();
-
-  // ---- phase C: y pass, sources, RK combination, post rule, reductions
-  T amax_x = T(0), amax_y = T(0), runup = T(0);
-  double deficit = 0.0;
-  bool bad = false;
+  // ---- y pass, sources, RK combination, post rule
   {
     const int c = tid % TX, r0 = (tid / TX) * S;
-    T dG[3][S], db[S], Gf[S + 1];
-    sweep_strip<T, S, 2>(spl + r0 * TX + c, TX, G::SPL, 3 * G::SPL, sb + r0 * G::BW + (c + 3), G::BW, eps12, dG,
-                         db, Gf);
     const int i = i0 + c;
-    if (i < nx) {
-      const T rxy = T(p.dx / p.dy);
-      const int jb = j0 + r0;
-      if (jb == 0) fsum_edge += Gf[0] * rxy;
-      const int kk = ny - jb;
+    const bool col_ok = i < nx;
+    // U^n of the own cells, fetched early (used at the end)
+    T u0[3][S];
+    if (STAGE != 1) {
 #pragma unroll
-      for (int k = 1; k <= S; ++k)
-        if (k == kk) fsum_edge -= Gf[k] * rxy;
+      for (int k = 0; k < S; ++k) {
+        const int j = j0 + r0 + k;
+        if (col_ok && j < ny) {
+          const size_t go = (size_t)j * io.pitch + i;
+          u0[0][k] = io.ha0[go];
+          u0[1][k] = io.hu0[go];
+          u0[2][k] = io.hv0[go];
+        } else {
+          u0[0][k] = u0[1][k] = u0[2][k] = T(0);
+        }
+      }
     }
+    Window<T, 1> win;
+    const int col = c + 3;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) win.put(q, bha, bhu, bhv, bb, (r0 + q) * G::P + col, aly, g, zref, p);
     const T inv6dy = T(1.0 / (6.0 * p.dy));
     const T g12dy = T(p.g / (12.0 * p.dy));
     const T tdt = T(dt);
     const T rcap = dt > 0.0 ? T(1.0 / dt) : T(0);
     const T gn2 = T(p.g * p.n2);
     const bool friction = p.n2 > 0.0;
+    const T wrk = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
+    const T rxy = T(p.dx / p.dy);
+    T prevF[3], prevB = T(0);
+    const int jb = j0 + r0;
 #pragma unroll
-    for (int k = 0; k < S; ++k) {
-      const int j = j0 + r0 + k;
-      if (i < nx && j < ny) {
-        const int o = (r0 + k) * TX + c;
-        const size_t go = (size_t)j * pitch + i;
-        const T ha = hin[go], hu = huin[go], hv = hvin[go];
-        const T bc = bb[go];
-        const T d = still_depth(bc, zref);
-        const T h = ha + d;
-        T Lh = sL[o] - dG[0][k] * inv6dy;
-        T Lhu = sL[G::NC + o] - dG[1][k] * inv6dy;
-        T Lhv = sL[2 * G::NC + o] - dG[2][k] * inv6dy - g12dy * sha[o] * db[k];
-        if (friction && !Num<T>::below(h, p.h_dry32, p.h_dry)) {
-          const T q = Num<T>::sqrt_(hu * hu + hv * hv);
-          T kap = gn2 * q * Num<T>::rcp(Num<T>::pow73(h));
-          if (dt > 0.0 && kap > rcap) kap = rcap;
-          Lhu -= kap * hu;
-          Lhv -= kap * hv;
-        }
-        // RK combination in increment form: U0 + w (U + dt L - U0)
-        T nha = ha + tdt * Lh, nhu = hu + tdt * Lhu, nhv = hv + tdt * Lhv;
-        if (STAGE != 1) {
-          const T w = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
-          const T ha0 = fd.h[0][go], hu0 = fd.hu[0][go], hv0 = fd.hv[0][go];
-          nha = ha0 + w * (nha - ha0);
-          nhu = hu0 + w * (nhu - hu0);
-          nhv = hv0 + w * (nhv - hv0);
-        }
-        // post-stage rule: clamp negative depth (counted), dry cells at rest
-        if (nha < -d) { deficit -= (double)(nha + d); nha = -d; }
-        const T nh = nha + d;
-        T u = T(0), v = T(0);
-        if (Num<T>::below(nh, p.h_dry32, p.h_dry)) { nhu = T(0); nhv = T(0); }
-        else { const T rr = Num<T>::rcp(nh); u = nhu * rr; v = nhv * rr; }
-        fd.h[OUTB][go] = nha;
-        fd.hu[OUTB][go] = nhu;
-        fd.hv[OUTB][go] = nhv;
-        const T cel = Num<T>::sqrt_(g * nh);
-        const T sx = fabs(u) + cel, sy = fabs(v) + cel;
-        if (!(sx <= T(3.0e38)) || !(sy <= T(3.0e38)) || !(fabs(nhu) <= T(3.0e38)) || !(fabs(nhv) <= T(3.0e38)))
-          bad = true;
-        amax_x = sx > amax_x ? sx : amax_x;
-        amax_y = sy > amax_y ? sy : amax_y;
-        if (STAGE == 3 && !Num<T>::below(nh, p.h_wet32, p.h_wet) && bc > T(0)) {
-          const T e = nh + bc;
-          runup = e > runup ? e : runup;
+    for (int k = 0; k <= S; ++k) {
+      win.put(5, bha, bhu, bhv, bb, (r0 + k + 5) * G::P + col, aly, g, zref, p);
+      T F6[3], B12 = T(0);
+      win.face(eps12, F6, B12);
+      if (col_ok && ((k == 0 && jb == 0) || (k > 0 && jb + k == ny)))
+        acc.edge += (jb + k == 0 ? 1.0 : -1.0) * (double)(F6[0] * rxy);
+      if (k > 0) {
+        const int kk = k - 1;
+        const int j = jb + kk;
+        if (col_ok && j < ny) {
+          const int o = (r0 + kk) * TX + c;
+          const int bo = (r0 + kk + 3) * G::P + col;
+          const T ha = bha[bo], hu = bhu[bo], hv = bhv[bo], bc = bb[bo];
+          const T d = still_depth(bc, zref);
+          const T h = ha + d;
+          T Lh = sL[o] - (F6[0] - prevF[0]) * inv6dy;
+          T Lhu = sL[G::NC + o] - (F6[1] - prevF[1]) * inv6dy;
+          T Lhv = sL[2 * G::NC + o] - (F6[2] - prevF[2]) * inv6dy - g12dy * ha * (B12 - prevB);
+          if (friction && !Num<T>::below(h, p.h_dry32, p.h_dry)) {
+            const T q = Num<T>::sqrt_(hu * hu + hv * hv);
+            T kap = gn2 * q * Num<T>::rcp(Num<T>::pow73(h));
+            kap = kap > rcap ? rcap : kap;
+            Lhu -= kap * hu;
+            Lhv -= kap * hv;
+          }
+          T nha = ha + tdt * Lh, nhu = hu + tdt * Lhu, nhv = hv + tdt * Lhv;
+          if (STAGE != 1) {
+            nha = u0[0][kk] + wrk * (nha - u0[0][kk]);
+            nhu = u0[1][kk] + wrk * (nhu - u0[1][kk]);
+            nhv = u0[2][kk] + wrk * (nhv - u0[2][kk]);
+          }
+          if (nha < -d) { acc.deficit -= (double)(nha + d); nha = -d; }
+          const T nh = nha + d;
+          T u = T(0), v = T(0);
+          if (Num<T>::below(nh, p.h_dry32, p.h_dry)) { nhu = T(0); nhv = T(0); }
+          else { const T rr = Num<T>::rcp(nh); u = nhu * rr; v = nhv * rr; }
+          const size_t go = (size_t)j * io.pitch + i;
+          io.oha[go] = nha;
+          io.ohu[go] = nhu;
+          io.ohv[go] = nhv;
+          const T cel = Num<T>::sqrt_(g * nh);
+          const T sx = fabs(u) + cel, sy = fabs(v) + cel;
+          acc.chk += sx + sy;  // non-finite values propagate to the per-CTA check
+          acc.ax = sx > acc.ax ? sx : acc.ax;
+          acc.ay = sy > acc.ay ? sy : acc.ay;
+          if (STAGE == 3 && !Num<T>::below(nh, p.h_wet32, p.h_wet) && bc > T(0)) {
+            const T e = nh + bc;
+            acc.ru = e > acc.ru ? e : acc.ru;
+          }
         }
       }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) prevF[q] = F6[q];
+      prevB = B12;
+      win.shift();
     }
   }
+}
 
-  // ---- block reductions and device-scope publication
-  const int w = tid >> 5, l = tid & 31;
-  amax_x = warp_max(amax_x);
-  amax_y = warp_max(amax_y);
-  runup = warp_max(runup);
-  deficit = warp_sum(deficit);
-  const double ef = warp_sum((double)fsum_edge);
+// Per-stage scalars and the skip decision, taken by thread 0 of every CTA;
+// the lead CTA of a scenario also does the per-step bookkeeping.  Stage s
+// reads the wave speeds of its input from slot s-1, publishes those of its
+// output to slot s mod 3 and clears slot (s+1) mod 3, which nothing reads or
+// writes during stage s.
+template <int STAGE>
+__device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, bool lead, RedSmem &red, double &ax,
+                                              double &ay) {
+  ax = bitsd(sc->alpha[STAGE - 1][0]);
+  ay = bitsd(sc->alpha[STAGE - 1][1]);
+  double dt = 0.0;
+  unsigned skip = sc->status != 0u;
+  if (STAGE == 1) {
+    const double t = sc->t;
+    if (sc->t_end > 0.0 && t >= sc->t_end) skip = 1;
+    if (p.fixed_dt > 0.0) dt = p.fixed_dt;
+    else {
+      const double den = ax / p.dx + ay / p.dy;
+      if (den > 0.0) dt = sc->cfl / den;
+      else if (!skip) { skip = 1; atomicOr(&sc->status, ST_DRY); }
+    }
+    if (sc->t_end > 0.0 && t + dt > sc->t_end) dt = sc->t_end - t;
+    if (lead) {
+      sc->running = skip ? 0u : 1u;
+      if (!skip) {
+        sc->dt = dt;
+        sc->t_step = t;
+        sc->parity = (unsigned)(sc->steps & 1);
+        sc->runup_now[sc->steps & 1] = 0ull;
+        sc->alpha[2][0] = 0ull;
+        sc->alpha[2][1] = 0ull;
+      }
+    }
+  } else {
+    if (!sc->running) skip = 1;
+    dt = sc->dt;
+    if (lead && !skip) {
+      sc->alpha[STAGE == 2 ? 0 : 1][0] = 0ull;
+      sc->alpha[STAGE == 2 ? 0 : 1][1] = 0ull;
+    }
+  }
+  red.skip = skip;
+  red.bad = 0u;
+  red.dt = dt;
+  const double tst = (STAGE == 1) ? sc->t : sc->t_step;
+  const double ts = (STAGE == 1) ? tst : (STAGE == 2 ? tst + dt : tst + 0.5 * dt);
+  red.eta_in[0] = (p.bc[0] == BC_INFLOW) ? inflow_eta(p, ts) : 0.0;
+}
+
+// Block reduction of the per-thread accumulators and device-scope
+// publication for one scenario.
+template <typename T, int NT, int STAGE>
+__device__ __forceinline__ void publish(const Phys &p, DevScalars *sc, bool lead, RedSmem &red, double dt,
+                                        const Acc<T> &acc) {
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const T ax = warp_max(acc.ax), ay = warp_max(acc.ay), ru = warp_max(acc.ru);
+  const double de = warp_sum(acc.deficit), ef = warp_sum(acc.edge);
+  const bool bad = !(acc.chk <= T(3.0e38));
   const unsigned anybad = __any_sync(0xffffffffu, bad);
   if (l == 0) {
-    red.a[w][0] = (double)amax_x;
-    red.a[w][1] = (double)amax_y;
-    red.s[w][0] = deficit;
+    red.a[w][0] = (double)ax;
+    red.a[w][1] = (double)ay;
+    red.s[w][0] = de;
     red.s[w][1] = ef;
-    red.r[w] = (double)runup;
+    red.r[w] = (double)ru;
     if (anybad) red.bad = 1u;
   }
   __syncthreads();
   if (tid == 0) {
-    double mx = 0.0, my = 0.0, de = 0.0, fe = 0.0, ru = 0.0;
+    double mx = 0.0, my = 0.0, dsum = 0.0, fsum = 0.0, rmax = 0.0;
     for (int q = 0; q < NT / 32; ++q) {
       mx = fmax(mx, red.a[q][0]);
       my = fmax(my, red.a[q][1]);
-      de += red.s[q][0];
-      fe += red.s[q][1];
-      ru = fmax(ru, red.r[q]);
+      dsum += red.s[q][0];
+      fsum += red.s[q][1];
+      rmax = fmax(rmax, red.r[q]);
     }
     atomicMax(&sc->alpha[STAGE % 3][0], dbits(mx));
     atomicMax(&sc->alpha[STAGE % 3][1], dbits(my));
     constexpr double wgt = (STAGE == 3) ? 1.0 : (STAGE == 2 ? 2.0 / 3.0 : 1.0 / 6.0);
     constexpr double wfl = (STAGE == 3) ? 2.0 / 3.0 : 1.0 / 6.0;
-    if (de != 0.0) atomicAdd(&sc->clamp_mass, wgt * de * p.dx * p.dy);
-    if (fe != 0.0) atomicAdd(&sc->boundary_mass, wfl * dt * fe * p.dy / 6.0);
-    if (STAGE == 3 && ru > 0.0) {
-      const unsigned long long rb = dbits(ru);
+    if (dsum != 0.0) atomicAdd(&sc->clamp_mass, wgt * dsum * p.dx * p.dy);
+    if (fsum != 0.0) atomicAdd(&sc->boundary_mass, wfl * dt * fsum * p.dy / 6.0);
+    if (STAGE == 3 && rmax > 0.0) {
+      const unsigned long long rb = dbits(rmax);
       atomicMax(&sc->runup_now[sc->parity], rb);
       atomicMax(&sc->runup_max, rb);
     }
-    if (red.bad || !(mx <= 1e300) || !(my <= 1e300)) atomicOr(&sc->status, ST_NONFINITE);
+    if (red.bad) atomicOr(&sc->status, ST_NONFINITE);
     if (STAGE == 3 && lead) {
       const double tn = sc->t_step + dt;
       sc->t = (sc->t_end > 0.0 && tn >= sc->t_end) ? sc->t_end : tn;
       sc->steps += 1;
     }
   }
+}
+
+// Persistent stage over all tiles of one scenario: CTA b handles tiles
+// b, b + gridDim.x, ...; the halo box of the next tile is copied
+// asynchronously while the current one is computed.
+template <typename T, int TX, int TY, int NT, int S, int STAGE>
+__device__ void stage_persistent(const StageIO<T> &io, const Phys &p, DevScalars *sc, T *smem, RedSmem &red,
+                                 int first, int stride, bool lead) {
+  using G = TileGeom<T, TX, TY>;
+  const int tid = threadIdx.x;
+  const int tiles_x = (io.nx + TX - 1) / TX, tiles_y = (io.ny + TY - 1) / TY;
+  const int ntiles = tiles_x * tiles_y;
+  if (tid == 0) {
+    double ax, ay;
+    stage_scalars<STAGE>(p, sc, lead, red, ax, ay);
+    red.a[0][0] = ax;
+    red.a[0][1] = ay;
+  }
+  __syncthreads();
+  if (red.skip) return;
+  const double dt = red.dt;
+  const T alx = T(red.a[0][0]), aly = T(red.a[0][1]);
+  const T zref = T(p.z_ref);
+  const T eta_in = T(red.eta_in[0]);
+  const T u_in = (p.bc[0] == BC_INFLOW) ? T(red.eta_in[0] * sqrt(p.g / p.inflow_depth)) : T(0);
+  T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
+  Acc<T> acc;
+  int t = first;
+  if (t < ntiles) issue_box<T, TX, TY, NT>(io, (t % tiles_x) * TX, (t / tiles_x) * TY, box0);
+  cp_commit();
+  for (int it = 0; t < ntiles; ++it, t += stride) {
+    T *box = (it & 1) ? box1 : box0;
+    const int tn = t + stride;
+    if (tn < ntiles) issue_box<T, TX, TY, NT>(io, (tn % tiles_x) * TX, (tn / tiles_x) * TY, (it & 1) ? box0 : box1);
+    cp_commit();
+    cp_wait<1>();
+    __syncthreads();
+    const int i0 = (t % tiles_x) * TX, j0 = (t / tiles_x) * TY;
+    if (i0 == 0 || j0 == 0 || i0 + TX + 3 > io.nx || j0 + TY + 3 > io.ny) {
+      patch_box<T, TX, TY, NT>(io, p, i0, j0, box, zref, eta_in, u_in);
+      __syncthreads();
+    }
+    tile_compute<T, TX, TY, NT, S, STAGE>(io, p, i0, j0, box, sL, dt, alx, aly, acc);
+    __syncthreads();
+  }
+  cp_wait<0>();
+  publish<T, NT, STAGE>(p, sc, lead, red, dt, acc);
 }
 
 }  // namespace swe

@@ -10,36 +10,75 @@
 
 namespace swe {
 
+// Persistent: CTA b handles tiles b, b + gridDim.x, ... of the scenario.
 template <typename T, int TX, int TY, int NT, int S, int STAGE, int MINB>
-__global__ void __launch_bounds__(NT, MINB) stage_kernel(Field<T> fd, Phys p, DevScalars *sc) {
+__global__ void __launch_bounds__(NT, MINB) stage_kernel(StageIO<T> io, Phys p, DevScalars *sc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RedSmem red;
-  stage_tile<T, TX, TY, NT, S, STAGE>(fd, p, sc, blockIdx.x * TX, blockIdx.y * TY, reinterpret_cast<T *>(smem_raw),
-                                      red, blockIdx.x == 0 && blockIdx.y == 0);
+  stage_persistent<T, TX, TY, NT, S, STAGE>(io, p, sc, reinterpret_cast<T *>(smem_raw), red, blockIdx.x,
+                                            gridDim.x, blockIdx.x == 0);
+}
+
+template <typename T>
+static StageIO<T> stage_io(const Field<T> &fd, int stage) {
+  StageIO<T> io;
+  const int in = stage - 1, out = stage % 3;
+  io.b = fd.b;
+  io.ha = fd.h[in];
+  io.hu = fd.hu[in];
+  io.hv = fd.hv[in];
+  io.ha0 = fd.h[0];
+  io.hu0 = fd.hu[0];
+  io.hv0 = fd.hv[0];
+  io.oha = fd.h[out];
+  io.ohu = fd.hu[out];
+  io.ohv = fd.hv[out];
+  io.nx = fd.nx;
+  io.ny = fd.ny;
+  io.pitch = fd.pitch;
+  return io;
 }
 
 template <typename T, int TX, int TY, int NT, int S, int MINB>
-static cudaError_t launch_stages(const Field<T> &fd, const Phys &p, DevScalars *sc, int stage, cudaStream_t st) {
-  constexpr size_t smem = sizeof(T) * TileGeom<TX, TY>::ELEMS;
-  const dim3 grid((fd.nx + TX - 1) / TX, (fd.ny + TY - 1) / TY);
-  switch (stage) {
-    case 1: stage_kernel<T, TX, TY, NT, S, 1, MINB><<<grid, NT, smem, st>>>(fd, p, sc); break;
-    case 2: stage_kernel<T, TX, TY, NT, S, 2, MINB><<<grid, NT, smem, st>>>(fd, p, sc); break;
-    default: stage_kernel<T, TX, TY, NT, S, 3, MINB><<<grid, NT, smem, st>>>(fd, p, sc); break;
+struct Shape {
+  static constexpr size_t smem = TileGeom<T, TX, TY>::BYTES;
+  static int resident;  // CTAs per SM, from the occupancy calculator
+  static int sms;
+
+  static cudaError_t prepare() {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(stage_kernel<T, TX, TY, NT, S, 1, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(stage_kernel<T, TX, TY, NT, S, 2, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(stage_kernel<T, TX, TY, NT, S, 3, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nb = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<T, TX, TY, NT, S, 2, MINB>, NT, smem);
+    resident = nb > 0 ? nb : 1;
+    return e;
   }
-  return cudaGetLastError();
-}
 
-template <typename T, int TX, int TY, int NT, int S, int MINB>
-static cudaError_t prepare(int) {
-  constexpr size_t smem = sizeof(T) * TileGeom<TX, TY>::ELEMS;
-  cudaError_t e;
-  e = cudaFuncSetAttribute(stage_kernel<T, TX, TY, NT, S, 1, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(stage_kernel<T, TX, TY, NT, S, 2, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(stage_kernel<T, TX, TY, NT, S, 3, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
+  static cudaError_t launch(const Field<T> &fd, const Phys &p, DevScalars *sc, int stage, cudaStream_t st) {
+    const int ntiles = ((fd.nx + TX - 1) / TX) * ((fd.ny + TY - 1) / TY);
+    int grid = resident * (sms > 0 ? sms : 1);
+    if (grid > ntiles) grid = ntiles;
+    const StageIO<T> io = stage_io(fd, stage);
+    switch (stage) {
+      case 1: stage_kernel<T, TX, TY, NT, S, 1, MINB><<<grid, NT, smem, st>>>(io, p, sc); break;
+      case 2: stage_kernel<T, TX, TY, NT, S, 2, MINB><<<grid, NT, smem, st>>>(io, p, sc); break;
+      default: stage_kernel<T, TX, TY, NT, S, 3, MINB><<<grid, NT, smem, st>>>(io, p, sc); break;
+    }
+    return cudaGetLastError();
+  }
+};
+template <typename T, int TX, int TY, int NT, int S, int MINB> int Shape<T, TX, TY, NT, S, MINB>::resident = 1;
+template <typename T, int TX, int TY, int NT, int S, int MINB> int Shape<T, TX, TY, NT, S, MINB>::sms = 1;
+
+template <typename T> using Shape1 = Shape<T, 32, 32, 128, 8, sizeof(T) == 8 ? 1 : 3>;
+template <typename T> using Shape2 = Shape<T, 64, 32, 256, 8, 1>;
+template <typename T> using Shape3 = Shape<T, 32, 64, 256, 8, 1>;
 
 #if SWE_PREC == 32
 // Compiled tile shapes: {TX, TY, threads}.  Strips of 8 cells per thread.
@@ -51,9 +90,9 @@ const TileShape *shape(int k) { return (k >= 1 && k <= kNumShapes) ? &kShapes[k 
 
 size_t shape_smem(int k, int elem) {
   switch (k) {
-    case 1: return (size_t)elem * TileGeom<32, 32>::ELEMS;
-    case 2: return (size_t)elem * TileGeom<64, 32>::ELEMS;
-    case 3: return (size_t)elem * TileGeom<32, 64>::ELEMS;
+    case 1: return elem == 8 ? TileGeom<double, 32, 32>::BYTES : TileGeom<float, 32, 32>::BYTES;
+    case 2: return elem == 8 ? TileGeom<double, 64, 32>::BYTES : TileGeom<float, 64, 32>::BYTES;
+    case 3: return elem == 8 ? TileGeom<double, 32, 64>::BYTES : TileGeom<float, 32, 64>::BYTES;
   }
   return 0;
 }
@@ -61,22 +100,20 @@ size_t shape_smem(int k, int elem) {
 
 template <typename T>
 cudaError_t prepare_shape(int k) {
-  constexpr bool D = sizeof(T) == 8;
   switch (k) {
-    case 1: return prepare<T, 32, 32, 128, 8, D ? 2 : 4>(0);
-    case 2: return prepare<T, 64, 32, 256, 8, D ? 1 : 2>(0);
-    case 3: return prepare<T, 32, 64, 256, 8, D ? 1 : 2>(0);
+    case 1: return Shape1<T>::prepare();
+    case 2: return Shape2<T>::prepare();
+    case 3: return Shape3<T>::prepare();
   }
   return cudaErrorInvalidValue;
 }
 
 template <typename T>
 cudaError_t launch_stage(int k, const Field<T> &fd, const Phys &p, DevScalars *sc, int stage, cudaStream_t st) {
-  constexpr bool D = sizeof(T) == 8;
   switch (k) {
-    case 1: return launch_stages<T, 32, 32, 128, 8, D ? 2 : 4>(fd, p, sc, stage, st);
-    case 2: return launch_stages<T, 64, 32, 256, 8, D ? 1 : 2>(fd, p, sc, stage, st);
-    case 3: return launch_stages<T, 32, 64, 256, 8, D ? 1 : 2>(fd, p, sc, stage, st);
+    case 1: return Shape1<T>::launch(fd, p, sc, stage, st);
+    case 2: return Shape2<T>::launch(fd, p, sc, stage, st);
+    case 3: return Shape3<T>::launch(fd, p, sc, stage, st);
   }
   return cudaErrorInvalidValue;
 }
