@@ -167,6 +167,32 @@ int swe_tile_shape(int k, int32_t *tx, int32_t *ty, int32_t *threads);
  * (*ms_total) and of each stage kernel (ms_stage[3], may be NULL). */
 int swe_time_stages(swe_handle *s, int32_t n, double cfl, double *ms_total, double *ms_stage);
 
+/* Allocation-free water volume of a caller-owned device depth field.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they need the diagnostic (a process
+ * that reserves its whole HBM budget up front, a loop that must not take
+ * the device-wide synchronisation of cudaMalloc/cudaFree, or a C host with no
+ * allocator or handle).  It computes sum(h) dx dy in FP64 with a fixed
+ * summation order, like swe_mass, using a scratch array of one FP64 partial
+ * per row that lives in the library's device image (SWE_NOALLOC_MAX_ROWS
+ * doubles, held by every device that loads the library until exit).
+ *   h         device array [ny][nx] (contiguous) of float (SWE_F32) or double
+ *             (SWE_F64), owned by the caller
+ *   mass      device pointer to one double, owned by the caller; written when
+ *             the enqueued work completes
+ *   stream    cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Returns SWE_EINVAL for null pointers, non-positive sizes or spacings, an
+ * unknown precision, or ny > SWE_NOALLOC_MAX_ROWS (checked before any device
+ * work); SWE_ECUDA if the launch fails.  Asynchronous; allocates nothing.
+ * The first call on a device looks up the scratch array's address and caches
+ * it: make that first call before any stream capture on the device.  All
+ * calls on a device share the scratch array, so calls whose work overlaps on
+ * the GPU (several streams or host threads) race; calls ordered on one
+ * stream are safe and need no clearing in between. */
+#define SWE_NOALLOC_MAX_ROWS 16384
+int swe_mass_noalloc(const void *h, int32_t precision, int32_t nx, int32_t ny, double dx, double dy,
+                     double *mass, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@ UNITS: List[Tuple[str, List[str], str]] = [
     ("swe_kernels.cu", ["-DSWE_PREC=32"], "swe_kernels_f32.o"),
     ("swe_kernels.cu", ["-DSWE_PREC=64"], "swe_kernels_f64.o"),
     ("swe_api.cu", [], "swe_api.o"),
+    ("swe_noalloc.cu", [], "swe_noalloc.o"),
 ]
 
 
