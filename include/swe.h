@@ -66,6 +66,8 @@ typedef struct {
   double manning_n;     /* Manning n of Eqs. (2)-(3); 0 disables friction */
   double h_dry;         /* depth below which a cell is dry (compared in FP64); 1e-5 m */
   double h_wet;         /* depth from which a land cell (b > 0) counts for runup; 1e-3 m */
+  double h_film;        /* films with h_dry <= h < h_film get the Kurganov-Petrova velocity
+                           desingularisation hu := sqrt(2) h^2 hu / sqrt(h^4 + h_film^4); 1e-3 m */
   double weno_eps;      /* WENO5 epsilon; 1e-6 */
   double fixed_dt;      /* > 0: fixed time step (the paper's runs use 5e-3 s); else CFL */
   double z_ref;         /* still-water level of the bed splitting; 0 m */
@@ -166,6 +168,68 @@ int swe_tile_shape(int k, int32_t *tx, int32_t *ty, int32_t *threads);
  * each stage kernel, wait, and return the summed milliseconds of whole steps
  * (*ms_total) and of each stage kernel (ms_stage[3], may be NULL). */
 int swe_time_stages(swe_handle *s, int32_t n, double cfl, double *ms_total, double *ms_stage);
+
+/* ----------------------------------------------------------------------
+ * Batched ensemble and continuous-batching serving (FP32, walls).
+ * A batch holds up to nslots independent scenarios ("slots") of any grid
+ * size, admitted while device memory stays within hbm_budget_bytes.
+ * swe_batch_run advances every live slot by up to k RK3 steps (each slot
+ * with its own CFL time step, stopping at its t_end) in ONE cooperative
+ * persistent kernel launch over a work list of (scenario, tile) pairs,
+ * with a bounded grid barrier between the three RK stages, replayed from a
+ * CUDA graph.  Each scenario keeps its own wave speeds, dt, time and step
+ * count on the device, so its result is the same alone and in any mix.
+ * ---------------------------------------------------------------------- */
+typedef struct swe_batch swe_batch;
+
+/* Device bytes one admission of this grid takes (counted against the budget). */
+size_t swe_batch_slot_bytes(const swe_grid *grid);
+
+/* Create an empty batch.  params: precision must be SWE_F32 and all four
+ * sides SWE_BC_WALL; tile 0 picks the default shape; stream as for swe_create.
+ * SWE_EINVAL otherwise. */
+int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *params, swe_batch **out);
+
+/* Admit a scenario: host FP64 bathymetry and state [ny][nx] (copied), run until
+ * simulated time t_end (> 0).  Allocates the slot's device memory stream-ordered
+ * (cudaMallocAsync).  Returns the slot index in *slot; SWE_EBUDGET if the
+ * budget would be exceeded, SWE_EFULL if no slot is free.  Call between runs. */
+int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, const double *bathymetry,
+                    const double *h, const double *hu, const double *hv, double t_end, int32_t *slot);
+
+/* Enqueue one persistent launch of k RK3 steps over all live slots with the
+ * given CFL number (asynchronous; slots past t_end are skipped). */
+int swe_batch_run(swe_batch *b, int32_t k_steps, double cfl);
+
+/* List live slots that reached t_end or failed (synchronises).  done_slots
+ * must hold nslots entries (may be NULL to count only). */
+int swe_batch_poll(swe_batch *b, int32_t *done_slots, int32_t *ndone);
+
+/* Copy a live slot's state to host FP64 arrays [ny][nx] (synchronises). */
+int swe_batch_get_state(swe_batch *b, int32_t slot, double *h, double *hu, double *hv);
+
+/* Diagnostics of a live slot (synchronises). */
+int swe_batch_diagnostics(swe_batch *b, int32_t slot, swe_diag *d);
+
+/* Copy out (any pointer may be NULL) and free a slot (stream-ordered free). */
+int swe_batch_retire(swe_batch *b, int32_t slot, double *h, double *hu, double *hv, double *mass,
+                     double *runup_max);
+
+/* Device bytes in use by live slots and the budget. */
+int swe_batch_memory(swe_batch *b, size_t *used, size_t *budget);
+
+/* SWE_ETIMEOUT if a grid-barrier wait ran out in a run (the launch then
+ * ended early; slots keep their last completed stage), else SWE_OK. */
+int swe_batch_status(swe_batch *b);
+
+/* Bounded-wait settings of the grid barrier: give up after timeout_s seconds
+ * (default 1).  extra_arrivals > 0 is a test hook that makes every barrier
+ * wait for arrivals that never come, so the timeout path can be exercised;
+ * 0 for normal use.  Also clears a timeout status.  Call between runs. */
+int swe_batch_set_barrier(swe_batch *b, double timeout_s, int32_t extra_arrivals);
+
+/* Free the batch and all slots.  NULL-safe. */
+int swe_batch_destroy(swe_batch *b);
 
 /* Allocation-free water volume of a caller-owned device depth field.
  * The paper has no counterpart: this entry point exists for callers that

@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
         ("cfl", ctypes.c_double), ("t_end", ctypes.c_double), ("b_jump_x", ctypes.c_double),
         ("b_jump_y", ctypes.c_double), ("inflow_amp", ctypes.c_double),
         ("inflow_period", ctypes.c_double), ("inflow_depth", ctypes.c_double),
-        ("z_ref", ctypes.c_double), ("bc", ctypes.c_int32 * 4),
+        ("z_ref", ctypes.c_double), ("h_film", ctypes.c_double), ("bc", ctypes.c_int32 * 4),
     ]
 
 
@@ -103,6 +103,7 @@ def params_of(sc) -> Params:
     p.b_jump_x, p.b_jump_y = sc.b_jump_x, sc.b_jump_y
     p.inflow_amp, p.inflow_period, p.inflow_depth = sc.inflow_amp, sc.inflow_period, sc.inflow_depth
     p.z_ref = sc.z_ref
+    p.h_film = sc.h_film
     for k in range(4):
         p.bc[k] = int(sc.bc[k])
     return p

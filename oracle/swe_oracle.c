@@ -45,7 +45,10 @@
  *  - Wet/dry (not described in the paper): velocities are zero where
  *    h < h_dry; after every stage h < 0 is set to 0 and hu = hv = 0 where
  *    h < h_dry; the mass added by that clamp is counted with the stage's
- *    weight in the final RK combination (1/6, 2/3, 1).
+ *    weight in the final RK combination (1/6, 2/3, 1).  Films with
+ *    h_dry <= h < h_film get the velocity desingularisation of Kurganov &
+ *    Petrova (2007): u = sqrt(2) h hu / sqrt(h^4 + h_film^4), hu := h u (and
+ *    the same for v), which keeps thin-film velocities bounded.
  *  - Friction is explicit, applied only where h >= h_dry, with the rate
  *    kappa = g n^2 |q| / h^(7/3) capped at 1/dt.
  *  - Walls: ghost k mirrors interior k-1 (h, b, tangential momentum even,
@@ -82,6 +85,7 @@ typedef struct {
   double inflow_period; /* N-wave period T; lambda = T sqrt(g d0) */
   double inflow_depth;  /* offshore depth d0 */
   double z_ref;         /* still-water level: d = max(z_ref - b, 0) */
+  double h_film;        /* film depth of the velocity desingularisation */
   int32_t bc[4];        /* x-, x+, y-, y+ */
 } or_params;
 
@@ -468,7 +472,8 @@ static int operator_L(const grid_t *g, const double *b, const double *h, const d
 }
 
 /* Post-stage rule: h < 0 -> 0 (returns the added depth summed in row order),
- * then hu = hv = 0 where h < h_dry. */
+ * then hu = hv = 0 where h < h_dry, and the film desingularisation where
+ * h_dry <= h < h_film. */
 static double post_rule(const grid_t *g, double *h, double *hu, double *hv) {
   const or_params *p = g->p;
   double *rows = (double *)calloc((size_t)g->ny, sizeof(double));
@@ -484,6 +489,11 @@ static double post_rule(const grid_t *g, double *h, double *hu, double *hv) {
       if (h[c] < p->h_dry) {
         hu[c] = 0.0;
         hv[c] = 0.0;
+      } else if (h[c] < p->h_film) {
+        double h2 = h[c] * h[c];
+        double f = sqrt(2.0) * h2 / sqrt(h2 * h2 + pow(p->h_film, 4.0));
+        hu[c] *= f;
+        hv[c] *= f;
       }
     }
     if (rows) rows[j] = s;

@@ -34,8 +34,8 @@ class SweError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [
         ("g", ctypes.c_double), ("manning_n", ctypes.c_double), ("h_dry", ctypes.c_double),
-        ("h_wet", ctypes.c_double), ("weno_eps", ctypes.c_double), ("fixed_dt", ctypes.c_double),
-        ("z_ref", ctypes.c_double), ("b_jump_x", ctypes.c_double), ("b_jump_y", ctypes.c_double),
+        ("h_wet", ctypes.c_double), ("h_film", ctypes.c_double), ("weno_eps", ctypes.c_double),
+        ("fixed_dt", ctypes.c_double), ("z_ref", ctypes.c_double), ("b_jump_x", ctypes.c_double), ("b_jump_y", ctypes.c_double),
         ("inflow_amp", ctypes.c_double), ("inflow_period", ctypes.c_double), ("inflow_depth", ctypes.c_double),
         ("bc", ctypes.c_int32 * 4), ("precision", ctypes.c_int32), ("tile", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
@@ -84,6 +84,19 @@ def _load() -> ctypes.CDLL:
         "swe_tile_shape": (ip, [ip, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                 ctypes.POINTER(ctypes.c_int32)]),
         "swe_time_stages": (ip, [H, ctypes.c_int32, ctypes.c_double, dp, dp]),
+        "swe_batch_slot_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid)]),
+        "swe_batch_create": (ip, [ctypes.c_int32, ctypes.c_size_t, ctypes.POINTER(Params), ctypes.POINTER(H)]),
+        "swe_batch_admit": (ip, [H, ctypes.POINTER(Grid), ctypes.c_double, ctypes.c_double, dp, dp, dp, dp,
+                                 ctypes.c_double, ctypes.POINTER(ctypes.c_int32)]),
+        "swe_batch_run": (ip, [H, ctypes.c_int32, ctypes.c_double]),
+        "swe_batch_poll": (ip, [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+        "swe_batch_get_state": (ip, [H, ctypes.c_int32, dp, dp, dp]),
+        "swe_batch_diagnostics": (ip, [H, ctypes.c_int32, ctypes.POINTER(Diag)]),
+        "swe_batch_retire": (ip, [H, ctypes.c_int32, dp, dp, dp, dp, dp]),
+        "swe_batch_memory": (ip, [H, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+        "swe_batch_status": (ip, [H]),
+        "swe_batch_set_barrier": (ip, [H, ctypes.c_double, ctypes.c_int32]),
+        "swe_batch_destroy": (ip, [H]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -121,7 +134,7 @@ def params_for(sc, precision: int = F32, stream: Optional[int] = None, tile: int
     """swe_params from a workload description (any object with the fields)."""
     p = Params()
     lib.swe_params_default(ctypes.byref(p))
-    p.g, p.manning_n, p.h_dry, p.h_wet = sc.g, sc.manning_n, sc.h_dry, sc.h_wet
+    p.g, p.manning_n, p.h_dry, p.h_wet, p.h_film = sc.g, sc.manning_n, sc.h_dry, sc.h_wet, sc.h_film
     p.weno_eps, p.fixed_dt, p.z_ref = sc.weno_eps, sc.fixed_dt, sc.z_ref
     p.b_jump_x, p.b_jump_y = sc.b_jump_x, sc.b_jump_y
     p.inflow_amp, p.inflow_period, p.inflow_depth = sc.inflow_amp, sc.inflow_period, sc.inflow_depth
@@ -239,3 +252,104 @@ class Solver:
         st = (ctypes.c_double * 3)()
         _check(lib.swe_time_stages(self._h, int(n), float(c), ctypes.byref(tot), st), "swe_time_stages")
         return tot.value, (st[0], st[1], st[2])
+
+
+def _diag_dict(d: Diag) -> Dict[str, float]:
+    return dict(t=d.t, steps=int(d.steps), last_dt=d.last_dt, alpha_x=d.alpha_x, alpha_y=d.alpha_y,
+                clamp_mass=d.clamp_mass, boundary_mass=d.boundary_mass, runup_now=d.runup_now,
+                runup_max=d.runup_max, status=int(d.status), tile=int(d.tile))
+
+
+def slot_bytes(nx: int, ny: int) -> int:
+    """Device bytes one batch admission of an nx x ny grid takes."""
+    return int(lib.swe_batch_slot_bytes(ctypes.byref(Grid(nx, ny))))
+
+
+class Batch:
+    """Independent scenarios advanced together by one persistent launch per
+    run (the ensemble and serving path, FP32)."""
+
+    def __init__(self, nslots: int, budget_bytes: int, template, stream: Optional[int] = None, tile: int = 0):
+        self._b = ctypes.c_void_p()
+        self.nslots = int(nslots)
+        self.params = params_for(template, F32, stream, tile)
+        _check(lib.swe_batch_create(self.nslots, int(budget_bytes), ctypes.byref(self.params), ctypes.byref(self._b)),
+               "swe_batch_create")
+        self.shapes: Dict[int, Tuple[int, int]] = {}
+
+    def close(self) -> None:
+        if self._b:
+            lib.swe_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def admit(self, sc, t_end: Optional[float] = None) -> int:
+        """Admit a scenario; raises SweError (EBUDGET / EFULL) if it does not fit."""
+        arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (sc.b, sc.h, sc.hu, sc.hv)]
+        slot = ctypes.c_int32(-1)
+        te = sc.t_end if t_end is None else t_end
+        _check(lib.swe_batch_admit(self._b, ctypes.byref(Grid(sc.nx, sc.ny)), float(sc.dx), float(sc.dy),
+                                   *[_dp(a) for a in arrs], float(te), ctypes.byref(slot)), "swe_batch_admit")
+        self.shapes[slot.value] = (sc.ny, sc.nx)
+        return slot.value
+
+    def try_admit(self, sc, t_end: Optional[float] = None) -> Optional[int]:
+        try:
+            return self.admit(sc, t_end)
+        except SweError as e:
+            if e.code in (EBUDGET, EFULL):
+                return None
+            raise
+
+    def run(self, k: int, cfl: float = 0.4) -> None:
+        _check(lib.swe_batch_run(self._b, int(k), float(cfl)), "swe_batch_run")
+
+    def poll(self):
+        out = (ctypes.c_int32 * self.nslots)()
+        n = ctypes.c_int32()
+        _check(lib.swe_batch_poll(self._b, out, ctypes.byref(n)), "swe_batch_poll")
+        return [out[k] for k in range(n.value)]
+
+    def status(self) -> int:
+        return int(lib.swe_batch_status(self._b))
+
+    def get_state(self, slot: int):
+        ny, nx = self.shapes[slot]
+        out = tuple(np.empty((ny, nx)) for _ in range(3))
+        _check(lib.swe_batch_get_state(self._b, int(slot), *[_dp(x) for x in out]), "swe_batch_get_state")
+        return out
+
+    def diagnostics(self, slot: int, check: bool = True) -> Dict[str, float]:
+        d = Diag()
+        rc = lib.swe_batch_diagnostics(self._b, int(slot), ctypes.byref(d))
+        if check:
+            _check(rc, "swe_batch_diagnostics")
+        return _diag_dict(d)
+
+    def retire(self, slot: int, want_state: bool = True):
+        ny, nx = self.shapes[slot]
+        st = tuple(np.empty((ny, nx)) for _ in range(3)) if want_state else None
+        m, r = ctypes.c_double(), ctypes.c_double()
+        ptrs = [_dp(x) for x in st] if st else [None, None, None]
+        _check(lib.swe_batch_retire(self._b, int(slot), *ptrs, ctypes.byref(m), ctypes.byref(r)), "swe_batch_retire")
+        del self.shapes[slot]
+        return st, m.value, r.value
+
+    def memory(self) -> Tuple[int, int]:
+        u, b = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib.swe_batch_memory(self._b, ctypes.byref(u), ctypes.byref(b)), "swe_batch_memory")
+        return u.value, b.value
+
+    def set_barrier(self, timeout_s: float, extra_arrivals: int = 0) -> None:
+        _check(lib.swe_batch_set_barrier(self._b, float(timeout_s), int(extra_arrivals)), "swe_batch_set_barrier")

@@ -25,7 +25,10 @@ UNITS: List[Tuple[str, List[str], str]] = [
     ("swe_kernels.cu", ["-DSWE_PREC=32"], "swe_kernels_f32.o"),
     ("swe_kernels.cu", ["-DSWE_PREC=64"], "swe_kernels_f64.o"),
     ("swe_api.cu", [], "swe_api.o"),
+    ("swe_aux.cu", [], "swe_aux.o"),
     ("swe_noalloc.cu", [], "swe_noalloc.o"),
+    ("swe_batch_kernels.cu", [], "swe_batch_kernels.o"),
+    ("swe_batch.cu", [], "swe_batch.o"),
 ]
 
 

@@ -12,154 +12,8 @@
 
 using namespace swe;
 
-namespace {
 
-// ---------------------------------------------------------------- kernels
-// Host-format FP64 [ny][nx] -> pitched planes.  With bed != nullptr the
-// field is a depth h stored as the anomaly ha = h - max(z_ref - b, 0).
-template <typename T, typename S>
-__global__ void k_import(const S *__restrict__ src, T *__restrict__ dst, const T *__restrict__ bed, double zref,
-                         int nx, int ny, int pitch) {
-  const size_t n = (size_t)nx * ny;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = q / nx, i = q - j * nx;
-    double v = (double)src[q];
-    if (bed) v -= fmax(zref - (double)bed[j * pitch + i], 0.0);
-    dst[j * pitch + i] = (T)v;
-  }
-}
-
-// Pitched planes -> contiguous [ny][nx]; with bed != nullptr, h = ha + d.
-template <typename T, typename S>
-__global__ void k_export(const T *__restrict__ src, S *__restrict__ dst, const T *__restrict__ bed, double zref,
-                         int nx, int ny, int pitch) {
-  const size_t n = (size_t)nx * ny;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = q / nx, i = q - j * nx;
-    double v = (double)src[j * pitch + i];
-    if (bed) v += fmax(zref - (double)bed[j * pitch + i], 0.0);
-    dst[q] = (S)v;
-  }
-}
-
-__global__ void k_set_cfl(DevScalars *sc, double cfl) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) sc->cfl = cfl;
-}
-
-__global__ void k_reset(DevScalars *sc, double t, double cfl, double t_end) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    for (int s = 0; s < 3; ++s) sc->alpha[s][0] = sc->alpha[s][1] = 0ull;
-    sc->dt = 0.0;
-    sc->t = t;
-    sc->t_step = t;
-    sc->steps = 0;
-    sc->runup_now[0] = sc->runup_now[1] = 0ull;
-    sc->runup_max = 0ull;
-    sc->clamp_mass = 0.0;
-    sc->boundary_mass = 0.0;
-    sc->t_end = t_end;
-    sc->cfl = cfl;
-    sc->status = 0u;
-    sc->running = 0u;
-    sc->parity = 1u;  // runup_now of "step -1" lives at parity 1 (steps = 0 -> next writes parity 0)
-    sc->active = 1u;
-  }
-}
-
-// Wave speeds (slot 0) and runup of the current state U^n, with the same
-// in-precision arithmetic as the stage epilogue (so that a state written out
-// and set again gives the same time step as an uninterrupted run).
-template <typename T>
-__global__ void k_state_stats(Field<T> fd, Phys p, DevScalars *sc) {
-  __shared__ double sm[32][3];
-  __shared__ unsigned sbad;
-  if (threadIdx.x == 0) sbad = 0u;
-  __syncthreads();
-  T mx = T(0), my = T(0), ru = T(0);
-  bool bad = false;
-  const T g = T(p.g);
-  const size_t n = (size_t)fd.nx * fd.ny;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = q / fd.nx, i = q - j * fd.nx;
-    const size_t o = j * fd.pitch + i;
-    const T b = fd.b[o];
-    const T h = fd.h[0][o] + still_depth(b, T(p.z_ref)), hu = fd.hu[0][o], hv = fd.hv[0][o];
-    if (!(fabs(h) <= T(3.0e38)) || !(fabs(hu) <= T(3.0e38)) || !(fabs(hv) <= T(3.0e38))) { bad = true; continue; }
-    T u = T(0), v = T(0);
-    if (!Num<T>::below(h, p.h_dry32, p.h_dry)) { const T rr = Num<T>::rcp(h); u = hu * rr; v = hv * rr; }
-    const T cel = Num<T>::sqrt_(g * (h > T(0) ? h : T(0)));
-    const T sx = fabs(u) + cel, sy = fabs(v) + cel;
-    mx = sx > mx ? sx : mx;
-    my = sy > my ? sy : my;
-    if (!Num<T>::below(h, p.h_wet32, p.h_wet) && b > T(0)) { const T e = h + b; ru = e > ru ? e : ru; }
-  }
-  mx = warp_max(mx);
-  my = warp_max(my);
-  ru = warp_max(ru);
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) sbad = 1u;
-  if ((threadIdx.x & 31) == 0) {
-    sm[threadIdx.x >> 5][0] = (double)mx;
-    sm[threadIdx.x >> 5][1] = (double)my;
-    sm[threadIdx.x >> 5][2] = (double)ru;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = sm[0][0], b = sm[0][1], r = sm[0][2];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      a = fmax(a, sm[w][0]);
-      b = fmax(b, sm[w][1]);
-      r = fmax(r, sm[w][2]);
-    }
-    atomicMax(&sc->alpha[0][0], (unsigned long long)__double_as_longlong(a));
-    atomicMax(&sc->alpha[0][1], (unsigned long long)__double_as_longlong(b));
-    if (r > 0.0) {
-      atomicMax(&sc->runup_now[1], (unsigned long long)__double_as_longlong(r));
-      atomicMax(&sc->runup_max, (unsigned long long)__double_as_longlong(r));
-    }
-    if (sbad) atomicOr(&sc->status, ST_NONFINITE);
-  }
-}
-
-// Mass, pass 1: per-block FP64 partial sums of h over rows, fixed order.
-template <typename T>
-__global__ void k_mass_partial(const T *__restrict__ ha, const T *__restrict__ bed, double zref, int nx, int ny,
-                               int pitch, double *__restrict__ part) {
-  __shared__ double sm[32];
-  double s = 0.0;
-  const size_t n = (size_t)nx * ny;
-  const size_t per = (n + gridDim.x - 1) / gridDim.x;
-  const size_t lo = blockIdx.x * per, hi = lo + per < n ? lo + per : n;
-  for (size_t q = lo + threadIdx.x; q < hi; q += blockDim.x) {
-    const size_t j = q / nx, i = q - j * nx;
-    const size_t o = j * pitch + i;
-    s += (double)ha[o] + fmax(zref - (double)bed[o], 0.0);
-  }
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
-    part[blockIdx.x] = t;
-  }
-}
-
-// Mass, pass 2: one block sums the partials in a fixed tree order.
-__global__ void k_mass_final(const double *__restrict__ part, int n, double area, double *__restrict__ out) {
-  __shared__ double sm[1024];
-  double s = 0.0;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) s += part[q];
-  sm[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = sm[0] * area;
-}
-
-constexpr int kMassBlocks = 1024;
-
+namespace swe {
 float thr32(double thr) {
   // smallest float f with (double)f >= thr: comparing h < f in FP32 is the
   // same predicate as (double)h < thr
@@ -168,8 +22,7 @@ float thr32(double thr) {
   while ((double)std::nextafter(f, -INFINITY) >= thr) f = std::nextafter(f, -INFINITY);
   return f;
 }
-
-}  // namespace
+}  // namespace swe
 
 struct swe_handle {
   int nx = 0, ny = 0, pitch = 0;
@@ -220,12 +73,6 @@ Field<T> field_of(const swe_handle *s) {
   return f;
 }
 
-int grid_blocks(size_t n, int threads) {
-  size_t b = (n + threads - 1) / threads;
-  if (b > 4096) b = 4096;
-  return (int)(b < 1 ? 1 : b);
-}
-
 cudaError_t enqueue_step(swe_handle *s, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
@@ -252,46 +99,41 @@ int upload_field(swe_handle *s, const double *src, void *dst, bool is_depth) {
   cudaError_t e = cudaMemcpyAsync(s->staging, src, sizeof(double) * (size_t)s->nx * s->ny, cudaMemcpyHostToDevice,
                                   s->stream);
   if (e != cudaSuccess) return cuda_check(s, e);
-  const size_t n = (size_t)s->nx * s->ny;
-  const int nb = grid_blocks(n, 256);
   if (s->prec == SWE_F64)
-    k_import<double, double><<<nb, 256, 0, s->stream>>>(s->staging, (double *)dst, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
+    e = import_plane<double>(s->staging, true, (double *)dst, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
   else
-    k_import<float, double><<<nb, 256, 0, s->stream>>>(s->staging, (float *)dst, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
-  return cuda_check(s, cudaGetLastError());
+    e = import_plane<float>(s->staging, true, (float *)dst, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
+  return cuda_check(s, e);
 }
 
 int download_field(swe_handle *s, const void *src, double *dst, bool is_depth) {
-  const size_t n = (size_t)s->nx * s->ny;
-  const int nb = grid_blocks(n, 256);
+  cudaError_t e;
   if (s->prec == SWE_F64)
-    k_export<double, double><<<nb, 256, 0, s->stream>>>((const double *)src, s->staging, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
+    e = export_plane<double>((const double *)src, s->staging, true, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
   else
-    k_export<float, double><<<nb, 256, 0, s->stream>>>((const float *)src, s->staging, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, s->staging, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream);
+    e = export_plane<float>((const float *)src, s->staging, true, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dst, s->staging, sizeof(double) * (size_t)s->nx * s->ny, cudaMemcpyDeviceToHost, s->stream);
   return cuda_check(s, e);
 }
 
 // Caller device arrays (handle precision, contiguous) <-> planes.
 int import_device(swe_handle *s, const void *src, void *dst, bool is_depth) {
-  const size_t n = (size_t)s->nx * s->ny;
-  const int nb = grid_blocks(n, 256);
+  cudaError_t e;
   if (s->prec == SWE_F64)
-    k_import<double, double><<<nb, 256, 0, s->stream>>>((const double *)src, (double *)dst, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
+    e = import_plane<double>(src, false, (double *)dst, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
   else
-    k_import<float, float><<<nb, 256, 0, s->stream>>>((const float *)src, (float *)dst, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
-  return cuda_check(s, cudaGetLastError());
+    e = import_plane<float>(src, false, (float *)dst, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
+  return cuda_check(s, e);
 }
 
 int export_device(swe_handle *s, const void *src, void *dst, bool is_depth) {
-  const size_t n = (size_t)s->nx * s->ny;
-  const int nb = grid_blocks(n, 256);
+  cudaError_t e;
   if (s->prec == SWE_F64)
-    k_export<double, double><<<nb, 256, 0, s->stream>>>((const double *)src, (double *)dst, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
+    e = export_plane<double>((const double *)src, dst, false, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
   else
-    k_export<float, float><<<nb, 256, 0, s->stream>>>((const float *)src, (float *)dst, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch);
-  return cuda_check(s, cudaGetLastError());
+    e = export_plane<float>((const float *)src, dst, false, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
+  return cuda_check(s, e);
 }
 
 int after_state_change(swe_handle *s) {
@@ -300,11 +142,10 @@ int after_state_change(swe_handle *s) {
   cudaError_t e = cudaMemcpyAsync(&t, &s->sc->t, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_check(s, e);
-  k_reset<<<1, 32, 0, s->stream>>>(s->sc, t, s->cfl_dev > 0 ? s->cfl_dev : 0.4, 0.0);
-  const size_t n = (size_t)s->nx * s->ny;
-  if (s->prec == SWE_F64) k_state_stats<double><<<grid_blocks(n, 256), 256, 0, s->stream>>>(field_of<double>(s), s->phys, s->sc);
-  else k_state_stats<float><<<grid_blocks(n, 256), 256, 0, s->stream>>>(field_of<float>(s), s->phys, s->sc);
-  e = cudaGetLastError();
+  e = reset_scalars(s->sc, t, s->cfl_dev > 0 ? s->cfl_dev : 0.4, 0.0, s->stream);
+  if (e == cudaSuccess)
+    e = s->prec == SWE_F64 ? state_stats<double>(field_of<double>(s), s->phys, s->sc, s->stream)
+                           : state_stats<float>(field_of<float>(s), s->phys, s->sc, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (s->cfl_dev <= 0) s->cfl_dev = 0.4;
   return cuda_check(s, e);
@@ -319,7 +160,8 @@ bool valid_params(const swe_params *p) {
   if ((p->bc[2] == SWE_BC_PERIODIC) != (p->bc[3] == SWE_BC_PERIODIC)) return false;
   if (p->bc[1] == SWE_BC_INFLOW || p->bc[2] == SWE_BC_INFLOW || p->bc[3] == SWE_BC_INFLOW) return false;
   if (p->bc[0] == SWE_BC_INFLOW && !(p->inflow_depth > 0.0 && p->inflow_period > 0.0)) return false;
-  if (!(p->g > 0.0) || !(p->manning_n >= 0.0) || !(p->h_dry >= 0.0) || !(p->h_wet >= 0.0) || !(p->weno_eps > 0.0))
+  if (!(p->g > 0.0) || !(p->manning_n >= 0.0) || !(p->h_dry >= 0.0) || !(p->h_wet >= 0.0) || !(p->h_film >= 0.0) ||
+      !(p->weno_eps > 0.0))
     return false;
   if (!std::isfinite(p->z_ref) || !std::isfinite(p->fixed_dt)) return false;
   if (p->tile < 0 || p->tile > num_shapes()) return false;
@@ -337,6 +179,7 @@ void swe_params_default(swe_params *p) {
   p->manning_n = 0.0;
   p->h_dry = 1e-5;
   p->h_wet = 1e-3;
+  p->h_film = 1e-3;
   p->weno_eps = 1e-6;
   p->fixed_dt = 0.0;
   p->z_ref = 0.0;
@@ -396,6 +239,9 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   ph.n2 = params->manning_n * params->manning_n;
   ph.h_dry = params->h_dry;
   ph.h_wet = params->h_wet;
+  ph.h_film = params->h_film;
+  ph.hf4 = params->h_film * params->h_film * params->h_film * params->h_film;
+  ph.h_film32 = thr32(params->h_film);
   ph.weno_eps = params->weno_eps;
   ph.fixed_dt = params->fixed_dt;
   ph.z_ref = params->z_ref;
@@ -451,10 +297,7 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
     rc = cuda_check(s, e);
   }
   if (rc == SWE_OK) rc = cuda_check(s, cudaMemsetAsync(s->mem, 0, plane_al * 10, s->stream));
-  if (rc == SWE_OK) {
-    k_reset<<<1, 32, 0, s->stream>>>(s->sc, 0.0, 0.4, 0.0);
-    rc = cuda_check(s, cudaGetLastError());
-  }
+  if (rc == SWE_OK) rc = cuda_check(s, reset_scalars(s->sc, 0.0, 0.4, 0.0, s->stream));
   if (rc == SWE_OK) rc = upload_field(s, bathymetry, s->b, false);
   if (rc == SWE_OK) rc = cuda_check(s, cudaStreamSynchronize(s->stream));
   if (rc != SWE_OK) {
@@ -491,8 +334,7 @@ int swe_step(swe_handle *s, int32_t n, double cfl) {
   cudaError_t e = cudaSuccess;
   if (s->prm.fixed_dt <= 0.0 && cfl != s->cfl_dev) {
     // ordered on the stream before the steps; the captured graph reads it
-    k_set_cfl<<<1, 32, 0, s->stream>>>(s->sc, cfl);
-    e = cudaGetLastError();
+    e = set_cfl(s->sc, cfl, s->stream);
     if (e != cudaSuccess) return cuda_check(s, e);
     s->cfl_dev = cfl;
   }
@@ -552,12 +394,10 @@ int swe_get_state_device(swe_handle *s, void *h, void *hu, void *hv) {
 
 int swe_mass(swe_handle *s, double *mass, double *clamp_mass) {
   if (!s) return SWE_EINVAL;
-  if (s->prec == SWE_F64)
-    k_mass_partial<double><<<kMassBlocks, 256, 0, s->stream>>>((const double *)s->h[0], (const double *)s->b, s->phys.z_ref, s->nx, s->ny, s->pitch, s->partials);
-  else
-    k_mass_partial<float><<<kMassBlocks, 256, 0, s->stream>>>((const float *)s->h[0], (const float *)s->b, s->phys.z_ref, s->nx, s->ny, s->pitch, s->partials);
-  k_mass_final<<<1, 1024, 0, s->stream>>>(s->partials, kMassBlocks, s->dx * s->dy, s->partials + kMassBlocks);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e =
+      s->prec == SWE_F64
+          ? swe::mass<double>((const double *)s->h[0], (const double *)s->b, s->phys.z_ref, s->nx, s->ny, s->pitch, s->dx * s->dy, s->partials, s->partials + kMassBlocks, s->stream)
+          : swe::mass<float>((const float *)s->h[0], (const float *)s->b, s->phys.z_ref, s->nx, s->ny, s->pitch, s->dx * s->dy, s->partials, s->partials + kMassBlocks, s->stream);
   double r[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&r[0], s->partials + kMassBlocks, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&r[1], &s->sc->clamp_mass, sizeof(double), cudaMemcpyDeviceToHost, s->stream);

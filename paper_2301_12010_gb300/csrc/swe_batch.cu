@@ -1,0 +1,403 @@
+// swe_batch.cu -- C ABI of the batched ensemble / serving path
+// (include/swe.h, swe_batch_*): slots admitted under an HBM budget, a slot
+// table in device memory, and k-step cooperative persistent launches replayed
+// from CUDA graphs.  Scenarios are independent (scenario-level data
+// parallelism); each keeps its own wave speeds, time step, time and step
+// count in device memory, so a scenario's result does not depend on what
+// else is in the batch.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/swe.h"
+#include "swe_batch.h"
+
+using namespace swe;
+
+namespace {
+
+struct Slot {
+  bool live = false;
+  int nx = 0, ny = 0, pitch = 0;
+  double dx = 0, dy = 0, t_end = 0;
+  size_t bytes = 0;
+  void *mem = nullptr;
+  double *staging = nullptr;
+  Field<float> fd{};
+  Phys p{};
+};
+
+size_t plane_bytes(int nx, int ny, int *pitch_out) {
+  const int pitch = ((nx + 31) / 32) * 32;
+  if (pitch_out) *pitch_out = pitch;
+  return (((size_t)pitch * ny * sizeof(float)) + 255) & ~(size_t)255;
+}
+
+size_t slot_bytes(int nx, int ny) {
+  const size_t plane = plane_bytes(nx, ny, nullptr);
+  const size_t stag = ((sizeof(double) * (size_t)nx * ny) + 255) & ~(size_t)255;
+  return plane * 10 + stag;
+}
+
+}  // namespace
+
+struct swe_batch {
+  int nslots = 0;
+  size_t budget = 0, used = 0;
+  swe_params prm{};
+  int tile = 1;
+  int grid = 0;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  std::vector<Slot> slots;
+  DevScalars *d_sc = nullptr;          // one per slot
+  BatchSlot<float> *d_table = nullptr; // live slots, work-list order
+  BatchCtl *d_ctl = nullptr;
+  double *d_part = nullptr;            // mass partials + result
+  std::map<int, cudaGraphExec_t> graphs;
+  double timeout_s = 1.0;
+  unsigned extra = 0;
+  int sticky = SWE_OK;
+};
+
+namespace {
+
+int bfail(swe_batch *b, cudaError_t e) {
+  if (e == cudaSuccess) return SWE_OK;
+  (void)cudaGetLastError();
+  const int code = e == cudaErrorMemoryAllocation ? SWE_ENOMEM : SWE_ECUDA;
+  if (b && b->sticky == SWE_OK) b->sticky = code;
+  return code;
+}
+
+Phys phys_of(const swe_params &q, double dx, double dy) {
+  Phys ph{};
+  ph.g = q.g;
+  ph.n2 = q.manning_n * q.manning_n;
+  ph.h_dry = q.h_dry;
+  ph.h_wet = q.h_wet;
+  ph.h_film = q.h_film;
+  ph.hf4 = q.h_film * q.h_film * q.h_film * q.h_film;
+  ph.h_film32 = thr32(q.h_film);
+  ph.weno_eps = q.weno_eps;
+  ph.fixed_dt = q.fixed_dt;
+  ph.z_ref = q.z_ref;
+  ph.b_jump_x = q.b_jump_x;
+  ph.b_jump_y = q.b_jump_y;
+  ph.inflow_amp = q.inflow_amp;
+  ph.inflow_period = q.inflow_period;
+  ph.inflow_depth = q.inflow_depth;
+  ph.dx = dx;
+  ph.dy = dy;
+  ph.h_dry32 = thr32(q.h_dry);
+  ph.h_wet32 = thr32(q.h_wet);
+  for (int k = 0; k < 4; ++k) ph.bc[k] = q.bc[k];
+  return ph;
+}
+
+// Rebuild the work list (live slots in index order) and the control block.
+int upload_table(swe_batch *b) {
+  std::vector<BatchSlot<float>> tab;
+  int total = 0;
+  const TileShape *ts = shape(b->tile);
+  for (int s = 0; s < b->nslots; ++s) {
+    const Slot &sl = b->slots[s];
+    if (!sl.live) continue;
+    BatchSlot<float> e{};
+    e.fd = sl.fd;
+    e.p = sl.p;
+    e.sc = b->d_sc + s;
+    e.tiles_x = (sl.nx + ts->tx - 1) / ts->tx;
+    e.ntiles = e.tiles_x * ((sl.ny + ts->ty - 1) / ts->ty);
+    e.first_item = total;
+    total += e.ntiles;
+    tab.push_back(e);
+  }
+  BatchCtl c{};
+  c.nslots = (int)tab.size();
+  c.total_items = total;
+  c.bar_count = 0;
+  c.bar_gen = 0;
+  c.status = 0;
+  c.bar_extra = b->extra;
+  c.bar_cycles = (long long)(b->timeout_s * 2.2e9);  // SM clock at most ~2.1 GHz
+  cudaError_t e = cudaSuccess;
+  if (!tab.empty())
+    e = cudaMemcpyAsync(b->d_table, tab.data(), sizeof(BatchSlot<float>) * tab.size(), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return bfail(b, e);
+}
+
+bool valid_slot(const swe_batch *b, int32_t s) { return b && s >= 0 && s < b->nslots && b->slots[s].live; }
+
+}  // namespace
+
+extern "C" {
+
+size_t swe_batch_slot_bytes(const swe_grid *grid) {
+  if (!grid || grid->nx < 3 || grid->ny < 3) return 0;
+  return slot_bytes(grid->nx, grid->ny);
+}
+
+int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *params, swe_batch **out) {
+  if (out) *out = nullptr;
+  if (!out || !params || nslots < 1 || nslots > 4096 || hbm_budget_bytes == 0) return SWE_EINVAL;
+  if (params->precision != SWE_F32) return SWE_EINVAL;  // the batch path is FP32
+  for (int k = 0; k < 4; ++k)
+    if (params->bc[k] != SWE_BC_WALL) return SWE_EINVAL;  // ensembles and requests are walled coasts
+  if (params->tile < 0 || params->tile > num_shapes()) return SWE_EINVAL;
+  if (!(params->g > 0.0) || !(params->weno_eps > 0.0) || !(params->h_dry >= 0.0) || !(params->manning_n >= 0.0))
+    return SWE_EINVAL;
+  swe_batch *b = new (std::nothrow) swe_batch();
+  if (!b) return SWE_ENOMEM;
+  b->nslots = nslots;
+  b->budget = hbm_budget_bytes;
+  b->prm = *params;
+  b->tile = params->tile > 0 ? params->tile : 1;
+  b->stream = (cudaStream_t)params->stream;
+  b->slots.resize(nslots);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_sc, sizeof(DevScalars) * nslots);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_table, sizeof(BatchSlot<float>) * nslots);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_part, sizeof(double) * (kMassBlocks + 1));
+  int per_sm = 0, dev = 0, sms = 0;
+  if (e == cudaSuccess) e = batch_resident(b->tile, &per_sm);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+  if (e != cudaSuccess) {
+    int rc = bfail(b, e);
+    swe_batch_destroy(b);
+    return rc;
+  }
+  b->grid = per_sm * sms;
+  int rc = upload_table(b);
+  if (rc != SWE_OK) {
+    swe_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return SWE_OK;
+}
+
+int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, const double *bathymetry,
+                    const double *h, const double *hu, const double *hv, double t_end, int32_t *slot) {
+  if (slot) *slot = -1;
+  if (!b || !grid || !bathymetry || !h || !hu || !hv || !slot) return SWE_EINVAL;
+  if (grid->nx < 3 || grid->ny < 3 || !(dx > 0.0) || !(dy > 0.0) || !(t_end > 0.0)) return SWE_EINVAL;
+  if ((long long)grid->nx * grid->ny > (1ll << 31)) return SWE_EINVAL;
+  const size_t need = slot_bytes(grid->nx, grid->ny);
+  if (b->used + need > b->budget) return SWE_EBUDGET;
+  int s = -1;
+  for (int k = 0; k < b->nslots; ++k)
+    if (!b->slots[k].live) { s = k; break; }
+  if (s < 0) return SWE_EFULL;
+  Slot &sl = b->slots[s];
+  sl = Slot();
+  sl.nx = grid->nx;
+  sl.ny = grid->ny;
+  sl.dx = dx;
+  sl.dy = dy;
+  sl.t_end = t_end;
+  const size_t plane = plane_bytes(sl.nx, sl.ny, &sl.pitch);
+  cudaError_t e = cudaMallocAsync(&sl.mem, need, b->stream);
+  if (e != cudaSuccess) return bfail(b, e);
+  char *q = (char *)sl.mem;
+  sl.fd.b = (const float *)q;
+  float *bplane = (float *)q;
+  q += plane;
+  for (int k = 0; k < 3; ++k) {
+    sl.fd.h[k] = (float *)q; q += plane;
+    sl.fd.hu[k] = (float *)q; q += plane;
+    sl.fd.hv[k] = (float *)q; q += plane;
+  }
+  sl.staging = (double *)q;
+  sl.fd.nx = sl.nx;
+  sl.fd.ny = sl.ny;
+  sl.fd.pitch = sl.pitch;
+  sl.p = phys_of(b->prm, dx, dy);
+  const size_t nb = sizeof(double) * (size_t)sl.nx * sl.ny;
+  const double zr = sl.p.z_ref;
+  e = cudaMemsetAsync(sl.mem, 0, plane * 10, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sl.staging, bathymetry, nb, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = import_plane<float>(sl.staging, true, bplane, nullptr, zr, sl.nx, sl.ny, sl.pitch, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sl.staging, h, nb, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = import_plane<float>(sl.staging, true, sl.fd.h[0], bplane, zr, sl.nx, sl.ny, sl.pitch, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sl.staging, hu, nb, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = import_plane<float>(sl.staging, true, sl.fd.hu[0], nullptr, zr, sl.nx, sl.ny, sl.pitch, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sl.staging, hv, nb, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = import_plane<float>(sl.staging, true, sl.fd.hv[0], nullptr, zr, sl.nx, sl.ny, sl.pitch, b->stream);
+  if (e == cudaSuccess) e = reset_scalars(b->d_sc + s, 0.0, 0.4, t_end, b->stream);
+  if (e == cudaSuccess) e = state_stats<float>(sl.fd, sl.p, b->d_sc + s, b->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(sl.mem, b->stream);
+    sl = Slot();
+    return bfail(b, e);
+  }
+  sl.live = true;
+  sl.bytes = need;
+  b->used += need;
+  const int rc = upload_table(b);
+  if (rc != SWE_OK) return rc;
+  *slot = s;
+  return SWE_OK;
+}
+
+int swe_batch_run(swe_batch *b, int32_t k_steps, double cfl) {
+  if (!b || k_steps < 0 || !(cfl > 0.0)) return SWE_EINVAL;
+  if (b->sticky != SWE_OK) return b->sticky;
+  if (k_steps == 0) return SWE_OK;
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < b->nslots && e == cudaSuccess; ++s)
+    if (b->slots[s].live) e = set_cfl(b->d_sc + s, cfl, b->stream);
+  if (e != cudaSuccess) return bfail(b, e);
+  auto it = b->graphs.find(k_steps);
+  if (it == b->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t le = cudaMemsetAsync(&b->d_ctl->bar_count, 0, sizeof(unsigned), b->cap);
+      if (le == cudaSuccess) le = batch_launch(b->tile, b->d_table, b->d_ctl, k_steps, b->grid, b->cap);
+      e = cudaStreamEndCapture(b->cap, &g);
+      if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, e);
+    it = b->graphs.emplace(k_steps, ex).first;
+  }
+  e = cudaGraphLaunch(it->second, b->stream);
+  return bfail(b, e);
+}
+
+int swe_batch_status(swe_batch *b) {
+  if (!b) return SWE_EINVAL;
+  if (b->sticky != SWE_OK) return b->sticky;
+  BatchCtl c;
+  cudaError_t e = cudaMemcpyAsync(&c, b->d_ctl, sizeof(c), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, e);
+  return (c.status & ST_TIMEOUT) ? SWE_ETIMEOUT : SWE_OK;
+}
+
+int swe_batch_poll(swe_batch *b, int32_t *done_slots, int32_t *ndone) {
+  if (!b || !ndone) return SWE_EINVAL;
+  *ndone = 0;
+  std::vector<DevScalars> h(b->nslots);
+  cudaError_t e = cudaMemcpyAsync(h.data(), b->d_sc, sizeof(DevScalars) * b->nslots, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, e);
+  int n = 0;
+  for (int s = 0; s < b->nslots; ++s) {
+    if (!b->slots[s].live) continue;
+    if (h[s].t >= b->slots[s].t_end || h[s].status != 0u) {
+      if (done_slots) done_slots[n] = s;
+      ++n;
+    }
+  }
+  *ndone = n;
+  return swe_batch_status(b);
+}
+
+int swe_batch_diagnostics(swe_batch *b, int32_t slot, swe_diag *d) {
+  if (!valid_slot(b, slot) || !d) return SWE_EINVAL;
+  DevScalars h;
+  cudaError_t e = cudaMemcpyAsync(&h, b->d_sc + slot, sizeof(h), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, e);
+  auto dbl = [](unsigned long long u) { double x; std::memcpy(&x, &u, 8); return x; };
+  d->t = h.t;
+  d->steps = h.steps;
+  d->last_dt = h.dt;
+  d->alpha_x = dbl(h.alpha[0][0]);
+  d->alpha_y = dbl(h.alpha[0][1]);
+  d->clamp_mass = h.clamp_mass;
+  d->boundary_mass = h.boundary_mass;
+  const unsigned long long rn = h.runup_now[(h.steps + 1) & 1];
+  d->runup_now = rn ? dbl(rn) : -INFINITY;
+  d->runup_max = h.runup_max ? dbl(h.runup_max) : -INFINITY;
+  d->tile = b->tile;
+  d->status = (h.status & ST_NONFINITE) ? SWE_ENONFINITE : ((h.status & ST_DRY) ? SWE_EINVAL : SWE_OK);
+  const int bs = swe_batch_status(b);
+  if (bs != SWE_OK) d->status = bs;
+  return d->status;
+}
+
+int swe_batch_get_state(swe_batch *b, int32_t slot, double *h, double *hu, double *hv) {
+  if (!valid_slot(b, slot) || !h || !hu || !hv) return SWE_EINVAL;
+  Slot &sl = b->slots[slot];
+  const size_t nb = sizeof(double) * (size_t)sl.nx * sl.ny;
+  double *dst[3] = {h, hu, hv};
+  const float *src[3] = {sl.fd.h[0], sl.fd.hu[0], sl.fd.hv[0]};
+  cudaError_t e = cudaSuccess;
+  for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
+    e = export_plane<float>(src[f], sl.staging, true, f == 0 ? sl.fd.b : nullptr, sl.p.z_ref, sl.nx, sl.ny, sl.pitch,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst[f], sl.staging, nb, cudaMemcpyDeviceToHost, b->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return bfail(b, e);
+}
+
+int swe_batch_retire(swe_batch *b, int32_t slot, double *h, double *hu, double *hv, double *mass, double *runup_max) {
+  if (!valid_slot(b, slot)) return SWE_EINVAL;
+  Slot &sl = b->slots[slot];
+  int rc = SWE_OK;
+  if (h && hu && hv) rc = swe_batch_get_state(b, slot, h, hu, hv);
+  if (rc == SWE_OK && mass) {
+    cudaError_t e = swe::mass<float>(sl.fd.h[0], sl.fd.b, sl.p.z_ref, sl.nx, sl.ny, sl.pitch, sl.dx * sl.dy,
+                                     b->d_part, b->d_part + kMassBlocks, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mass, b->d_part + kMassBlocks, sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    rc = bfail(b, e);
+  }
+  if (rc == SWE_OK && runup_max) {
+    swe_diag d;
+    swe_batch_diagnostics(b, slot, &d);
+    *runup_max = d.runup_max;
+  }
+  if (rc != SWE_OK) return rc;
+  cudaError_t e = cudaFreeAsync(sl.mem, b->stream);
+  b->used -= sl.bytes;
+  sl = Slot();
+  if (e != cudaSuccess) return bfail(b, e);
+  return upload_table(b);
+}
+
+int swe_batch_memory(swe_batch *b, size_t *used, size_t *budget) {
+  if (!b) return SWE_EINVAL;
+  if (used) *used = b->used;
+  if (budget) *budget = b->budget;
+  return SWE_OK;
+}
+
+int swe_batch_set_barrier(swe_batch *b, double timeout_s, int32_t extra_arrivals) {
+  if (!b || !(timeout_s > 0.0) || extra_arrivals < 0) return SWE_EINVAL;
+  b->timeout_s = timeout_s;
+  b->extra = (unsigned)extra_arrivals;
+  b->sticky = SWE_OK;
+  return upload_table(b);  // also clears the barrier words and the status
+}
+
+int swe_batch_destroy(swe_batch *b) {
+  if (!b) return SWE_OK;
+  cudaStreamSynchronize(b->stream);
+  for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto &sl : b->slots)
+    if (sl.mem) cudaFreeAsync(sl.mem, b->stream);
+  cudaStreamSynchronize(b->stream);
+  if (b->d_sc) cudaFree(b->d_sc);
+  if (b->d_table) cudaFree(b->d_table);
+  if (b->d_ctl) cudaFree(b->d_ctl);
+  if (b->d_part) cudaFree(b->d_part);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+  return SWE_OK;
+}
+
+}  // extern "C"

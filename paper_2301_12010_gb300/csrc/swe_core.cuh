@@ -60,11 +60,11 @@ struct DevScalars {
 
 // Physical and numerical parameters, constant over a run.
 struct Phys {
-  double g, n2, h_dry, h_wet, weno_eps, fixed_dt, z_ref;
+  double g, n2, h_dry, h_wet, h_film, hf4, weno_eps, fixed_dt, z_ref;
   double b_jump_x, b_jump_y;
   double inflow_amp, inflow_period, inflow_depth;
   double dx, dy;
-  float h_dry32, h_wet32;  // smallest floats whose double value is >= h_dry / h_wet
+  float h_dry32, h_wet32, h_film32;  // smallest floats whose double value is >= h_dry / h_wet / h_film
   int bc[4];
 };
 
@@ -95,6 +95,11 @@ template <> struct Num<float> {
   // h^(7/3) for h > 0 through exp2/log2 hardware approximations
   static __device__ __forceinline__ float pow73(float h) { return exp2f(2.33333333f * __log2f(h)); }
   static __device__ __forceinline__ bool below(float h, float thr32, double) { return h < thr32; }
+  static __device__ __forceinline__ float rsqrt_(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  }
 };
 template <> struct Num<double> {
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
@@ -102,41 +107,51 @@ template <> struct Num<double> {
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double pow73(double h) { return h * h * cbrt(h); }
   static __device__ __forceinline__ bool below(double h, float, double thr) { return h < thr; }
+  static __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
 };
 
-// WENO5-JS value at the right face of v2 (Jiang & Shu 1996), scaled by 6:
-// returns 6*W and the unnormalised weights a_k and 1/sum(d_k a_k') needed to
-// apply the same weights to the bed.  t_k = 12 eps + 12 beta_k, so that
-// a_k = d_k / t_k^2 has the ratios of d_k / (eps + beta_k)^2.
+// WENO5-JS (Jiang & Shu 1996) at the right face of v2, scaled by 6.
+// With t_k = 12 eps + 12 beta_k = q_k + 3 e_k^2, where q_k = 13 D2_k^2 + 12 eps
+// is the second-difference part of the stencil's smoothness (cached by the
+// caller: it depends on the 3-cell window only) and e_k its first-difference
+// part, the weights d_k / t_k^2 have the ratios of d_k / (eps + beta_k)^2.
+// Returns 6 W; a_k = 1/t_k^2 and rdn = 1 / sum d_k a_k are returned for
+// applying the same weights to the bed.  Linear weights d_k are folded into
+// the candidate coefficients (wc*).
 template <typename T>
-__device__ __forceinline__ T weno5x6(T v0, T v1, T v2, T v3, T v4, T eps12, T &a0, T &a1, T &a2, T &rdn) {
-  const T d20 = v0 - T(2) * v1 + v2;
-  const T d21 = v1 - T(2) * v2 + v3;
-  const T d22 = v2 - T(2) * v3 + v4;
+__device__ __forceinline__ T weno5q(T v0, T v1, T v2, T v3, T v4, T q0, T q1, T q2, T &a0, T &a1, T &a2,
+                                    T &rdn) {
   const T e0 = v0 - T(4) * v1 + T(3) * v2;
   const T e1 = v1 - v3;
   const T e2 = T(3) * v2 - T(4) * v3 + v4;
-  const T t0 = T(13) * d20 * d20 + T(3) * e0 * e0 + eps12;
-  const T t1 = T(13) * d21 * d21 + T(3) * e1 * e1 + eps12;
-  const T t2 = T(13) * d22 * d22 + T(3) * e2 * e2 + eps12;
-  const T r0 = Num<T>::rcp(t0), r1 = Num<T>::rcp(t1), r2 = Num<T>::rcp(t2);
-  a0 = T(0.1) * r0 * r0;
-  a1 = T(0.6) * r1 * r1;
-  a2 = T(0.3) * r2 * r2;
-  const T p0 = T(2) * v0 - T(7) * v1 + T(11) * v2;
-  const T p1 = -v1 + T(5) * v2 + T(2) * v3;
-  const T p2 = T(2) * v2 + T(5) * v3 - v4;
-  rdn = Num<T>::rcp(a0 + a1 + a2);
+  const T r0 = Num<T>::rcp(T(3) * e0 * e0 + q0);
+  const T r1 = Num<T>::rcp(T(3) * e1 * e1 + q1);
+  const T r2 = Num<T>::rcp(T(3) * e2 * e2 + q2);
+  a0 = r0 * r0;
+  a1 = r1 * r1;
+  a2 = r2 * r2;
+  rdn = Num<T>::rcp(T(0.1) * a0 + T(0.6) * a1 + T(0.3) * a2);
+  // d_k * (6 p_k): 0.1 (2, -7, 11), 0.6 (-1, 5, 2), 0.3 (2, 5, -1)
+  const T p0 = T(0.2) * v0 - T(0.7) * v1 + T(1.1) * v2;
+  const T p1 = T(-0.6) * v1 + T(3.0) * v2 + T(1.2) * v3;
+  const T p2 = T(0.6) * v2 + T(1.5) * v3 - T(0.3) * v4;
   return (a0 * p0 + a1 * p1 + a2 * p2) * rdn;
 }
 
 // 6 * (weighted candidate values) of a stencil with given weights.
 template <typename T>
 __device__ __forceinline__ T weighted6(T v0, T v1, T v2, T v3, T v4, T a0, T a1, T a2, T rdn) {
-  const T p0 = T(2) * v0 - T(7) * v1 + T(11) * v2;
-  const T p1 = -v1 + T(5) * v2 + T(2) * v3;
-  const T p2 = T(2) * v2 + T(5) * v3 - v4;
+  const T p0 = T(0.2) * v0 - T(0.7) * v1 + T(1.1) * v2;
+  const T p1 = T(-0.6) * v1 + T(3.0) * v2 + T(1.2) * v3;
+  const T p2 = T(0.6) * v2 + T(1.5) * v3 - T(0.3) * v4;
   return (a0 * p0 + a1 * p1 + a2 * p2) * rdn;
+}
+
+// Second-difference smoothness part of the 3-cell window (a, b, c).
+template <typename T>
+__device__ __forceinline__ T qwin(T a, T b, T c, T eps12) {
+  const T d2 = a - T(2) * b + c;
+  return T(13) * d2 * d2 + eps12;
 }
 
 // Carrier N-wave of Eq. (20) entering through the x- edge (peak elevation
@@ -208,25 +223,22 @@ __device__ __forceinline__ void load_cell(const T *__restrict__ b, const T *__re
   }
 }
 
-// Split fluxes of one cell along direction DIR (0: x with F, 1: y with G)
-// from the anomaly form: h = ha + d, pressure g ha (h + d)/2 = g (h^2-d^2)/2,
-// Q = (ha, hu, hv).
-template <typename T, int DIR>
-__device__ __forceinline__ void split_cell(T ha, T hu, T hv, T b, T alpha, T g, T zref, const Phys &p, T fp[3],
+// Split fluxes of one cell in the frame of a sweep: qn is the discharge
+// normal to the faces (hu for x, hv for y) and qt the tangential one.  With
+// h = ha + d and pressure g ha (h + d)/2 = g (h^2 - d^2)/2:
+//   F = (qn, qn un + pressure, qt un),  Q = (ha, qn, qt),  f+- = (F +- alpha Q)/2,
+// i.e. F of Eq. (2) in x and G of Eq. (3) (with its momentum components
+// swapped) in y.
+template <typename T>
+__device__ __forceinline__ void split_cell(T ha, T qn, T qt, T b, T alpha, T g, T zref, const Phys &p, T fp[3],
                                            T fm[3]) {
   const T d = still_depth(b, zref);
   const T h = ha + d;
-  T u = T(0), v = T(0);
-  if (!Num<T>::below(h, p.h_dry32, p.h_dry)) {
-    const T r = Num<T>::rcp(h);
-    u = hu * r;
-    v = hv * r;
-  }
+  T un = T(0);
+  if (!Num<T>::below(h, p.h_dry32, p.h_dry)) un = qn * Num<T>::rcp(h);
   const T pres = T(0.5) * g * ha * (h + d);
-  T F0, F1, F2;
-  if (DIR == 0) { F0 = hu; F1 = hu * u + pres; F2 = hv * u; }
-  else { F0 = hv; F1 = hu * v; F2 = hv * v + pres; }
-  const T q0 = alpha * ha, q1 = alpha * hu, q2 = alpha * hv;
+  const T F0 = qn, F1 = qn * un + pres, F2 = qt * un;
+  const T q0 = alpha * ha, q1 = alpha * qn, q2 = alpha * qt;
   fp[0] = T(0.5) * (F0 + q0); fm[0] = T(0.5) * (F0 - q0);
   fp[1] = T(0.5) * (F1 + q1); fm[1] = T(0.5) * (F1 - q1);
   fp[2] = T(0.5) * (F2 + q2); fm[2] = T(0.5) * (F2 - q2);
@@ -267,7 +279,8 @@ struct TileGeom {
   static constexpr int P = ((BW + 7) / 8) * 8 + 1;
   static constexpr int FIELD = BH * P;  // one field of the box
   static constexpr int BOX = 4 * FIELD; // ha, hu, hv, b
-  static constexpr int NC = TX * TY;
+  static constexpr int LP = TX + 1;        // L_x row pitch (x-pass lanes on 8 rows hit distinct banks)
+  static constexpr int NC = TY * LP;       // one L_x component
   static constexpr int ELEMS = 2 * BOX + 3 * NC;  // two boxes (double buffer) + L_x
   static constexpr size_t BYTES = sizeof(T) * (size_t)ELEMS;
 };
@@ -324,8 +337,8 @@ __device__ __forceinline__ void issue_box(const StageIO<T> &io, int i0, int j0, 
 // never read by a valid cell.  Walls mirror cells of the same box; inflow
 // ghosts carry the N-wave; periodic ghosts are read across the seam.
 template <typename T, int TX, int TY, int NT>
-__device__ __forceinline__ void patch_box(const StageIO<T> &io, const Phys &p, int i0, int j0, T *box, T zref,
-                                          T eta_in, T u_in) {
+__device__ __noinline__ void patch_box(const StageIO<T> &io, const Phys &p, int i0, int j0, T *box, T zref,
+                                       T eta_in, T u_in) {
   using G = TileGeom<T, TX, TY>;
   const int nx = io.nx, ny = io.ny;
   T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
@@ -379,20 +392,29 @@ __device__ __forceinline__ void patch_box(const StageIO<T> &io, const Phys &p, i
   }
 }
 
-// Sliding WENO5 window over one line of the box.  For faces k = 0..S (face k
-// at the left of strip cell k), with split fluxes computed on the fly from
-// the raw box: F6[m] = 6 Fhat_m, B12 = 12 bhat (normal-momentum weights).
-template <typename T, int DIR>
+// Sliding WENO5 window along one line of the box (one strip of S cells), in
+// the frame of the sweep.  Slots 0..5 hold cells c0-3+k .. c0+2+k for face k
+// (between slots 2 and 3); qp[s] / qm[s] cache the second-difference
+// smoothness of the 3-cell window centred at slot s for f+ / f-.
+template <typename T>
 struct Window {
   T fp[3][6], fm[3][6], bw[6];
-  __device__ __forceinline__ void put(int q, const T *bha, const T *bhu, const T *bhv, const T *bb, int o, T alpha,
+  T qp[3][5], qm[3][5];
+  __device__ __forceinline__ void put(int q, const T *bha, const T *bqn, const T *bqt, const T *bb, int o, T alpha,
                                       T g, T zref, const Phys &p) {
     T a[3], m[3];
     const T b = bb[o];
-    split_cell<T, DIR>(bha[o], bhu[o], bhv[o], b, alpha, g, zref, p, a, m);
+    split_cell<T>(bha[o], bqn[o], bqt[o], b, alpha, g, zref, p, a, m);
 #pragma unroll
     for (int c = 0; c < 3; ++c) { fp[c][q] = a[c]; fm[c][q] = m[c]; }
     bw[q] = b;
+  }
+  __device__ __forceinline__ void window_terms(int s, T eps12) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      qp[c][s] = qwin(fp[c][s - 1], fp[c][s], fp[c][s + 1], eps12);
+      qm[c][s] = qwin(fm[c][s - 1], fm[c][s], fm[c][s + 1], eps12);
+    }
   }
   __device__ __forceinline__ void shift() {
 #pragma unroll
@@ -401,28 +423,66 @@ struct Window {
       for (int c = 0; c < 3; ++c) { fp[c][q] = fp[c][q + 1]; fm[c][q] = fm[c][q + 1]; }
       bw[q] = bw[q + 1];
     }
+#pragma unroll
+    for (int q = 1; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { qp[c][q] = qp[c][q + 1]; qm[c][q] = qm[c][q + 1]; }
   }
-  // face between window cells 2 and 3
-  __device__ __forceinline__ void face(T eps12, T F6[3], T &B12) const {
-    constexpr int MOM = DIR == 0 ? 1 : 2;
+  // face between slots 2 and 3: F6[c] = 6 Fhat_c, B12 = 12 bhat (weights of c = 1)
+  __device__ __forceinline__ void face(T F6[3], T &B12) const {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       T a0, a1, a2, rp, c0, c1, c2, rm;
-      const T Fp = weno5x6<T>(fp[c][0], fp[c][1], fp[c][2], fp[c][3], fp[c][4], eps12, a0, a1, a2, rp);
-      const T Fm = weno5x6<T>(fm[c][5], fm[c][4], fm[c][3], fm[c][2], fm[c][1], eps12, c0, c1, c2, rm);
+      const T Fp = weno5q<T>(fp[c][0], fp[c][1], fp[c][2], fp[c][3], fp[c][4], qp[c][1], qp[c][2], qp[c][3], a0,
+                             a1, a2, rp);
+      const T Fm = weno5q<T>(fm[c][5], fm[c][4], fm[c][3], fm[c][2], fm[c][1], qm[c][4], qm[c][3], qm[c][2], c0,
+                             c1, c2, rm);
       F6[c] = Fp + Fm;
-      if (c == MOM)
+      if (c == 1)
         B12 = weighted6<T>(bw[0], bw[1], bw[2], bw[3], bw[4], a0, a1, a2, rp) +
               weighted6<T>(bw[5], bw[4], bw[3], bw[2], bw[1], c0, c1, c2, rm);
     }
   }
 };
 
+// One strip: faces k = 0..S (face k at the left of strip cell k).  Returns
+// dF[c][k] = 6 (Fhat_c(k+1) - Fhat_c(k)) and db[k] = 12 (bhat(k+1) - bhat(k))
+// for the S cells, and adds the mass flux through the domain edges that the
+// strip owns (face -1/2 at k = 0 of the first strip, face n-1/2 at k >= 1).
+template <typename T, int S>
+__device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T *bqt, const T *bb, int o0, int st,
+                                            T alpha, T g, T zref, T eps12, const Phys &p, int ia, int n,
+                                            bool edge_ok, T dF[3][S], T db[S], T &edge) {
+  Window<T> win;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) win.put(q, bha, bqn, bqt, bb, o0 + q * st, alpha, g, zref, p);
+#pragma unroll
+  for (int q = 1; q < 4; ++q) win.window_terms(q, eps12);
+  T prevF[3], prevB = T(0);
+#pragma unroll
+  for (int k = 0; k <= S; ++k) {
+    win.put(5, bha, bqn, bqt, bb, o0 + (k + 5) * st, alpha, g, zref, p);
+    win.window_terms(4, eps12);
+    T F6[3], B12 = T(0);
+    win.face(F6, B12);
+    if (edge_ok && ((k == 0 && ia == 0) || (k > 0 && ia + k == n))) edge += (k == 0) ? F6[0] : -F6[0];
+    if (k > 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dF[c][k - 1] = F6[c] - prevF[c];
+      db[k - 1] = B12 - prevB;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) prevF[c] = F6[c];
+    prevB = B12;
+    win.shift();
+  }
+}
+
 // Per-CTA accumulators carried across the tiles of one launch.
 template <typename T>
 struct Acc {
   T ax = T(0), ay = T(0), ru = T(0), chk = T(0);
-  double deficit = 0.0, edge = 0.0;
+  T deficit = T(0), edge = T(0);  // diagnostics, summed in the state's precision per thread
 };
 
 // One RK3 stage (Eq. (8), Shu-Osher form, increment form) on one tile whose
@@ -430,7 +490,10 @@ struct Acc {
 //   stage 1: U1 = U^n + dt L(U^n)
 //   stage 2: U2 = U^n + 1/4 (U1 + dt L(U1) - U^n)
 //   stage 3: U^{n+1} = U^n + 2/3 (U2 + dt L(U2) - U^n)   (written over U^n)
-// followed by the post-stage rule, with L of Eq. (7).
+// followed by the post-stage rule, with L of Eq. (7).  Pass 0 sweeps x and
+// stores L_x; pass 1 sweeps y, adds L_y and the sources and updates.  Both
+// passes run the same sweep code (loop not unrolled: one copy of the WENO
+// body in the instruction stream).
 template <typename T, int TX, int TY, int NT, int S, int STAGE>
 __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p, int i0, int j0, const T *box,
                                              T *sL, double dt, T alx, T aly, Acc<T> &acc) {
@@ -442,69 +505,50 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
   const int nx = io.nx, ny = io.ny;
   const T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
   const T g = T(p.g), zref = T(p.z_ref), eps12 = T(12.0 * p.weno_eps);
+  // x pass: lane l of warp w takes row 8*(w % (TY/8)) + l/4 and strip 4*(w / (TY/8)) + l%4
+  const int w = tid >> 5, l = tid & 31;
+  const int xr = 8 * (w % (TY / 8)) + (l >> 2);
+  const int xc0 = (4 * (w / (TY / 8)) + (l & 3)) * S;
+  // y pass: thread takes column tid % TX and strip tid / TX
+  const int yc = tid % TX, yr0 = (tid / TX) * S;
+  const int i = i0 + yc;
 
-  // ---- x pass: lane l of warp w: row 8*(w % (TY/8)) + l/4, strip 4*(w / (TY/8)) + l%4
-  {
-    const int w = tid >> 5, l = tid & 31;
-    const int r = 8 * (w % (TY / 8)) + (l >> 2);
-    const int c0 = (4 * (w / (TY / 8)) + (l & 3)) * S;
-    const int row = (r + 3) * G::P;
-    Window<T, 0> win;
-#pragma unroll
-    for (int q = 0; q < 5; ++q) win.put(q, bha, bhu, bhv, bb, row + c0 + q, alx, g, zref, p);
-    const T inv6dx = T(1.0 / (6.0 * p.dx));
-    const T g12dx = T(p.g / (12.0 * p.dx));
-    T prevF[3], prevB = T(0);
-    const bool edge_row = (j0 + r < ny);
-    const int ia = i0 + c0;
-#pragma unroll
-    for (int k = 0; k <= S; ++k) {
-      win.put(5, bha, bhu, bhv, bb, row + c0 + k + 5, alx, g, zref, p);
-      T F6[3], B12 = T(0);
-      win.face(eps12, F6, B12);
-      if (k > 0) {
-        const int o = r * TX + c0 + k - 1;
-        const T ha = bha[row + c0 + k + 2];
-        sL[o] = -(F6[0] - prevF[0]) * inv6dx;
-        sL[G::NC + o] = -(F6[1] - prevF[1]) * inv6dx - g12dx * ha * (B12 - prevB);
-        sL[2 * G::NC + o] = -(F6[2] - prevF[2]) * inv6dx;
-      }
-      // faces -1/2 (k = 0 of the first strip) and nx-1/2 (k >= 1 of the strip holding cell nx-1)
-      if (edge_row && ((k == 0 && ia == 0) || (k > 0 && ia + k == nx)))
-        acc.edge += (ia + k == 0) ? (double)F6[0] : -(double)F6[0];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) prevF[c] = F6[c];
-      prevB = B12;
-      win.shift();
-    }
-  }
-  __syncthreads();
-
-  // ---- y pass, sources, RK combination, post rule
-  {
-    const int c = tid % TX, r0 = (tid / TX) * S;
-    const int i = i0 + c;
-    const bool col_ok = i < nx;
-    // U^n of the own cells, fetched early (used at the end)
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool X = pass == 0;
+    // U^n of the y-pass cells (stages 2, 3), fetched before the sweep so that
+    // the global-memory latency hides behind it
     T u0[3][S];
-    if (STAGE != 1) {
+    if (STAGE != 1 && !X) {
 #pragma unroll
       for (int k = 0; k < S; ++k) {
-        const int j = j0 + r0 + k;
-        if (col_ok && j < ny) {
-          const size_t go = (size_t)j * io.pitch + i;
-          u0[0][k] = io.ha0[go];
-          u0[1][k] = io.hu0[go];
-          u0[2][k] = io.hv0[go];
-        } else {
-          u0[0][k] = u0[1][k] = u0[2][k] = T(0);
-        }
+        const int j = j0 + yr0 + k;
+        const bool ok = i < nx && j < ny;
+        const size_t go = ok ? (size_t)j * io.pitch + i : 0;
+        u0[0][k] = ok ? io.ha0[go] : T(0);
+        u0[1][k] = ok ? io.hu0[go] : T(0);
+        u0[2][k] = ok ? io.hv0[go] : T(0);
       }
     }
-    Window<T, 1> win;
-    const int col = c + 3;
+    T dF[3][S], db[S];
+    sweep_strip<T, S>(bha, X ? bhu : bhv, X ? bhv : bhu, bb, X ? (xr + 3) * G::P + xc0 : yr0 * G::P + yc + 3,
+                      X ? 1 : G::P, X ? alx : aly, g, zref, eps12, p, X ? i0 + xc0 : j0 + yr0, X ? nx : ny,
+                      X ? (j0 + xr < ny) : (i < nx), dF, db, acc.edge);
+    if (X) {
+      const T inv6dx = T(1.0 / (6.0 * p.dx));
+      const T g12dx = T(p.g / (12.0 * p.dx));
 #pragma unroll
-    for (int q = 0; q < 5; ++q) win.put(q, bha, bhu, bhv, bb, (r0 + q) * G::P + col, aly, g, zref, p);
+      for (int k = 0; k < S; ++k) {
+        const int o = xr * G::LP + xc0 + k;
+        const T ha = bha[(xr + 3) * G::P + xc0 + k + 3];
+        sL[o] = -dF[0][k] * inv6dx;
+        sL[G::NC + o] = -dF[1][k] * inv6dx - g12dx * ha * db[k];
+        sL[2 * G::NC + o] = -dF[2][k] * inv6dx;
+      }
+      __syncthreads();
+      continue;
+    }
+    // y pass epilogue: sources, RK combination, post rule (dF[1] is hv, dF[2] hu)
     const T inv6dy = T(1.0 / (6.0 * p.dy));
     const T g12dy = T(p.g / (12.0 * p.dy));
     const T tdt = T(dt);
@@ -512,65 +556,60 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
     const T gn2 = T(p.g * p.n2);
     const bool friction = p.n2 > 0.0;
     const T wrk = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
-    const T rxy = T(p.dx / p.dy);
-    T prevF[3], prevB = T(0);
-    const int jb = j0 + r0;
 #pragma unroll
-    for (int k = 0; k <= S; ++k) {
-      win.put(5, bha, bhu, bhv, bb, (r0 + k + 5) * G::P + col, aly, g, zref, p);
-      T F6[3], B12 = T(0);
-      win.face(eps12, F6, B12);
-      if (col_ok && ((k == 0 && jb == 0) || (k > 0 && jb + k == ny)))
-        acc.edge += (jb + k == 0 ? 1.0 : -1.0) * (double)(F6[0] * rxy);
-      if (k > 0) {
-        const int kk = k - 1;
-        const int j = jb + kk;
-        if (col_ok && j < ny) {
-          const int o = (r0 + kk) * TX + c;
-          const int bo = (r0 + kk + 3) * G::P + col;
-          const T ha = bha[bo], hu = bhu[bo], hv = bhv[bo], bc = bb[bo];
-          const T d = still_depth(bc, zref);
-          const T h = ha + d;
-          T Lh = sL[o] - (F6[0] - prevF[0]) * inv6dy;
-          T Lhu = sL[G::NC + o] - (F6[1] - prevF[1]) * inv6dy;
-          T Lhv = sL[2 * G::NC + o] - (F6[2] - prevF[2]) * inv6dy - g12dy * ha * (B12 - prevB);
-          if (friction && !Num<T>::below(h, p.h_dry32, p.h_dry)) {
-            const T q = Num<T>::sqrt_(hu * hu + hv * hv);
-            T kap = gn2 * q * Num<T>::rcp(Num<T>::pow73(h));
-            kap = kap > rcap ? rcap : kap;
-            Lhu -= kap * hu;
-            Lhv -= kap * hv;
+    for (int k = 0; k < S; ++k) {
+      const int j = j0 + yr0 + k;
+      if (i < nx && j < ny) {
+        const int o = (yr0 + k) * G::LP + yc;
+        const int bo = (yr0 + k + 3) * G::P + yc + 3;
+        const T ha = bha[bo], hu = bhu[bo], hv = bhv[bo], bc = bb[bo];
+        const T d = still_depth(bc, zref);
+        const T h = ha + d;
+        T Lh = sL[o] - dF[0][k] * inv6dy;
+        T Lhu = sL[G::NC + o] - dF[2][k] * inv6dy;
+        T Lhv = sL[2 * G::NC + o] - dF[1][k] * inv6dy - g12dy * ha * db[k];
+        if (friction && !Num<T>::below(h, p.h_dry32, p.h_dry)) {
+          const T q = Num<T>::sqrt_(hu * hu + hv * hv);
+          T kap = gn2 * q * Num<T>::rcp(Num<T>::pow73(h));
+          kap = kap > rcap ? rcap : kap;
+          Lhu -= kap * hu;
+          Lhv -= kap * hv;
+        }
+        T nha = ha + tdt * Lh, nhu = hu + tdt * Lhu, nhv = hv + tdt * Lhv;
+        const size_t go = (size_t)j * io.pitch + i;
+        if (STAGE != 1) {
+          nha = u0[0][k] + wrk * (nha - u0[0][k]);
+          nhu = u0[1][k] + wrk * (nhu - u0[1][k]);
+          nhv = u0[2][k] + wrk * (nhv - u0[2][k]);
+        }
+        if (nha < -d) { acc.deficit -= nha + d; nha = -d; }
+        const T nh = nha + d;
+        T u = T(0), v = T(0);
+        if (Num<T>::below(nh, p.h_dry32, p.h_dry)) { nhu = T(0); nhv = T(0); }
+        else {
+          if (Num<T>::below(nh, p.h_film32, p.h_film)) {  // film: bounded velocity
+            const T h2 = nh * nh;
+            const T f = T(1.4142135623730951) * h2 * Num<T>::rsqrt_(h2 * h2 + T(p.hf4));
+            nhu *= f;
+            nhv *= f;
           }
-          T nha = ha + tdt * Lh, nhu = hu + tdt * Lhu, nhv = hv + tdt * Lhv;
-          if (STAGE != 1) {
-            nha = u0[0][kk] + wrk * (nha - u0[0][kk]);
-            nhu = u0[1][kk] + wrk * (nhu - u0[1][kk]);
-            nhv = u0[2][kk] + wrk * (nhv - u0[2][kk]);
-          }
-          if (nha < -d) { acc.deficit -= (double)(nha + d); nha = -d; }
-          const T nh = nha + d;
-          T u = T(0), v = T(0);
-          if (Num<T>::below(nh, p.h_dry32, p.h_dry)) { nhu = T(0); nhv = T(0); }
-          else { const T rr = Num<T>::rcp(nh); u = nhu * rr; v = nhv * rr; }
-          const size_t go = (size_t)j * io.pitch + i;
-          io.oha[go] = nha;
-          io.ohu[go] = nhu;
-          io.ohv[go] = nhv;
-          const T cel = Num<T>::sqrt_(g * nh);
-          const T sx = fabs(u) + cel, sy = fabs(v) + cel;
-          acc.chk += sx + sy;  // non-finite values propagate to the per-CTA check
-          acc.ax = sx > acc.ax ? sx : acc.ax;
-          acc.ay = sy > acc.ay ? sy : acc.ay;
-          if (STAGE == 3 && !Num<T>::below(nh, p.h_wet32, p.h_wet) && bc > T(0)) {
-            const T e = nh + bc;
-            acc.ru = e > acc.ru ? e : acc.ru;
-          }
+          const T rr = Num<T>::rcp(nh);
+          u = nhu * rr;
+          v = nhv * rr;
+        }
+        io.oha[go] = nha;
+        io.ohu[go] = nhu;
+        io.ohv[go] = nhv;
+        const T cel = Num<T>::sqrt_(g * nh);
+        const T sx = fabs(u) + cel, sy = fabs(v) + cel;
+        acc.chk += sx + sy;  // non-finite values propagate to the per-CTA check
+        acc.ax = sx > acc.ax ? sx : acc.ax;
+        acc.ay = sy > acc.ay ? sy : acc.ay;
+        if (STAGE == 3 && !Num<T>::below(nh, p.h_wet32, p.h_wet) && bc > T(0)) {
+          const T e = nh + bc;
+          acc.ru = e > acc.ru ? e : acc.ru;
         }
       }
-#pragma unroll
-      for (int q = 0; q < 3; ++q) prevF[q] = F6[q];
-      prevB = B12;
-      win.shift();
     }
   }
 }
@@ -583,34 +622,36 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
 template <int STAGE>
 __device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, bool lead, RedSmem &red, double &ax,
                                               double &ay) {
-  ax = bitsd(sc->alpha[STAGE - 1][0]);
-  ay = bitsd(sc->alpha[STAGE - 1][1]);
+  // read through L2 (other CTAs wrote these before the last grid barrier or launch)
+  ax = bitsd(__ldcg(&sc->alpha[STAGE - 1][0]));
+  ay = bitsd(__ldcg(&sc->alpha[STAGE - 1][1]));
+  const double t_now = __ldcg(&sc->t), t_end = __ldcg(&sc->t_end);
   double dt = 0.0;
-  unsigned skip = sc->status != 0u;
+  unsigned skip = __ldcg(&sc->status) != 0u;
   if (STAGE == 1) {
-    const double t = sc->t;
-    if (sc->t_end > 0.0 && t >= sc->t_end) skip = 1;
+    if (t_end > 0.0 && t_now >= t_end) skip = 1;
     if (p.fixed_dt > 0.0) dt = p.fixed_dt;
     else {
       const double den = ax / p.dx + ay / p.dy;
-      if (den > 0.0) dt = sc->cfl / den;
+      if (den > 0.0) dt = __ldcg(&sc->cfl) / den;
       else if (!skip) { skip = 1; atomicOr(&sc->status, ST_DRY); }
     }
-    if (sc->t_end > 0.0 && t + dt > sc->t_end) dt = sc->t_end - t;
+    if (t_end > 0.0 && t_now + dt > t_end) dt = t_end - t_now;
     if (lead) {
       sc->running = skip ? 0u : 1u;
       if (!skip) {
+        const long long steps = __ldcg(&sc->steps);
         sc->dt = dt;
-        sc->t_step = t;
-        sc->parity = (unsigned)(sc->steps & 1);
-        sc->runup_now[sc->steps & 1] = 0ull;
+        sc->t_step = t_now;
+        sc->parity = (unsigned)(steps & 1);
+        sc->runup_now[steps & 1] = 0ull;
         sc->alpha[2][0] = 0ull;
         sc->alpha[2][1] = 0ull;
       }
     }
   } else {
-    if (!sc->running) skip = 1;
-    dt = sc->dt;
+    if (!__ldcg(&sc->running)) skip = 1;
+    dt = __ldcg(&sc->dt);
     if (lead && !skip) {
       sc->alpha[STAGE == 2 ? 0 : 1][0] = 0ull;
       sc->alpha[STAGE == 2 ? 0 : 1][1] = 0ull;
@@ -619,7 +660,7 @@ __device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, boo
   red.skip = skip;
   red.bad = 0u;
   red.dt = dt;
-  const double tst = (STAGE == 1) ? sc->t : sc->t_step;
+  const double tst = (STAGE == 1) ? t_now : __ldcg(&sc->t_step);
   const double ts = (STAGE == 1) ? tst : (STAGE == 2 ? tst + dt : tst + 0.5 * dt);
   red.eta_in[0] = (p.bc[0] == BC_INFLOW) ? inflow_eta(p, ts) : 0.0;
 }
@@ -631,7 +672,7 @@ __device__ __forceinline__ void publish(const Phys &p, DevScalars *sc, bool lead
                                         const Acc<T> &acc) {
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   const T ax = warp_max(acc.ax), ay = warp_max(acc.ay), ru = warp_max(acc.ru);
-  const double de = warp_sum(acc.deficit), ef = warp_sum(acc.edge);
+  const double de = warp_sum((double)acc.deficit), ef = warp_sum((double)acc.edge);
   const bool bad = !(acc.chk <= T(3.0e38));
   const unsigned anybad = __any_sync(0xffffffffu, bad);
   if (l == 0) {
@@ -660,14 +701,14 @@ __device__ __forceinline__ void publish(const Phys &p, DevScalars *sc, bool lead
     if (fsum != 0.0) atomicAdd(&sc->boundary_mass, wfl * dt * fsum * p.dy / 6.0);
     if (STAGE == 3 && rmax > 0.0) {
       const unsigned long long rb = dbits(rmax);
-      atomicMax(&sc->runup_now[sc->parity], rb);
+      atomicMax(&sc->runup_now[__ldcg(&sc->parity)], rb);
       atomicMax(&sc->runup_max, rb);
     }
     if (red.bad) atomicOr(&sc->status, ST_NONFINITE);
     if (STAGE == 3 && lead) {
-      const double tn = sc->t_step + dt;
-      sc->t = (sc->t_end > 0.0 && tn >= sc->t_end) ? sc->t_end : tn;
-      sc->steps += 1;
+      const double tn = __ldcg(&sc->t_step) + dt, te = __ldcg(&sc->t_end);
+      sc->t = (te > 0.0 && tn >= te) ? te : tn;
+      sc->steps = __ldcg(&sc->steps) + 1;
     }
   }
 }
@@ -717,6 +758,172 @@ __device__ void stage_persistent(const StageIO<T> &io, const Phys &p, DevScalars
   }
   cp_wait<0>();
   publish<T, NT, STAGE>(p, sc, lead, red, dt, acc);
+}
+
+// ------------------------------------------------------------ batch driver
+// One scenario of a batch as the kernels see it (device memory).
+template <typename T>
+struct BatchSlot {
+  Field<T> fd;
+  Phys p;
+  DevScalars *sc;
+  int tiles_x, ntiles, first_item, pad;
+};
+
+// Batch control block (device memory).
+struct BatchCtl {
+  int nslots;               // entries of the slot table
+  int total_items;          // tiles over all entries (the work list)
+  unsigned bar_count;       // grid barrier: arrivals in the current round
+  unsigned bar_gen;         // grid barrier: completed rounds
+  unsigned status;          // ST_TIMEOUT when a barrier wait ran out
+  unsigned bar_extra;       // test hook: arrivals expected beyond the grid (0)
+  long long bar_cycles;     // bounded wait: SM clock cycles before giving up
+};
+
+// Grid-wide barrier of a cooperative launch with a bounded wait.  Returns
+// false (and sets ST_TIMEOUT) if the other CTAs did not arrive in time; the
+// caller then leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(BatchCtl *ctl, unsigned nblocks) {
+  __shared__ unsigned ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1u;
+    volatile unsigned *gen = &ctl->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned expect = nblocks + ctl->bar_extra;
+    if (atomicAdd(&ctl->bar_count, 1u) == expect - 1u) {
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > ctl->bar_cycles || *(volatile unsigned *)&ctl->status) {
+          atomicOr(&ctl->status, ST_TIMEOUT);
+          ok = 0u;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();  // acquire: later loads see what other CTAs wrote before the barrier
+  }
+  __syncthreads();
+  return ok != 0u;
+}
+
+template <typename T>
+__device__ __forceinline__ int slot_of_item(const BatchSlot<T> *slots, int n, int item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (slots[mid].first_item <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ StageIO<T> io_of(const Field<T> &fd, int stage) {
+  StageIO<T> io;
+  const int in = stage - 1, out = stage % 3;
+  io.b = fd.b;
+  io.ha = fd.h[in];
+  io.hu = fd.hu[in];
+  io.hv = fd.hv[in];
+  io.ha0 = fd.h[0];
+  io.hu0 = fd.hu[0];
+  io.hv0 = fd.hv[0];
+  io.oha = fd.h[out];
+  io.ohu = fd.hu[out];
+  io.ohv = fd.hv[out];
+  io.nx = fd.nx;
+  io.ny = fd.ny;
+  io.pitch = fd.pitch;
+  return io;
+}
+
+// One RK stage over the work list of a batch: CTA b handles items b,
+// b + gridDim.x, ...  Per-scenario scalars are taken when the CTA enters a
+// scenario and its accumulators are published when it leaves it; the lead
+// CTA of a scenario is the one that owns its tile 0.
+template <typename T, int TX, int TY, int NT, int S, int STAGE>
+__device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T *smem, RedSmem &red, Phys &sp) {
+  using G = TileGeom<T, TX, TY>;
+  __shared__ int s_slot;
+  __shared__ unsigned s_skip;
+  __shared__ StageIO<T> s_io;  // planes of the current scenario (kept out of registers)
+  T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
+  const int tid = threadIdx.x;
+  const int G0 = gridDim.x;
+  int cur = -1;
+  bool lead = false, skip = true;
+  double dt = 0.0;
+  T alx = T(0), aly = T(0), eta_in = T(0), u_in = T(0);
+  Acc<T> acc;
+  int item = blockIdx.x;
+  if (item < total) {
+    const int s0 = slot_of_item(slots, nslots, item);
+    const int t0 = item - slots[s0].first_item;
+    issue_box<T, TX, TY, NT>(io_of(slots[s0].fd, STAGE), (t0 % slots[s0].tiles_x) * TX, (t0 / slots[s0].tiles_x) * TY, box0);
+  }
+  cp_commit();
+  for (int it = 0; item < total; ++it, item += G0) {
+    if (tid == 0) s_slot = slot_of_item(slots, nslots, item);
+    __syncthreads();
+    const int s = s_slot;
+    const BatchSlot<T> &sl = slots[s];
+    if (s != cur) {
+      if (cur >= 0 && !skip) publish<T, NT, STAGE>(sp, slots[cur].sc, lead, red, dt, acc);
+      acc = Acc<T>();
+      __syncthreads();
+      if (tid == 0) {
+        sp = sl.p;
+        s_io = io_of(sl.fd, STAGE);
+        double ax, ay;
+        const bool ld = (sl.first_item % G0) == (int)blockIdx.x;
+        stage_scalars<STAGE>(sp, sl.sc, ld, red, ax, ay);
+        red.a[0][0] = ax;
+        red.a[0][1] = ay;
+        s_skip = red.skip;
+      }
+      __syncthreads();
+      cur = s;
+      lead = (sl.first_item % G0) == (int)blockIdx.x;
+      skip = s_skip != 0u;
+      dt = red.dt;
+      alx = T(red.a[0][0]);
+      aly = T(red.a[0][1]);
+      eta_in = T(red.eta_in[0]);
+      u_in = (sp.bc[0] == BC_INFLOW) ? T(red.eta_in[0] * sqrt(sp.g / sp.inflow_depth)) : T(0);
+    }
+    T *box = (it & 1) ? box1 : box0;
+    const int nitem = item + G0;
+    if (nitem < total) {
+      const int ns = slot_of_item(slots, nslots, nitem);
+      const int nt = nitem - slots[ns].first_item;
+      issue_box<T, TX, TY, NT>(io_of(slots[ns].fd, STAGE), (nt % slots[ns].tiles_x) * TX,
+                               (nt / slots[ns].tiles_x) * TY, (it & 1) ? box0 : box1);
+    }
+    cp_commit();
+    cp_wait<1>();
+    __syncthreads();
+    if (!skip) {
+      const int t = item - sl.first_item;
+      const int tiles_x = sl.tiles_x;
+      const int i0 = (t % tiles_x) * TX, j0 = (t / tiles_x) * TY;
+      if (i0 == 0 || j0 == 0 || i0 + TX + 3 > s_io.nx || j0 + TY + 3 > s_io.ny) {
+        patch_box<T, TX, TY, NT>(s_io, sp, i0, j0, box, T(sp.z_ref), eta_in, u_in);
+        __syncthreads();
+      }
+      tile_compute<T, TX, TY, NT, S, STAGE>(s_io, sp, i0, j0, box, sL, dt, alx, aly, acc);
+    }
+    __syncthreads();
+  }
+  cp_wait<0>();
+  if (cur >= 0 && !skip) publish<T, NT, STAGE>(sp, slots[cur].sc, lead, red, dt, acc);
 }
 
 }  // namespace swe

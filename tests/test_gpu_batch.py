@@ -1,0 +1,132 @@
+"""The batched ensemble path (persistent multi-scenario kernel) against the
+single-scenario path and the FP64 oracle, plus its admission, completion and
+bounded-barrier behaviour."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2301_12010_gb300 as swe  # noqa: E402
+
+GB = 1 << 30
+
+
+def stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def small_ensemble(count=5, seed=21):
+    # small grids with a narrow land strip (sea on the x- side, hills on land)
+    ens = W.mitigation_ensemble(count=count, seed=seed, nx_range=(96, 224), ny_range=(32, 160), land_width=90.0)
+    return [sc.copy(t_end=1e6) for sc in ens]
+
+
+def alone(sc, steps, cfl=0.4):
+    with swe.Solver(sc, precision=swe.F32, stream=stream()) as s:
+        s.step(steps, cfl)
+        st = s.get_state()
+        d = s.diagnostics()
+    return st, d
+
+
+def batch_run(scs, steps, tile=0, runs=(20, 15)):
+    with swe.Batch(max(2, len(scs)), 4 * GB, scs[0], stream=stream(), tile=tile) as b:
+        slots = [b.admit(sc) for sc in scs]
+        done = 0
+        for k in runs:
+            b.run(k)
+            done += k
+        assert done == steps
+        return [(b.get_state(s), b.diagnostics(s)) for s in slots]
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3])
+def test_batch_result_is_the_same_alone_and_in_the_mix(tile):
+    # each scenario keeps its own wave speeds, dt and time: bit-for-bit the
+    # same whether it runs alone or with the others
+    ens = small_ensemble()
+    mix = batch_run(ens, 35, tile)
+    for sc, (st_mix, d_mix) in zip(ens, mix):
+        (st_alone, d_alone), = batch_run([sc], 35, tile)
+        for a, m in zip(st_alone, st_mix):
+            assert np.array_equal(a, m)
+        assert d_alone["t"] == d_mix["t"] and d_mix["steps"] == 35
+
+
+def test_batch_matches_single_scenario_solver():
+    # same arithmetic in a separately compiled kernel: FP32 rounding level
+    ens = small_ensemble()
+    mix = batch_run(ens, 35)
+    for sc, ((h, hu, hv), d) in zip(ens, mix):
+        (rh, rhu, rhv), dr = alone(sc, 35)
+        et, er = h + sc.b, rh + sc.b
+        assert np.sqrt(((et - er) ** 2).sum() / (er ** 2).sum()) <= 1e-6
+        assert np.abs(hu - rhu).max() <= 1e-4 * max(np.abs(rhu).max(), 1.0)
+        assert d["t"] == pytest.approx(dr["t"], rel=1e-6)
+
+
+def test_batch_matches_fp64_oracle():
+    sc = small_ensemble(1, seed=5)[0]
+    ref = oracle.Simulation(sc)
+    ref.step(40)
+    with swe.Batch(2, GB, sc, stream=stream()) as b:
+        s = b.admit(sc)
+        b.run(40)
+        h, hu, hv = b.get_state(s)
+    et = np.where(h >= 1e-5, h + sc.b, 0.0)
+    er = np.where(ref.h >= 1e-5, ref.h + sc.b, 0.0)
+    assert np.sqrt(((et - er) ** 2).sum() / (er ** 2).sum()) <= 1e-4
+
+
+def test_batch_stops_at_t_end_and_reports_done():
+    ens = small_ensemble(3, seed=8)
+    with swe.Batch(4, GB, ens[0], stream=stream()) as b:
+        s0 = b.admit(ens[0], t_end=0.7)
+        s1 = b.admit(ens[1], t_end=1e6)
+        b.run(50)
+        assert b.poll() == [s0]
+        d0 = b.diagnostics(s0)
+        assert d0["t"] == 0.7
+        st, m, r = b.retire(s0)
+        ref, dr = alone(ens[0].copy(t_end=0.7), 0)
+        assert st[0].shape == ens[0].h.shape and m > 0
+        assert b.diagnostics(s1)["steps"] == 50
+
+
+def test_batch_budget_full_and_retire_accounting():
+    ens = small_ensemble(3, seed=9)
+    need = [swe.slot_bytes(sc.nx, sc.ny) for sc in ens]
+    with swe.Batch(2, need[0] + need[1], ens[0], stream=stream()) as b:
+        a = b.admit(ens[0])
+        c = b.admit(ens[1])
+        assert b.memory()[0] == need[0] + need[1]
+        with pytest.raises(swe.SweError) as ei:
+            b.admit(ens[2])
+        assert ei.value.code in (swe.EFULL, swe.EBUDGET)
+        b.retire(a, want_state=False)
+        assert b.memory()[0] == need[1]
+        assert b.try_admit(ens[2]) is not None or need[2] > need[0]
+
+
+def test_batch_barrier_timeout_is_reported_and_recoverable():
+    ens = small_ensemble(2, seed=13)
+    ref = batch_run(ens, 12, runs=(12,))
+    with swe.Batch(4, GB, ens[0], stream=stream()) as b:
+        slots = [b.admit(sc) for sc in ens]
+        b.set_barrier(0.02, extra_arrivals=1)  # waits for an arrival that never comes
+        b.run(1)
+        assert b.status() == swe.ETIMEOUT
+        b.set_barrier(1.0, 0)
+        assert b.status() == swe.OK
+        b.run(12)
+        for s, (st, d) in zip(slots, ref):
+            got = b.get_state(s)
+            for g, r in zip(got, st):
+                assert np.array_equal(g, r)

@@ -42,6 +42,7 @@ class Scenario:
     manning_n: float = 0.0
     h_dry: float = 1e-5
     h_wet: float = 1e-3
+    h_film: float = 1e-3  # film depth of the velocity desingularisation
     weno_eps: float = 1e-6
     fixed_dt: float = 0.0
     cfl: float = 0.4
@@ -230,7 +231,7 @@ def mitigation_scenario(nx: int, ny: int, rng: np.random.Generator, shore: np.nd
 
 
 def mitigation_ensemble(count: int = 64, seed: int = 4, dx: float = 2.0, t_end: float = 1200.0,
-                        nx_range=(512, 1024), ny_range=(256, 1024)) -> List[Scenario]:
+                        nx_range=(512, 1024), ny_range=(256, 1024), land_width: float = 400.0) -> List[Scenario]:
     """Seeded ensemble of uneven grids (multiples of 32) sharing one seeded
     shoreline, each with its own hill layout."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -239,7 +240,7 @@ def mitigation_ensemble(count: int = 64, seed: int = 4, dx: float = 2.0, t_end: 
     for s in range(count):
         nx = int(rng.integers(nx_range[0] // 32, nx_range[1] // 32 + 1)) * 32
         ny = int(rng.integers(ny_range[0] // 32, ny_range[1] // 32 + 1)) * 32
-        sc = mitigation_scenario(nx, ny, rng, shore, dx=dx, name="ensemble_%02d" % s)
+        sc = mitigation_scenario(nx, ny, rng, shore, dx=dx, land_width=land_width, name="ensemble_%02d" % s)
         sc.t_end = t_end
         out.append(sc)
     return out
