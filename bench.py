@@ -127,6 +127,57 @@ def cpu_baseline(sc, budget_s: float = 12.0):
             % (steps, sc.nx, sc.ny, oracle.num_threads())}
 
 
+def ensemble_bench(swe, W, torch, steps: int = 20):
+    """C4: the 64-scenario mitigation ensemble advanced by one persistent
+    batched launch per run, against the same 64 scenarios stepped one after
+    another by the single-scenario path, on the same GPU."""
+    ens = W.mitigation_ensemble()
+    cells = sum(sc.cells for sc in ens)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with swe.Batch(len(ens), 150 << 30, ens[0], stream=stream.cuda_stream) as b:
+        for sc in ens:
+            b.admit(sc)
+        b.run(2)
+        b.poll()
+        ev[0].record(stream)
+        b.run(steps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        assert b.status() == swe.OK
+    solvers = [swe.Solver(sc, precision=swe.F32, stream=stream.cuda_stream) for sc in ens]
+    for s in solvers:
+        s.step(2)
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    for s in solvers:
+        s.step(steps)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    for s in solvers:
+        s.close()
+    tb = ev[0].elapsed_time(ev[1]) / 1e3
+    ts = ev[2].elapsed_time(ev[3]) / 1e3
+    return {"scenarios": len(ens), "cells": cells, "steps": steps,
+            "batched_cell_updates_per_s": cells * steps / tb, "sequential_cell_updates_per_s": cells * steps / ts,
+            "speedup_batched_vs_sequential": ts / tb, "launches_batched": 1, "launches_sequential": 3 * steps * len(ens)}
+
+
+def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: float = 20.0):
+    """C5 (bounded sample): Poisson requests, N log-uniform in [256, 2048],
+    coast and hills as the ensemble, 150 GB budget, continuous batching."""
+    from paper_2301_12010_gb300.serve import Server
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for rate in rates:
+        reqs = W.serving_requests(rate=rate, count=count, horizon=horizon)
+        with Server(reqs[0].scenario, nslots=64, budget_bytes=150 << 30, k_steps=50, stream=stream) as srv:
+            rep = srv.serve(reqs)
+        out["%g_req_per_s" % rate] = rep.summary()
+    return {"sample": "%d requests per rate, %g s simulated horizon (config horizon 600 s)" % (count, horizon),
+            "rates": out}
+
+
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle on the host cores, each step one
     RK3 step of a 512 x 512 window (the inflow edge) of the coastal DEM."""
@@ -169,6 +220,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -277,6 +330,10 @@ def main():
                     "how": "swe_set_state(pinned FP64 host) + swe_step(1) + swe_get_state(pinned FP64 host)"},
             "sim": {"t": diag["t"], "steps": diag["steps"], "last_dt": diag["last_dt"]},
         }
+        if ws == 1 and not args.no_ensemble:
+            line["ensemble"] = ensemble_bench(swe, W, torch)
+        if ws == 1 and not args.no_serving:
+            line["serving"] = serving_bench(swe, W, torch)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(sc)
         print(json.dumps(line), flush=True)

@@ -58,6 +58,7 @@ struct swe_batch {
   std::map<int, cudaGraphExec_t> graphs;
   double timeout_s = 1.0;
   unsigned extra = 0;
+  double cfl = 0.4;  // CFL number in the slots' device scalars
   int sticky = SWE_OK;
 };
 
@@ -231,7 +232,7 @@ int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, co
   if (e == cudaSuccess) e = import_plane<float>(sl.staging, true, sl.fd.hu[0], nullptr, zr, sl.nx, sl.ny, sl.pitch, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sl.staging, hv, nb, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = import_plane<float>(sl.staging, true, sl.fd.hv[0], nullptr, zr, sl.nx, sl.ny, sl.pitch, b->stream);
-  if (e == cudaSuccess) e = reset_scalars(b->d_sc + s, 0.0, 0.4, t_end, b->stream);
+  if (e == cudaSuccess) e = reset_scalars(b->d_sc + s, 0.0, b->cfl, t_end, b->stream);
   if (e == cudaSuccess) e = state_stats<float>(sl.fd, sl.p, b->d_sc + s, b->stream);
   if (e != cudaSuccess) {
     cudaFreeAsync(sl.mem, b->stream);
@@ -252,9 +253,12 @@ int swe_batch_run(swe_batch *b, int32_t k_steps, double cfl) {
   if (b->sticky != SWE_OK) return b->sticky;
   if (k_steps == 0) return SWE_OK;
   cudaError_t e = cudaSuccess;
-  for (int s = 0; s < b->nslots && e == cudaSuccess; ++s)
-    if (b->slots[s].live) e = set_cfl(b->d_sc + s, cfl, b->stream);
-  if (e != cudaSuccess) return bfail(b, e);
+  if (cfl != b->cfl) {
+    for (int s = 0; s < b->nslots && e == cudaSuccess; ++s)
+      if (b->slots[s].live) e = set_cfl(b->d_sc + s, cfl, b->stream);
+    if (e != cudaSuccess) return bfail(b, e);
+    b->cfl = cfl;
+  }
   auto it = b->graphs.find(k_steps);
   if (it == b->graphs.end()) {
     cudaGraph_t g = nullptr;

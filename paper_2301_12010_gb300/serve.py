@@ -1,0 +1,132 @@
+"""Continuous-batching serving loop over the batch ABI.
+
+Requests (scenario solves of different sizes) arrive on a wall-clock
+timeline.  Between K-step macro-launches the loop admits waiting requests in
+arrival order as slots and HBM budget free up (swe_batch_admit; states stay
+resident on the device), launches one persistent kernel that advances every
+live scenario (swe_batch_run), and retires the scenarios that reached their
+horizon (swe_batch_retire: result copied to the host).  Work of requests that
+arrive while others run overlaps on the device.  Latency is arrival ->
+result on the host.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from collections import deque
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import Batch, slot_bytes
+
+
+@dataclasses.dataclass
+class Result:
+    index: int
+    arrival: float      # s, on the loop's clock
+    admitted: float
+    finished: float
+    cells: int
+    steps: int
+    t: float
+    mass: float
+    runup_max: float
+    state: Optional[tuple] = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclasses.dataclass
+class Report:
+    results: List[Result]
+    wall: float
+    macro_launches: int
+    max_live: int
+    cell_updates: float
+
+    def latency_ms(self, q: float) -> float:
+        lat = np.array([r.latency for r in self.results]) * 1e3
+        return float(np.percentile(lat, q)) if len(lat) else float("nan")
+
+    def summary(self) -> Dict[str, float]:
+        return {"requests": len(self.results), "p50_ms": self.latency_ms(50), "p99_ms": self.latency_ms(99),
+                "throughput_cell_updates_per_s": self.cell_updates / self.wall if self.wall > 0 else 0.0,
+                "wall_s": self.wall, "macro_launches": self.macro_launches, "max_live_slots": self.max_live}
+
+
+class Server:
+    """A serving loop with nslots slots and an HBM budget (bytes)."""
+
+    def __init__(self, template, nslots: int = 64, budget_bytes: int = 150 << 30, k_steps: int = 50,
+                 cfl: float = 0.4, stream: Optional[int] = None, tile: int = 0, keep_state: bool = False):
+        self.batch = Batch(nslots, budget_bytes, template, stream=stream, tile=tile)
+        self.k = int(k_steps)
+        self.cfl = float(cfl)
+        self.keep_state = keep_state
+
+    def close(self):
+        self.batch.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def serve(self, requests: Sequence, time_scale: float = 1.0, max_wall: Optional[float] = None) -> Report:
+        """requests: objects with .arrival (s) and .scenario (with .t_end).
+        time_scale compresses the arrival timeline (arrival / time_scale)."""
+        order = sorted(range(len(requests)), key=lambda k: requests[k].arrival)
+        incoming = deque(order)
+        waiting: deque = deque()
+        live: Dict[int, tuple] = {}  # slot -> (request index, admitted time)
+        results: List[Result] = []
+        launches = 0
+        max_live = 0
+        cell_updates = 0.0
+        steps_seen: Dict[int, int] = {}
+        t0 = time.perf_counter()
+        while incoming or waiting or live:
+            now = time.perf_counter() - t0
+            if max_wall is not None and now > max_wall:
+                break
+            while incoming and requests[incoming[0]].arrival / time_scale <= now:
+                waiting.append(incoming.popleft())
+            # admit in arrival order while slots and budget allow
+            while waiting:
+                k = waiting[0]
+                sc = requests[k].scenario
+                slot = self.batch.try_admit(sc)
+                if slot is None:
+                    break
+                waiting.popleft()
+                live[slot] = (k, time.perf_counter() - t0)
+                steps_seen[slot] = 0
+            max_live = max(max_live, len(live))
+            if not live:
+                if incoming:
+                    wait = requests[incoming[0]].arrival / time_scale - (time.perf_counter() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.05))
+                continue
+            self.batch.run(self.k, self.cfl)
+            launches += 1
+            for slot in self.batch.poll():
+                k, adm = live.pop(slot)
+                d = self.batch.diagnostics(slot, check=False)
+                st, m, r = self.batch.retire(slot, want_state=self.keep_state)
+                sc = requests[k].scenario
+                fin = time.perf_counter() - t0
+                results.append(Result(k, requests[k].arrival / time_scale, adm, fin, sc.cells, d["steps"], d["t"],
+                                      m, r, st))
+                cell_updates += float(sc.cells) * d["steps"]
+        wall = time.perf_counter() - t0
+        return Report(results, wall, launches, max_live, cell_updates)
+
+
+def budget_for(requests: Sequence) -> int:
+    """Device bytes needed to hold every request at once."""
+    return int(sum(slot_bytes(r.scenario.nx, r.scenario.ny) for r in requests))
