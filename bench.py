@@ -135,7 +135,8 @@ def ensemble_bench(swe, W, torch, steps: int = 20):
     cells = sum(sc.cells for sc in ens)
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    with swe.Batch(len(ens), 150 << 30, ens[0], stream=stream.cuda_stream) as b:
+    best, ms_shapes = swe.autotune([(sc.nx, sc.ny) for sc in ens], precision=swe.F32, batch=True, steps=3)
+    with swe.Batch(len(ens), 150 << 30, ens[0], stream=stream.cuda_stream, tile=0) as b:
         for sc in ens:
             b.admit(sc)
         b.run(2)
@@ -158,9 +159,27 @@ def ensemble_bench(swe, W, torch, steps: int = 20):
         s.close()
     tb = ev[0].elapsed_time(ev[1]) / 1e3
     ts = ev[2].elapsed_time(ev[3]) / 1e3
-    return {"scenarios": len(ens), "cells": cells, "steps": steps,
+    return {"scenarios": len(ens), "cells": cells, "steps": steps, "batch_tile": best, "autotune_ms": ms_shapes,
             "batched_cell_updates_per_s": cells * steps / tb, "sequential_cell_updates_per_s": cells * steps / ts,
             "speedup_batched_vs_sequential": ts / tb, "launches_batched": 1, "launches_sequential": 3 * steps * len(ens)}
+
+
+def fp64_bench(swe, W, torch, sc, steps: int = 10):
+    """The same coastal-DEM workload with FP64 state and arithmetic (the
+    parity path; GB300's FP64 rate is a small fraction of FP32)."""
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with swe.Solver(sc, precision=swe.F64, stream=stream.cuda_stream) as s:
+        s.step(2)
+        s.sync()
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.sync()
+    ms = e0.elapsed_time(e1)
+    return {"value": sc.cells * steps / (ms / 1e3), "unit": "cell-updates/s", "steps": steps,
+            "ms_per_step": ms / steps, "dtype": "f64"}
 
 
 def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: float = 20.0):
@@ -222,6 +241,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -247,6 +267,10 @@ def main():
 
     sc = W.coastal_dem(n=args.n)
     stream = torch.cuda.current_stream()
+    tune = None
+    if args.tile == 0:
+        best, ms_shapes = swe.autotune([(sc.nx, sc.ny)], precision=swe.F32, steps=5)
+        tune = {"best": best, "ms_per_step": ms_shapes, "shapes": swe.tile_shapes()}
     solver = swe.Solver(sc, precision=swe.F32, stream=stream.cuda_stream, tile=args.tile)
     solver.step(args.warmup)
     solver.sync()
@@ -323,6 +347,7 @@ def main():
                              "bytes_per_cell_stage": BYTES_PER_CELL_STAGE[dom],
                              "step_frac": (108.0 * cells * args.steps * ws / (ms_max / 1e3) / 1e9) / hbm_peak},
             "stage_ms": stage_ms,
+            "autotune": tune,
             "gpu_launches": 3 * args.steps,
             "clocks": clk,
             "e2e": {"value": e2e_v, "unit": "cell-updates/s", "h2d_bytes_per_step": 3 * 8 * cells,
@@ -330,6 +355,8 @@ def main():
                     "how": "swe_set_state(pinned FP64 host) + swe_step(1) + swe_get_state(pinned FP64 host)"},
             "sim": {"t": diag["t"], "steps": diag["steps"], "last_dt": diag["last_dt"]},
         }
+        if ws == 1 and not args.no_fp64:
+            line["fp64"] = fp64_bench(swe, W, torch, sc)
         if ws == 1 and not args.no_ensemble:
             line["ensemble"] = ensemble_bench(swe, W, torch)
         if ws == 1 and not args.no_serving:

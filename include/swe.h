@@ -169,6 +169,23 @@ int swe_tile_shape(int k, int32_t *tx, int32_t *ty, int32_t *threads);
  * (*ms_total) and of each stage kernel (ms_stage[3], may be NULL). */
 int swe_time_stages(swe_handle *s, int32_t n, double cfl, double *ms_total, double *ms_stage);
 
+/* Tile-shape autotuner (native timing loop).  Times every compiled tile
+ * shape for `steps` RK3 steps on a synthetic moving-water scenario: of grid
+ * grids[0] on the single-scenario path (mode 0), or of all ngrids grids in
+ * one batch (mode 1, FP32).  Returns the fastest shape in *best_tile and the
+ * milliseconds per step of each shape in ms_per_step[swe_tile_count()] (may be
+ * NULL; -1 for a shape that does not fit), and records the winner in a JSON
+ * cache ($SWE_AUTOTUNE_CACHE, default ~/.cache/swe_gb300_autotune.json) keyed
+ * by GPU name, precision, mode and size bucket (log2 of the cell count; one
+ * entry for batches).  swe_create and swe_batch_create use the cached shape
+ * when params->tile == 0 (shape 1 if there is none).  Allocates and frees
+ * its own scratch handles; synchronises. */
+int swe_autotune(const swe_grid *grids, int32_t ngrids, int32_t precision, int32_t mode, int32_t steps,
+                 int32_t *best_tile, double *ms_per_step);
+
+/* Cached shape for (precision, mode, cell count), or 0 if none. */
+int swe_autotune_lookup(int32_t precision, int32_t mode, double cells);
+
 /* ----------------------------------------------------------------------
  * Batched ensemble and continuous-batching serving (FP32, walls).
  * A batch holds up to nslots independent scenarios ("slots") of any grid

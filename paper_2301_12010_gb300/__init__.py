@@ -97,6 +97,9 @@ def _load() -> ctypes.CDLL:
         "swe_batch_status": (ip, [H]),
         "swe_batch_set_barrier": (ip, [H, ctypes.c_double, ctypes.c_int32]),
         "swe_batch_destroy": (ip, [H]),
+        "swe_autotune": (ip, [ctypes.POINTER(Grid), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                              ctypes.POINTER(ctypes.c_int32), dp]),
+        "swe_autotune_lookup": (ip, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -258,6 +261,18 @@ def _diag_dict(d: Diag) -> Dict[str, float]:
     return dict(t=d.t, steps=int(d.steps), last_dt=d.last_dt, alpha_x=d.alpha_x, alpha_y=d.alpha_y,
                 clamp_mass=d.clamp_mass, boundary_mass=d.boundary_mass, runup_now=d.runup_now,
                 runup_max=d.runup_max, status=int(d.status), tile=int(d.tile))
+
+
+def autotune(shapes, precision: int = F32, batch: bool = False, steps: int = 10):
+    """Time every compiled tile shape (C++ timing loop) on synthetic scenarios
+    of the given (nx, ny) grid sizes; the winner goes to the autotune cache and
+    is used by Solver / Batch created with tile=0.  Returns (best, ms_per_step)."""
+    grids = (Grid * len(shapes))(*[Grid(int(nx), int(ny)) for nx, ny in shapes])
+    best = ctypes.c_int32()
+    ms = (ctypes.c_double * lib.swe_tile_count())()
+    _check(lib.swe_autotune(grids, len(shapes), int(precision), 1 if batch else 0, int(steps), ctypes.byref(best), ms),
+           "swe_autotune")
+    return best.value, list(ms)
 
 
 def slot_bytes(nx: int, ny: int) -> int:

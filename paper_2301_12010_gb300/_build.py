@@ -29,6 +29,7 @@ UNITS: List[Tuple[str, List[str], str]] = [
     ("swe_noalloc.cu", [], "swe_noalloc.o"),
     ("swe_batch_kernels.cu", [], "swe_batch_kernels.o"),
     ("swe_batch.cu", [], "swe_batch.o"),
+    ("swe_autotune.cu", [], "swe_autotune.o"),
 ]
 
 

@@ -229,7 +229,11 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   s->prm = *params;
   s->prec = params->precision;
   s->elem = s->prec == SWE_F64 ? 8 : 4;
-  s->tile = params->tile > 0 ? params->tile : 1;
+  if (params->tile > 0) s->tile = params->tile;
+  else {
+    const int cached = swe_autotune_lookup(params->precision, 0, (double)grid->nx * grid->ny);
+    s->tile = cached > 0 ? cached : 1;
+  }
   s->stream = (cudaStream_t)params->stream;
   const int align = 32;  // elements: 128 B rows in FP32, 256 B in FP64
   s->pitch = ((s->nx + align - 1) / align) * align;
@@ -255,6 +259,7 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   ph.h_dry32 = thr32(params->h_dry);
   ph.h_wet32 = thr32(params->h_wet);
   for (int k = 0; k < 4; ++k) ph.bc[k] = params->bc[k];
+  finish_phys(ph);
 
   const size_t plane = (size_t)s->pitch * s->ny * s->elem;
   const size_t plane_al = (plane + 255) & ~(size_t)255;

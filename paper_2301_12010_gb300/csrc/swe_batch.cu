@@ -94,6 +94,7 @@ Phys phys_of(const swe_params &q, double dx, double dy) {
   ph.h_dry32 = thr32(q.h_dry);
   ph.h_wet32 = thr32(q.h_wet);
   for (int k = 0; k < 4; ++k) ph.bc[k] = q.bc[k];
+  finish_phys(ph);
   return ph;
 }
 
@@ -157,7 +158,11 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
   b->nslots = nslots;
   b->budget = hbm_budget_bytes;
   b->prm = *params;
-  b->tile = params->tile > 0 ? params->tile : 1;
+  if (params->tile > 0) b->tile = params->tile;
+  else {
+    const int cached = swe_autotune_lookup(SWE_F32, 1, 0.0);
+    b->tile = cached > 0 ? cached : 1;
+  }
   b->stream = (cudaStream_t)params->stream;
   b->slots.resize(nslots);
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);

@@ -58,6 +58,13 @@ struct DevScalars {
   unsigned active;                  // batch: slot is live
 };
 
+// Derived constants of the stage arithmetic, precomputed on the host in the
+// state's precision (keeps FP64 work out of the FP32 kernels).
+template <typename T>
+struct Consts {
+  T g, zref, eps12, inv6dx, g12dx, inv6dy, g12dy, gn2, hf4;
+};
+
 // Physical and numerical parameters, constant over a run.
 struct Phys {
   double g, n2, h_dry, h_wet, h_film, hf4, weno_eps, fixed_dt, z_ref;
@@ -66,7 +73,33 @@ struct Phys {
   double dx, dy;
   float h_dry32, h_wet32, h_film32;  // smallest floats whose double value is >= h_dry / h_wet / h_film
   int bc[4];
+  Consts<float> c32;
+  Consts<double> c64;
 };
+
+template <typename T>
+__host__ __device__ __forceinline__ const Consts<T> &consts(const Phys &p);
+template <>
+__host__ __device__ __forceinline__ const Consts<float> &consts<float>(const Phys &p) { return p.c32; }
+template <>
+__host__ __device__ __forceinline__ const Consts<double> &consts<double>(const Phys &p) { return p.c64; }
+
+// Fill the derived constants of a Phys (host side, once).
+inline void finish_phys(Phys &p) {
+  Consts<double> c;
+  c.g = p.g;
+  c.zref = p.z_ref;
+  c.eps12 = 12.0 * p.weno_eps;
+  c.inv6dx = 1.0 / (6.0 * p.dx);
+  c.g12dx = p.g / (12.0 * p.dx);
+  c.inv6dy = 1.0 / (6.0 * p.dy);
+  c.g12dy = p.g / (12.0 * p.dy);
+  c.gn2 = p.g * p.n2;
+  c.hf4 = p.hf4;
+  p.c64 = c;
+  p.c32 = {(float)c.g, (float)c.zref, (float)c.eps12, (float)c.inv6dx, (float)c.g12dx, (float)c.inv6dy,
+           (float)c.g12dy, (float)c.gn2, (float)c.hf4};
+}
 
 template <typename T>
 struct Field {
@@ -445,6 +478,139 @@ struct Window {
   }
 };
 
+// ------------------------------------------------- packed FP32 (f32x2) path
+// Components 0 (mass) and 1 (normal momentum) of a sweep share every stencil
+// position, so their reconstructions run as float2 pairs with the packed
+// FP32 instructions of sm_100+ (one issue slot for two lanes); component 2
+// stays scalar.  Each lane follows the same operation sequence as the scalar
+// reconstruction below, so both lanes round exactly like scalar code.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(Num<float>::rcp(a.x), Num<float>::rcp(a.y)); }
+
+// Scalar FP32 reconstruction with the explicit operation sequence of weno5p.
+__device__ __forceinline__ float weno5s(float v0, float v1, float v2, float v3, float v4, float q0, float q1, float q2,
+                                        float &a0, float &a1, float &a2, float &rdn) {
+  const float e0 = fmaf(3.f, v2, fmaf(-4.f, v1, v0));
+  const float e1 = fmaf(-1.f, v3, v1);
+  const float e2 = fmaf(-4.f, v3, fmaf(3.f, v2, v4));
+  const float r0 = Num<float>::rcp(fmaf(3.f * e0, e0, q0));
+  const float r1 = Num<float>::rcp(fmaf(3.f * e1, e1, q1));
+  const float r2 = Num<float>::rcp(fmaf(3.f * e2, e2, q2));
+  a0 = r0 * r0;
+  a1 = r1 * r1;
+  a2 = r2 * r2;
+  rdn = Num<float>::rcp(fmaf(0.3f, a2, fmaf(0.6f, a1, 0.1f * a0)));
+  const float p0 = fmaf(1.1f, v2, fmaf(-0.7f, v1, 0.2f * v0));
+  const float p1 = fmaf(1.2f, v3, fmaf(3.0f, v2, -0.6f * v1));
+  const float p2 = fmaf(-0.3f, v4, fmaf(1.5f, v3, 0.6f * v2));
+  return fmaf(a2, p2, fmaf(a1, p1, a0 * p0)) * rdn;
+}
+
+__device__ __forceinline__ float2 weno5p(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float2 q0, float2 q1,
+                                         float2 q2, float2 &a0, float2 &a1, float2 &a2, float2 &rdn) {
+  const float2 e0 = fma2(f2(3.f), v2, fma2(f2(-4.f), v1, v0));
+  const float2 e1 = fma2(f2(-1.f), v3, v1);
+  const float2 e2 = fma2(f2(-4.f), v3, fma2(f2(3.f), v2, v4));
+  const float2 r0 = rcp2(fma2(mul2(f2(3.f), e0), e0, q0));
+  const float2 r1 = rcp2(fma2(mul2(f2(3.f), e1), e1, q1));
+  const float2 r2 = rcp2(fma2(mul2(f2(3.f), e2), e2, q2));
+  a0 = mul2(r0, r0);
+  a1 = mul2(r1, r1);
+  a2 = mul2(r2, r2);
+  rdn = rcp2(fma2(f2(0.3f), a2, fma2(f2(0.6f), a1, mul2(f2(0.1f), a0))));
+  const float2 p0 = fma2(f2(1.1f), v2, fma2(f2(-0.7f), v1, mul2(f2(0.2f), v0)));
+  const float2 p1 = fma2(f2(1.2f), v3, fma2(f2(3.0f), v2, mul2(f2(-0.6f), v1)));
+  const float2 p2 = fma2(f2(-0.3f), v4, fma2(f2(1.5f), v3, mul2(f2(0.6f), v2)));
+  return mul2(fma2(a2, p2, fma2(a1, p1, mul2(a0, p0))), rdn);
+}
+
+__device__ __forceinline__ float weighted6s(float v0, float v1, float v2, float v3, float v4, float a0, float a1,
+                                            float a2, float rdn) {
+  const float p0 = fmaf(1.1f, v2, fmaf(-0.7f, v1, 0.2f * v0));
+  const float p1 = fmaf(1.2f, v3, fmaf(3.0f, v2, -0.6f * v1));
+  const float p2 = fmaf(-0.3f, v4, fmaf(1.5f, v3, 0.6f * v2));
+  return fmaf(a2, p2, fmaf(a1, p1, a0 * p0)) * rdn;
+}
+
+__device__ __forceinline__ float qwins(float a, float b, float c, float eps12) {
+  const float d2 = fmaf(-2.f, b, a) + c;
+  return fmaf(13.f * d2, d2, eps12);
+}
+__device__ __forceinline__ float2 qwinp(float2 a, float2 b, float2 c, float2 eps12) {
+  const float2 d2 = add2(fma2(f2(-2.f), b, a), c);
+  return fma2(mul2(f2(13.f), d2), d2, eps12);
+}
+
+// Packed FP32 window: (component 0, component 1) as float2, component 2 scalar.
+struct WindowP {
+  float2 fp01[6], fm01[6];
+  float fp2[6], fm2[6], bw[6];
+  float2 qp01[5], qm01[5];
+  float qp2[5], qm2[5];
+  __device__ __forceinline__ void put(int q, const float *bha, const float *bqn, const float *bqt, const float *bb,
+                                      int o, float alpha, float g, float zref, const Phys &p) {
+    const float ha = bha[o], qn = bqn[o], qt = bqt[o], b = bb[o];
+    const float d = still_depth(b, zref);
+    const float h = ha + d;
+    float un = 0.f;
+    if (!Num<float>::below(h, p.h_dry32, p.h_dry)) un = qn * Num<float>::rcp(h);
+    const float pres = 0.5f * g * ha * (h + d);
+    // F = (qn, qn un + pres, qt un), Q = (ha, qn, qt); f+- = F/2 +- (alpha/2) Q
+    const float2 hF = mul2(f2(0.5f), make_float2(qn, fmaf(qn, un, pres)));
+    const float2 hQ = mul2(f2(0.5f * alpha), make_float2(ha, qn));
+    fp01[q] = add2(hF, hQ);
+    fm01[q] = fma2(f2(-1.f), hQ, hF);
+    const float hF2 = 0.5f * (qt * un), hQ2 = (0.5f * alpha) * qt;
+    fp2[q] = hF2 + hQ2;
+    fm2[q] = hF2 - hQ2;
+    bw[q] = b;
+  }
+  __device__ __forceinline__ void window_terms(int s, float eps12) {
+    qp01[s] = qwinp(fp01[s - 1], fp01[s], fp01[s + 1], f2(eps12));
+    qm01[s] = qwinp(fm01[s - 1], fm01[s], fm01[s + 1], f2(eps12));
+    qp2[s] = qwins(fp2[s - 1], fp2[s], fp2[s + 1], eps12);
+    qm2[s] = qwins(fm2[s - 1], fm2[s], fm2[s + 1], eps12);
+  }
+  __device__ __forceinline__ void shift() {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      fp01[q] = fp01[q + 1];
+      fm01[q] = fm01[q + 1];
+      fp2[q] = fp2[q + 1];
+      fm2[q] = fm2[q + 1];
+      bw[q] = bw[q + 1];
+    }
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+      qp01[q] = qp01[q + 1];
+      qm01[q] = qm01[q + 1];
+      qp2[q] = qp2[q + 1];
+      qm2[q] = qm2[q + 1];
+    }
+  }
+  __device__ __forceinline__ void face(float F6[3], float &B12) const {
+    float2 a0, a1, a2, rp, c0, c1, c2, rm;
+    const float2 Fp = weno5p(fp01[0], fp01[1], fp01[2], fp01[3], fp01[4], qp01[1], qp01[2], qp01[3], a0, a1, a2, rp);
+    const float2 Fm = weno5p(fm01[5], fm01[4], fm01[3], fm01[2], fm01[1], qm01[4], qm01[3], qm01[2], c0, c1, c2, rm);
+    const float2 F01 = add2(Fp, Fm);
+    F6[0] = F01.x;
+    F6[1] = F01.y;
+    // bed with the weights of component 1 (the .y lanes)
+    B12 = weighted6s(bw[0], bw[1], bw[2], bw[3], bw[4], a0.y, a1.y, a2.y, rp.y) +
+          weighted6s(bw[5], bw[4], bw[3], bw[2], bw[1], c0.y, c1.y, c2.y, rm.y);
+    float s0, s1, s2, sr, t0, t1, t2, tr;
+    const float Gp = weno5s(fp2[0], fp2[1], fp2[2], fp2[3], fp2[4], qp2[1], qp2[2], qp2[3], s0, s1, s2, sr);
+    const float Gm = weno5s(fm2[5], fm2[4], fm2[3], fm2[2], fm2[1], qm2[4], qm2[3], qm2[2], t0, t1, t2, tr);
+    F6[2] = Gp + Gm;
+  }
+};
+
+template <typename T> struct WindowOf { using type = Window<T>; };
+template <> struct WindowOf<float> { using type = WindowP; };
+
 // One strip: faces k = 0..S (face k at the left of strip cell k).  Returns
 // dF[c][k] = 6 (Fhat_c(k+1) - Fhat_c(k)) and db[k] = 12 (bhat(k+1) - bhat(k))
 // for the S cells, and adds the mass flux through the domain edges that the
@@ -453,7 +619,7 @@ template <typename T, int S>
 __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T *bqt, const T *bb, int o0, int st,
                                             T alpha, T g, T zref, T eps12, const Phys &p, int ia, int n,
                                             bool edge_ok, T dF[3][S], T db[S], T &edge) {
-  Window<T> win;
+  typename WindowOf<T>::type win;
 #pragma unroll
   for (int q = 0; q < 5; ++q) win.put(q, bha, bqn, bqt, bb, o0 + q * st, alpha, g, zref, p);
 #pragma unroll
@@ -496,7 +662,7 @@ struct Acc {
 // body in the instruction stream).
 template <typename T, int TX, int TY, int NT, int S, int STAGE>
 __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p, int i0, int j0, const T *box,
-                                             T *sL, double dt, T alx, T aly, Acc<T> &acc) {
+                                             T *sL, T tdt, T rcap, T alx, T aly, Acc<T> &acc) {
   using G = TileGeom<T, TX, TY>;
   static_assert(TX % S == 0 && TY % S == 0, "strip length must divide the tile");
   static_assert((TX / S) * TY == NT && (TY / S) * TX == NT, "one strip per thread in both passes");
@@ -504,7 +670,8 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
   const int tid = threadIdx.x;
   const int nx = io.nx, ny = io.ny;
   const T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
-  const T g = T(p.g), zref = T(p.z_ref), eps12 = T(12.0 * p.weno_eps);
+  const Consts<T> &K = consts<T>(p);
+  const T g = K.g, zref = K.zref, eps12 = K.eps12;
   // x pass: lane l of warp w takes row 8*(w % (TY/8)) + l/4 and strip 4*(w / (TY/8)) + l%4
   const int w = tid >> 5, l = tid & 31;
   const int xr = 8 * (w % (TY / 8)) + (l >> 2);
@@ -535,8 +702,8 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
                       X ? 1 : G::P, X ? alx : aly, g, zref, eps12, p, X ? i0 + xc0 : j0 + yr0, X ? nx : ny,
                       X ? (j0 + xr < ny) : (i < nx), dF, db, acc.edge);
     if (X) {
-      const T inv6dx = T(1.0 / (6.0 * p.dx));
-      const T g12dx = T(p.g / (12.0 * p.dx));
+      const T inv6dx = K.inv6dx;
+      const T g12dx = K.g12dx;
 #pragma unroll
       for (int k = 0; k < S; ++k) {
         const int o = xr * G::LP + xc0 + k;
@@ -549,11 +716,9 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
       continue;
     }
     // y pass epilogue: sources, RK combination, post rule (dF[1] is hv, dF[2] hu)
-    const T inv6dy = T(1.0 / (6.0 * p.dy));
-    const T g12dy = T(p.g / (12.0 * p.dy));
-    const T tdt = T(dt);
-    const T rcap = dt > 0.0 ? T(1.0 / dt) : T(0);
-    const T gn2 = T(p.g * p.n2);
+    const T inv6dy = K.inv6dy;
+    const T g12dy = K.g12dy;
+    const T gn2 = K.gn2;
     const bool friction = p.n2 > 0.0;
     const T wrk = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
 #pragma unroll
@@ -571,7 +736,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
         if (friction && !Num<T>::below(h, p.h_dry32, p.h_dry)) {
           const T q = Num<T>::sqrt_(hu * hu + hv * hv);
           T kap = gn2 * q * Num<T>::rcp(Num<T>::pow73(h));
-          kap = kap > rcap ? rcap : kap;
+          kap = kap > rcap ? rcap : kap;  // rcap = 1/dt
           Lhu -= kap * hu;
           Lhv -= kap * hv;
         }
@@ -589,7 +754,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
         else {
           if (Num<T>::below(nh, p.h_film32, p.h_film)) {  // film: bounded velocity
             const T h2 = nh * nh;
-            const T f = T(1.4142135623730951) * h2 * Num<T>::rsqrt_(h2 * h2 + T(p.hf4));
+            const T f = T(1.4142135623730951) * h2 * Num<T>::rsqrt_(h2 * h2 + K.hf4);
             nhu *= f;
             nhv *= f;
           }
@@ -732,8 +897,9 @@ __device__ void stage_persistent(const StageIO<T> &io, const Phys &p, DevScalars
   __syncthreads();
   if (red.skip) return;
   const double dt = red.dt;
+  const T tdt = T(dt), rcap = dt > 0.0 ? T(1.0 / dt) : T(0);
   const T alx = T(red.a[0][0]), aly = T(red.a[0][1]);
-  const T zref = T(p.z_ref);
+  const T zref = consts<T>(p).zref;
   const T eta_in = T(red.eta_in[0]);
   const T u_in = (p.bc[0] == BC_INFLOW) ? T(red.eta_in[0] * sqrt(p.g / p.inflow_depth)) : T(0);
   T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
@@ -753,7 +919,7 @@ __device__ void stage_persistent(const StageIO<T> &io, const Phys &p, DevScalars
       patch_box<T, TX, TY, NT>(io, p, i0, j0, box, zref, eta_in, u_in);
       __syncthreads();
     }
-    tile_compute<T, TX, TY, NT, S, STAGE>(io, p, i0, j0, box, sL, dt, alx, aly, acc);
+    tile_compute<T, TX, TY, NT, S, STAGE>(io, p, i0, j0, box, sL, tdt, rcap, alx, aly, acc);
     __syncthreads();
   }
   cp_wait<0>();
@@ -861,7 +1027,7 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
   int cur = -1;
   bool lead = false, skip = true;
   double dt = 0.0;
-  T alx = T(0), aly = T(0), eta_in = T(0), u_in = T(0);
+  T tdt = T(0), rcap = T(0), alx = T(0), aly = T(0), eta_in = T(0), u_in = T(0);
   Acc<T> acc;
   int item = blockIdx.x;
   if (item < total) {
@@ -894,6 +1060,8 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
       lead = (sl.first_item % G0) == (int)blockIdx.x;
       skip = s_skip != 0u;
       dt = red.dt;
+      tdt = T(dt);
+      rcap = dt > 0.0 ? T(1.0 / dt) : T(0);
       alx = T(red.a[0][0]);
       aly = T(red.a[0][1]);
       eta_in = T(red.eta_in[0]);
@@ -915,10 +1083,10 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
       const int tiles_x = sl.tiles_x;
       const int i0 = (t % tiles_x) * TX, j0 = (t / tiles_x) * TY;
       if (i0 == 0 || j0 == 0 || i0 + TX + 3 > s_io.nx || j0 + TY + 3 > s_io.ny) {
-        patch_box<T, TX, TY, NT>(s_io, sp, i0, j0, box, T(sp.z_ref), eta_in, u_in);
+        patch_box<T, TX, TY, NT>(s_io, sp, i0, j0, box, consts<T>(sp).zref, eta_in, u_in);
         __syncthreads();
       }
-      tile_compute<T, TX, TY, NT, S, STAGE>(s_io, sp, i0, j0, box, sL, dt, alx, aly, acc);
+      tile_compute<T, TX, TY, NT, S, STAGE>(s_io, sp, i0, j0, box, sL, tdt, rcap, alx, aly, acc);
     }
     __syncthreads();
   }
