@@ -20,17 +20,17 @@ LIB = os.path.join(PKG, "libswe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 
-# (source, extra flags, object name)
-UNITS: List[Tuple[str, List[str], str]] = [
-    ("swe_kernels.cu", ["-DSWE_PREC=32"], "swe_kernels_f32.o"),
-    ("swe_kernels.cu", ["-DSWE_PREC=64"], "swe_kernels_f64.o"),
-    ("swe_api.cu", [], "swe_api.o"),
-    ("swe_aux.cu", [], "swe_aux.o"),
-    ("swe_noalloc.cu", [], "swe_noalloc.o"),
-    ("swe_batch_kernels.cu", [], "swe_batch_kernels.o"),
-    ("swe_batch.cu", [], "swe_batch.o"),
-    ("swe_autotune.cu", [], "swe_autotune.o"),
-]
+# (source, extra flags, object name): one unit per (precision, tile shape) for
+# the stage kernels and one per shape for the batch kernel, compiled in parallel
+SHAPES = (1, 2, 3, 4, 5)
+UNITS: List[Tuple[str, List[str], str]] = (
+    [("swe_kernels.cu", ["-DSWE_PREC=%d" % p, "-DSWE_SHAPE=%d" % k], "swe_kernels_f%d_s%d.o" % (p, k))
+     for p in (32, 64) for k in SHAPES]
+    + [("swe_batch_kernels.cu", ["-DSWE_SHAPE=%d" % k], "swe_batch_kernels_s%d.o" % k) for k in SHAPES]
+    + [("swe_shapes.cu", [], "swe_shapes.o"), ("swe_api.cu", [], "swe_api.o"), ("swe_aux.cu", [], "swe_aux.o"),
+       ("swe_noalloc.cu", [], "swe_noalloc.o"), ("swe_batch.cu", [], "swe_batch.o"),
+       ("swe_autotune.cu", [], "swe_autotune.o")]
+)
 
 
 def nvcc() -> str:
@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False, extra: List[str] | None = 
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
         return r.stdout + r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(UNITS), max(2, os.cpu_count() or 2))) as ex:
         logs = list(ex.map(compile_unit, UNITS))
     if verbose:
         for l in logs:

@@ -1,14 +1,22 @@
-// swe_batch_kernels.cu -- the persistent multi-scenario kernel: k RK3 steps
-// of every live scenario of a batch in one cooperative launch, the three
-// stages separated by a bounded grid barrier.  FP32, one instantiation per
-// tile shape.
-#include "swe_batch.h"
+// swe_batch_kernels.cu -- the persistent multi-scenario kernel for one tile
+// shape (SWE_SHAPE): k RK3 steps of every live scenario of a batch in one
+// cooperative launch, the three stages separated by a bounded grid barrier.
+// FP32.
+#ifndef SWE_SHAPE
+#define SWE_SHAPE 1
+#endif
+#include "swe_core.cuh"
+#include "swe_launch.h"
 
 namespace swe {
 
-template <int TX, int TY, int NT, int S, int MINB>
-__global__ void __launch_bounds__(NT, MINB)
+using P = ShapeP<SWE_SHAPE>;
+
+// Templated on the shape index so that every unit's kernel has a distinct name.
+template <int K>
+__global__ void __launch_bounds__(ShapeP<K>::NT, ShapeP<K>::MINB32)
     batch_kernel(const BatchSlot<float> *slots, BatchCtl *ctl, int k_steps) {
+  using P = ShapeP<K>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RedSmem red;
   __shared__ Phys sp;
@@ -16,59 +24,42 @@ __global__ void __launch_bounds__(NT, MINB)
   const int nslots = *(volatile int *)&ctl->nslots;
   const int total = *(volatile int *)&ctl->total_items;
   for (int k = 0; k < k_steps; ++k) {
-    batch_stage<float, TX, TY, NT, S, 1>(slots, nslots, total, smem, red, sp);
+    batch_stage<float, P::TX, P::TY, P::NT, P::S, 1>(slots, nslots, total, smem, red, sp);
     if (!grid_barrier(ctl, gridDim.x)) return;
-    batch_stage<float, TX, TY, NT, S, 2>(slots, nslots, total, smem, red, sp);
+    batch_stage<float, P::TX, P::TY, P::NT, P::S, 2>(slots, nslots, total, smem, red, sp);
     if (!grid_barrier(ctl, gridDim.x)) return;
-    batch_stage<float, TX, TY, NT, S, 3>(slots, nslots, total, smem, red, sp);
+    batch_stage<float, P::TX, P::TY, P::NT, P::S, 3>(slots, nslots, total, smem, red, sp);
     if (!grid_barrier(ctl, gridDim.x)) return;
   }
 }
 
-template <int TX, int TY, int NT, int S, int MINB>
-struct BatchShape {
-  static constexpr size_t smem = TileGeom<float, TX, TY>::BYTES;
-  static cudaError_t resident(int *per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<TX, TY, NT, S, MINB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<TX, TY, NT, S, MINB>, NT, smem);
-  }
-  static cudaError_t launch(const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, cudaStream_t st) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, batch_kernel<TX, TY, NT, S, MINB>, slots, ctl, k);
-  }
-};
-
-using B1 = BatchShape<32, 32, 128, 8, 3>;
-using B2 = BatchShape<64, 32, 256, 8, 1>;
-using B3 = BatchShape<32, 64, 256, 8, 1>;
-
-cudaError_t batch_resident(int shape, int *per_sm) {
-  switch (shape) {
-    case 1: return B1::resident(per_sm);
-    case 2: return B2::resident(per_sm);
-    case 3: return B3::resident(per_sm);
-  }
-  return cudaErrorInvalidValue;
+namespace {
+constexpr size_t kSmem = TileGeom<float, P::TX, P::TY>::BYTES;
 }
 
-cudaError_t batch_launch(int shape, const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, cudaStream_t st) {
-  switch (shape) {
-    case 1: return B1::launch(slots, ctl, k, grid, st);
-    case 2: return B2::launch(slots, ctl, k, grid, st);
-    case 3: return B3::launch(slots, ctl, k, grid, st);
-  }
-  return cudaErrorInvalidValue;
+#define SWE_CAT2(a, b) a##b
+#define SWE_CAT(a, b) SWE_CAT2(a, b)
+
+cudaError_t SWE_CAT(batch_resident_, SWE_SHAPE)(int *per_sm) {
+  cudaError_t e =
+      cudaFuncSetAttribute(batch_kernel<SWE_SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<SWE_SHAPE>, P::NT, kSmem);
+}
+
+cudaError_t SWE_CAT(batch_launch_, SWE_SHAPE)(const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid,
+                                              cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(P::NT);
+  cfg.dynamicSmemBytes = kSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_kernel<SWE_SHAPE>, slots, ctl, k);
 }
 
 }  // namespace swe

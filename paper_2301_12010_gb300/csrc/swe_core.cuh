@@ -666,16 +666,21 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
   using G = TileGeom<T, TX, TY>;
   static_assert(TX % S == 0 && TY % S == 0, "strip length must divide the tile");
   static_assert((TX / S) * TY == NT && (TY / S) * TX == NT, "one strip per thread in both passes");
-  static_assert(TY % 8 == 0 && (TX / S) % 4 == 0, "x-pass warp covers 8 rows x 4 strips");
+  // x pass: a warp covers RW rows x SW strips; with the box row pitch = 1 mod 8
+  // the lanes' window loads hit distinct banks (8 rows x 4 strips of 8 cells,
+  // or 16 rows x 2 strips of 16 cells)
+  constexpr int SW = (S >= 16) ? 2 : 4, RW = 32 / SW;
+  static_assert(TY % RW == 0 && (TX / S) % SW == 0 && (TY / RW) * ((TX / S) / SW) == NT / 32,
+                "x-pass warps tile the rows and strips");
   const int tid = threadIdx.x;
   const int nx = io.nx, ny = io.ny;
   const T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
   const Consts<T> &K = consts<T>(p);
   const T g = K.g, zref = K.zref, eps12 = K.eps12;
-  // x pass: lane l of warp w takes row 8*(w % (TY/8)) + l/4 and strip 4*(w / (TY/8)) + l%4
+  // x pass: lane l of warp w takes row RW*(w % (TY/RW)) + l/SW and strip SW*(w / (TY/RW)) + l%SW
   const int w = tid >> 5, l = tid & 31;
-  const int xr = 8 * (w % (TY / 8)) + (l >> 2);
-  const int xc0 = (4 * (w / (TY / 8)) + (l & 3)) * S;
+  const int xr = RW * (w % (TY / RW)) + l / SW;
+  const int xc0 = (SW * (w / (TY / RW)) + l % SW) * S;
   // y pass: thread takes column tid % TX and strip tid / TX
   const int yc = tid % TX, yr0 = (tid / TX) * S;
   const int i = i0 + yc;
@@ -992,7 +997,7 @@ __device__ __forceinline__ int slot_of_item(const BatchSlot<T> *slots, int n, in
 }
 
 template <typename T>
-__device__ __forceinline__ StageIO<T> io_of(const Field<T> &fd, int stage) {
+__host__ __device__ __forceinline__ StageIO<T> io_of(const Field<T> &fd, int stage) {
   StageIO<T> io;
   const int in = stage - 1, out = stage % 3;
   io.b = fd.b;

@@ -12,6 +12,38 @@ struct TileShape {
   int tx, ty, threads;
 };
 
+// Compiled tile shapes: (index, TX, TY, threads, strip length S, CTAs per SM
+// asked of the register allocator in FP32, in FP64).  One translation unit
+// per (precision, shape) builds the stage kernels, one per shape the batch
+// kernel.
+#define SWE_SHAPES(X)              \
+  X(1, 32, 32, 128, 8, 3, 2)       \
+  X(2, 64, 32, 256, 8, 1, 1)       \
+  X(3, 32, 64, 256, 8, 1, 1)       \
+  X(4, 32, 32, 128, 8, 2, 1)       \
+  X(5, 64, 64, 256, 16, 1, 1)
+
+template <int K>
+struct ShapeP;
+#define SWE_PICK(K, TX_, TY_, NT_, S_, M32_, M64_)                                                   \
+  template <>                                                                                    \
+  struct ShapeP<K> {                                                                             \
+    static constexpr int TX = TX_, TY = TY_, NT = NT_, S = S_, MINB32 = M32_, MINB64 = M64_;    \
+  };
+SWE_SHAPES(SWE_PICK)
+#undef SWE_PICK
+
+#define SWE_DECL(K, TX_, TY_, NT_, S_, M32_, M64_)                                                   \
+  template <typename T>                                                                          \
+  cudaError_t prepare_shape_##K();                                                               \
+  template <typename T>                                                                          \
+  cudaError_t launch_shape_##K(const Field<T> &fd, const Phys &p, DevScalars *sc, int stage,      \
+                               cudaStream_t st);                                                 \
+  cudaError_t batch_resident_##K(int *per_sm);                                                   \
+  cudaError_t batch_launch_##K(const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, cudaStream_t st);
+SWE_SHAPES(SWE_DECL)
+#undef SWE_DECL
+
 int num_shapes();
 const TileShape *shape(int k);  // k = 1 .. num_shapes()
 size_t shape_smem(int k, int elem_bytes);
@@ -38,5 +70,8 @@ template <typename T>
 cudaError_t prepare_shape(int k);
 template <typename T>
 cudaError_t launch_stage(int k, const Field<T> &fd, const Phys &p, DevScalars *sc, int stage, cudaStream_t st);
+// CTAs per SM of the batch kernel for a shape, and one cooperative launch.
+cudaError_t batch_resident(int shape, int *per_sm);
+cudaError_t batch_launch(int shape, const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, cudaStream_t st);
 
 }  // namespace swe

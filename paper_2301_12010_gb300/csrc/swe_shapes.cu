@@ -1,0 +1,74 @@
+// swe_shapes.cu -- the table of compiled tile shapes and the dispatch from a
+// shape index to its per-shape kernels.
+#include "swe_launch.h"
+
+namespace swe {
+
+static const TileShape kShapes[] = {
+#define SWE_ROW(K, TX, TY, NT, S, M32, M64) {TX, TY, NT},
+    SWE_SHAPES(SWE_ROW)
+#undef SWE_ROW
+};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+int num_shapes() { return kNumShapes; }
+const TileShape *shape(int k) { return (k >= 1 && k <= kNumShapes) ? &kShapes[k - 1] : nullptr; }
+
+size_t shape_smem(int k, int elem) {
+  switch (k) {
+#define SWE_CASE(K, TX, TY, NT, S, M32, M64) \
+  case K: return elem == 8 ? TileGeom<double, TX, TY>::BYTES : TileGeom<float, TX, TY>::BYTES;
+    SWE_SHAPES(SWE_CASE)
+#undef SWE_CASE
+  }
+  return 0;
+}
+
+template <typename T>
+cudaError_t prepare_shape(int k) {
+  switch (k) {
+#define SWE_CASE(K, TX, TY, NT, S, M32, M64) \
+  case K: return prepare_shape_##K<T>();
+    SWE_SHAPES(SWE_CASE)
+#undef SWE_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_stage(int k, const Field<T> &fd, const Phys &p, DevScalars *sc, int stage, cudaStream_t st) {
+  switch (k) {
+#define SWE_CASE(K, TX, TY, NT, S, M32, M64) \
+  case K: return launch_shape_##K<T>(fd, p, sc, stage, st);
+    SWE_SHAPES(SWE_CASE)
+#undef SWE_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t batch_resident(int k, int *per_sm) {
+  switch (k) {
+#define SWE_CASE(K, TX, TY, NT, S, M32, M64) \
+  case K: return batch_resident_##K(per_sm);
+    SWE_SHAPES(SWE_CASE)
+#undef SWE_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t batch_launch(int k, const BatchSlot<float> *slots, BatchCtl *ctl, int steps, int grid, cudaStream_t st) {
+  switch (k) {
+#define SWE_CASE(K, TX, TY, NT, S, M32, M64) \
+  case K: return batch_launch_##K(slots, ctl, steps, grid, st);
+    SWE_SHAPES(SWE_CASE)
+#undef SWE_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t prepare_shape<float>(int);
+template cudaError_t prepare_shape<double>(int);
+template cudaError_t launch_stage<float>(int, const Field<float> &, const Phys &, DevScalars *, int, cudaStream_t);
+template cudaError_t launch_stage<double>(int, const Field<double> &, const Phys &, DevScalars *, int, cudaStream_t);
+
+}  // namespace swe

@@ -68,4 +68,5 @@ def test_tile_shapes(swe):
     shapes = swe.tile_shapes()
     assert len(shapes) >= 3
     for tx, ty, nt in shapes:
-        assert (tx // 8) * ty == nt and (ty // 8) * tx == nt
+        # one strip of S = 8 or 16 cells per thread in both sweep directions
+        assert any((tx // S) * ty == nt and (ty // S) * tx == nt for S in (8, 16))

@@ -47,7 +47,7 @@ def batch_run(scs, steps, tile=0, runs=(20, 15)):
         return [(b.get_state(s), b.diagnostics(s)) for s in slots]
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5])
 def test_batch_result_is_the_same_alone_and_in_the_mix(tile):
     # each scenario keeps its own wave speeds, dt and time: bit-for-bit the
     # same whether it runs alone or with the others

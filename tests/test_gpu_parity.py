@@ -49,14 +49,15 @@ def run_oracle(sc, steps):
 
 
 # ------------------------------------------------------------------ FP64
-def test_fp64_tile_that_does_not_fit_is_rejected():
-    # the 32x64 shape needs more shared memory than a CTA may use in FP64
+@pytest.mark.parametrize("tile", [3, 5])
+def test_fp64_tile_that_does_not_fit_is_rejected(tile):
+    # these shapes need more shared memory than a CTA may use in FP64
     with pytest.raises(swe.SweError) as ei:
-        swe.Solver(W.gaussian_hump(n=32), precision=swe.F64, stream=stream(), tile=3)
+        swe.Solver(W.gaussian_hump(n=32), precision=swe.F64, stream=stream(), tile=tile)
     assert ei.value.code == swe.EINVAL
 
 
-@pytest.mark.parametrize("tile", [1, 2])
+@pytest.mark.parametrize("tile", [1, 2, 4])
 def test_fp64_hump_128(tile):
     sc = W.gaussian_hump()
     ref = run_oracle(sc, 200)
@@ -68,7 +69,7 @@ def test_fp64_hump_128(tile):
 
 
 @pytest.mark.parametrize("shape", [(77, 45), (3, 3), (37, 4), (130, 97)])
-@pytest.mark.parametrize("tile", [1, 2])
+@pytest.mark.parametrize("tile", [1, 2, 4])
 def test_fp64_ragged_random(shape, tile):
     nx, ny = shape
     rng = np.random.default_rng(nx * 1000 + ny)
@@ -123,7 +124,7 @@ def test_fp64_planar_beach_full_5000_steps():
 
 
 # ------------------------------------------------------------------ FP32
-@pytest.mark.parametrize("tile", [1, 2, 3])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5])
 def test_fp32_hump_128(tile):
     sc = W.gaussian_hump()
     ref = run_oracle(sc, 200)
@@ -133,7 +134,7 @@ def test_fp32_hump_128(tile):
 
 
 @pytest.mark.parametrize("shape", [(77, 45), (3, 3), (37, 4), (130, 97)])
-@pytest.mark.parametrize("tile", [1, 2, 3])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5])
 def test_fp32_ragged_random(shape, tile):
     nx, ny = shape
     rng = np.random.default_rng(nx * 1000 + ny)
