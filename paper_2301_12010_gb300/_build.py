@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -20,9 +21,20 @@ LIB = os.path.join(PKG, "libswe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 
+
+
+def _shapes() -> Tuple[int, ...]:
+    """Indices of the tile shapes declared in the SWE_SHAPES table of swe_launch.h."""
+    with open(os.path.join(CSRC, "swe_launch.h")) as f:
+        text = f.read()
+    table = text[text.index("#define SWE_SHAPES(X)"):]
+    table = table[:table.index("\n\n")]
+    return tuple(int(k) for k in re.findall(r"\bX\((\d+),", table))
+
+
 # (source, extra flags, object name): one unit per (precision, tile shape) for
 # the stage kernels and one per shape for the batch kernel, compiled in parallel
-SHAPES = (1, 2, 3, 4, 5)
+SHAPES = _shapes()
 UNITS: List[Tuple[str, List[str], str]] = (
     [("swe_kernels.cu", ["-DSWE_PREC=%d" % p, "-DSWE_SHAPE=%d" % k], "swe_kernels_f%d_s%d.o" % (p, k))
      for p in (32, 64) for k in SHAPES]
@@ -41,7 +53,7 @@ def nvcc() -> str:
 
 
 def _sources() -> List[str]:
-    out = []
+    out = [os.path.abspath(__file__)]
     for d in (CSRC, os.path.join(ROOT, "include")):
         for f in os.listdir(d):
             if f.endswith((".cu", ".cuh", ".h")):

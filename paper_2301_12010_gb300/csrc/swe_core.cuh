@@ -62,7 +62,12 @@ struct DevScalars {
 // state's precision (keeps FP64 work out of the FP32 kernels).
 template <typename T>
 struct Consts {
-  T g, zref, eps12, inv6dx, g12dx, inv6dy, g12dy, gn2, hf4;
+  T g, zref, eps12;
+  T pg;          // sqrt(3)/4 g: pressure factor of the carried split fluxes
+  T rfx, rfy;    // 1 / (6 sqrt(3) dx), 1 / (6 sqrt(3) dy): carried flux sums to dF/dx
+  T g12dx, g12dy;  // g / (12 dx), g / (12 dy): bed source from 12 bhat differences
+  T ewx, ewy;    // dy / (6 sqrt(3)), dx / (6 sqrt(3)): edge flux sums to m^3/s
+  T gn2, hf4;
 };
 
 // Physical and numerical parameters, constant over a run.
@@ -89,16 +94,20 @@ inline void finish_phys(Phys &p) {
   Consts<double> c;
   c.g = p.g;
   c.zref = p.z_ref;
+  const double s3 = 1.7320508075688772;  // sqrt(3)
   c.eps12 = 12.0 * p.weno_eps;
-  c.inv6dx = 1.0 / (6.0 * p.dx);
+  c.pg = 0.25 * s3 * p.g;
+  c.rfx = 1.0 / (6.0 * s3 * p.dx);
+  c.rfy = 1.0 / (6.0 * s3 * p.dy);
   c.g12dx = p.g / (12.0 * p.dx);
-  c.inv6dy = 1.0 / (6.0 * p.dy);
   c.g12dy = p.g / (12.0 * p.dy);
+  c.ewx = p.dy / (6.0 * s3);
+  c.ewy = p.dx / (6.0 * s3);
   c.gn2 = p.g * p.n2;
   c.hf4 = p.hf4;
   p.c64 = c;
-  p.c32 = {(float)c.g, (float)c.zref, (float)c.eps12, (float)c.inv6dx, (float)c.g12dx, (float)c.inv6dy,
-           (float)c.g12dy, (float)c.gn2, (float)c.hf4};
+  p.c32 = {(float)c.g,   (float)c.zref,  (float)c.eps12, (float)c.pg,  (float)c.rfx, (float)c.rfy,
+           (float)c.g12dx, (float)c.g12dy, (float)c.ewx,  (float)c.ewy, (float)c.gn2, (float)c.hf4};
 }
 
 template <typename T>
@@ -143,48 +152,98 @@ template <> struct Num<double> {
   static __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
 };
 
-// WENO5-JS (Jiang & Shu 1996) at the right face of v2, scaled by 6.
-// With t_k = 12 eps + 12 beta_k = q_k + 3 e_k^2, where q_k = 13 D2_k^2 + 12 eps
-// is the second-difference part of the stencil's smoothness (cached by the
-// caller: it depends on the 3-cell window only) and e_k its first-difference
-// part, the weights d_k / t_k^2 have the ratios of d_k / (eps + beta_k)^2.
-// Returns 6 W; a_k = 1/t_k^2 and rdn = 1 / sum d_k a_k are returned for
-// applying the same weights to the bed.  Linear weights d_k are folded into
-// the candidate coefficients (wc*).
-template <typename T>
-__device__ __forceinline__ T weno5q(T v0, T v1, T v2, T v3, T v4, T q0, T q1, T q2, T &a0, T &a1, T &a2,
-                                    T &rdn) {
-  const T e0 = v0 - T(4) * v1 + T(3) * v2;
-  const T e1 = v1 - v3;
-  const T e2 = T(3) * v2 - T(4) * v3 + v4;
-  const T r0 = Num<T>::rcp(T(3) * e0 * e0 + q0);
-  const T r1 = Num<T>::rcp(T(3) * e1 * e1 + q1);
-  const T r2 = Num<T>::rcp(T(3) * e2 * e2 + q2);
-  a0 = r0 * r0;
-  a1 = r1 * r1;
-  a2 = r2 * r2;
-  rdn = Num<T>::rcp(T(0.1) * a0 + T(0.6) * a1 + T(0.3) * a2);
-  // d_k * (6 p_k): 0.1 (2, -7, 11), 0.6 (-1, 5, 2), 0.3 (2, 5, -1)
-  const T p0 = T(0.2) * v0 - T(0.7) * v1 + T(1.1) * v2;
-  const T p1 = T(-0.6) * v1 + T(3.0) * v2 + T(1.2) * v3;
-  const T p2 = T(0.6) * v2 + T(1.5) * v3 - T(0.3) * v4;
-  return (a0 * p0 + a1 * p1 + a2 * p2) * rdn;
+// ------------------------------------------ reconstruction value operations
+// Overloads for FP32 scalars, packed FP32 pairs (float2: the f32x2 FMA, ADD
+// and MUL instructions of sm_100+ issue both lanes in one slot), FP64
+// scalars and FP64 pairs (double2, lane by lane).  sp<V>(c) splats a constant.
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float vrcp(float a) { return Num<float>::rcp(a); }
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ double vmul(double a, double b) { return a * b; }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double vrcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(vrcp(a.x), vrcp(a.y)); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 vrcp(double2 a) { return make_double2(1.0 / a.x, 1.0 / a.y); }
+template <typename V> __device__ __forceinline__ V sp(double c);
+template <> __device__ __forceinline__ float sp<float>(double c) { return (float)c; }
+template <> __device__ __forceinline__ double sp<double>(double c) { return c; }
+template <> __device__ __forceinline__ float2 sp<float2>(double c) { return make_float2((float)c, (float)c); }
+template <> __device__ __forceinline__ double2 sp<double2>(double c) { return make_double2(c, c); }
+template <typename V> __device__ __forceinline__ V vsub(V a, V b) { return vfma(sp<V>(-1.0), b, a); }
+
+// Pair type of a precision: components 0 and 1 of a sweep travel together.
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+  using type = float2;
+  static __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Pair<double> {
+  using type = double2;
+  static __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+};
+
+// ------------------------------------------------------- WENO5 reconstruction
+// Fifth-order WENO of Jiang and Shu (Sec. 2) written in first differences.
+// For the five upwind values v0..v4 of a face (upwind cell v2) let
+// d_j = v_j - v_{j-1}, j = 1..4.  Then
+//   12 beta_k = 13 D_k^2 + 3 E_k^2,  D_k = d_{k+2} - d_{k+1},
+//   E_0 = d_1 - 3 d_2,  E_1 = d_2 + d_3,  E_2 = d_4 - 3 d_3   (signs irrelevant),
+// and the candidate values are 6 p_k = 6 v2 + C_k with
+//   C_0 = 5 d_2 - 2 d_1,  C_1 = d_2 + 2 d_3,  C_2 = 4 d_3 - d_4.
+// The sweep carries the split fluxes times sqrt(3), so that 3 E_k^2 is the
+// square e_k^2 of the same combination of the carried differences and
+// 12 (eps + beta_k) = q_k + e_k^2, where q_k = 13/3 D_k^2 + 12 eps is cached
+// per stencil centre.  With a_k = 1 / (12 (eps + beta_k))^2 and the linear
+// weights gamma = (0.1, 0.6, 0.3), 6 W = 6 v2 + S rdn with
+//   S = sum_k gamma_k a_k C_k,  rdn = 1 / sum_k gamma_k a_k.
+// A_k = (-0.1 a_0, 0.6 a_1, -0.3 a_2) carry the signs of the forms -C_0 =
+// 2 e_0 + d_2, C_1 = e_1 + d_3, -C_2 = e_2 - d_3 and are returned for the bed.
+// MIR: the mirrored side (f- reconstructed from the right), whose differences
+// arrive in the sweep's order, i.e. negated; S comes out negated and rdn is
+// returned negated, so that S rdn is unchanged.  A constant state has all
+// d_j = 0 and reconstructs to exactly v2.
+template <bool MIR, typename V>
+__device__ __forceinline__ V weno_side(V d1, V d2, V d3, V d4, V q0, V q1, V q2, V &A0, V &A1, V &A2, V &rdn) {
+  const V e0 = vfma(sp<V>(-3.0), d2, d1);
+  const V e1 = vadd(d2, d3);
+  const V e2 = vfma(sp<V>(-3.0), d3, d4);
+  const V r0 = vrcp(vfma(e0, e0, q0));
+  const V r1 = vrcp(vfma(e1, e1, q1));
+  const V r2 = vrcp(vfma(e2, e2, q2));
+  A0 = vmul(vmul(r0, r0), sp<V>(-0.1));
+  A1 = vmul(vmul(r1, r1), sp<V>(0.6));
+  A2 = vmul(vmul(r2, r2), sp<V>(-0.3));
+  rdn = vrcp(MIR ? vadd(vsub(A0, A1), A2) : vsub(vsub(A1, A0), A2));
+  const V c0 = vfma(sp<V>(2.0), e0, d2);
+  const V c1 = vadd(e1, d3);
+  const V c2 = vsub(e2, d3);
+  return vfma(A2, c2, vfma(A1, c1, vmul(A0, c0)));
 }
 
-// 6 * (weighted candidate values) of a stencil with given weights.
-template <typename T>
-__device__ __forceinline__ T weighted6(T v0, T v1, T v2, T v3, T v4, T a0, T a1, T a2, T rdn) {
-  const T p0 = T(0.2) * v0 - T(0.7) * v1 + T(1.1) * v2;
-  const T p1 = T(-0.6) * v1 + T(3.0) * v2 + T(1.2) * v3;
-  const T p2 = T(0.6) * v2 + T(1.5) * v3 - T(0.3) * v4;
-  return (a0 * p0 + a1 * p1 + a2 * p2) * rdn;
+// The same weighted sum for other values (the bed) under given weights A_k.
+template <typename V>
+__device__ __forceinline__ V weighted_side(V d1, V d2, V d3, V d4, V A0, V A1, V A2) {
+  const V c0 = vfma(sp<V>(-5.0), d2, vmul(sp<V>(2.0), d1));  // -C_0
+  const V c1 = vfma(sp<V>(2.0), d3, d2);                      //  C_1
+  const V c2 = vfma(sp<V>(-4.0), d3, d4);                     // -C_2
+  return vfma(A2, c2, vfma(A1, c1, vmul(A0, c0)));
 }
 
-// Second-difference smoothness part of the 3-cell window (a, b, c).
-template <typename T>
-__device__ __forceinline__ T qwin(T a, T b, T c, T eps12) {
-  const T d2 = a - T(2) * b + c;
-  return T(13) * d2 * d2 + eps12;
+// q = 13/3 D^2 + 12 eps of the stencil centred between differences a and b.
+template <typename V>
+__device__ __forceinline__ V qterm(V a, V b, V eps12) {
+  const V D = vsub(b, a);
+  return vfma(vmul(sp<V>(13.0 / 3.0), D), D, eps12);
 }
 
 // Carrier N-wave of Eq. (20) entering through the x- edge (peak elevation
@@ -204,77 +263,6 @@ template <typename T>
 __device__ __forceinline__ T still_depth(T b, T zref) {
   T d = zref - b;
   return d > T(0) ? d : T(0);
-}
-
-// State (ha, hu, hv) and bed of cell (i, j), where (i, j) may lie up to 3
-// cells outside the interior in at most one direction (ghosts per boundary
-// type: mirrored walls, the inflow wave, or periodic wrap with bed offset).
-template <typename T>
-__device__ __forceinline__ void load_cell(const T *__restrict__ b, const T *__restrict__ ha,
-                                          const T *__restrict__ hu, const T *__restrict__ hv, int nx, int ny,
-                                          int pitch, const Phys &p, T zref, T eta_in, T u_in, int i, int j, T &ch,
-                                          T &chu, T &chv, T &cb) {
-  int si = i, sj = j;
-  bool fu = false, fv = false, inflow = false, seam = false;
-  T bshift = T(0);
-  if (i < 0) {
-    if (p.bc[0] == BC_PERIODIC) { si = i + nx; bshift = T(-p.b_jump_x); seam = true; }
-    else { si = -1 - i; fu = true; inflow = (p.bc[0] == BC_INFLOW); }
-  } else if (i >= nx) {
-    if (p.bc[1] == BC_PERIODIC) { si = i - nx; bshift = T(p.b_jump_x); seam = true; }
-    else { si = 2 * nx - 1 - i; fu = true; }
-  }
-  if (j < 0) {
-    if (p.bc[2] == BC_PERIODIC) { sj = j + ny; bshift = T(-p.b_jump_y); seam = true; }
-    else { sj = -1 - j; fv = true; }
-  } else if (j >= ny) {
-    if (p.bc[3] == BC_PERIODIC) { sj = j - ny; bshift = T(p.b_jump_y); seam = true; }
-    else { sj = 2 * ny - 1 - j; fv = true; }
-  }
-  const size_t o = (size_t)sj * pitch + si;
-  const T bs = b[o];
-  cb = bs + bshift;
-  if (inflow) {
-    // h = max(eta_in - b, 0), u = eta_in sqrt(g/d0), v = 0; in anomaly form
-    const T dg = still_depth(cb, zref);
-    if (cb < zref) {
-      const T a = eta_in - zref;
-      ch = a > -dg ? a : -dg;
-    } else {
-      const T hg = eta_in - cb;
-      ch = hg > T(0) ? hg : T(0);
-    }
-    chu = (ch + dg) * u_in;
-    chv = T(0);
-  } else {
-    ch = ha[o];
-    chu = hu[o];
-    chv = hv[o];
-    if (seam) ch = (ch + still_depth(bs, zref)) - still_depth(cb, zref);  // same h, new d
-    if (fu) chu = -chu;
-    if (fv) chv = -chv;
-  }
-}
-
-// Split fluxes of one cell in the frame of a sweep: qn is the discharge
-// normal to the faces (hu for x, hv for y) and qt the tangential one.  With
-// h = ha + d and pressure g ha (h + d)/2 = g (h^2 - d^2)/2:
-//   F = (qn, qn un + pressure, qt un),  Q = (ha, qn, qt),  f+- = (F +- alpha Q)/2,
-// i.e. F of Eq. (2) in x and G of Eq. (3) (with its momentum components
-// swapped) in y.
-template <typename T>
-__device__ __forceinline__ void split_cell(T ha, T qn, T qt, T b, T alpha, T g, T zref, const Phys &p, T fp[3],
-                                           T fm[3]) {
-  const T d = still_depth(b, zref);
-  const T h = ha + d;
-  T un = T(0);
-  if (!Num<T>::below(h, p.h_dry32, p.h_dry)) un = qn * Num<T>::rcp(h);
-  const T pres = T(0.5) * g * ha * (h + d);
-  const T F0 = qn, F1 = qn * un + pres, F2 = qt * un;
-  const T q0 = alpha * ha, q1 = alpha * qn, q2 = alpha * qt;
-  fp[0] = T(0.5) * (F0 + q0); fm[0] = T(0.5) * (F0 - q0);
-  fp[1] = T(0.5) * (F1 + q1); fm[1] = T(0.5) * (F1 - q1);
-  fp[2] = T(0.5) * (F2 + q2); fm[2] = T(0.5) * (F2 - q2);
 }
 
 template <typename T> __device__ __forceinline__ T warp_max(T v) {
@@ -425,163 +413,100 @@ __device__ __noinline__ void patch_box(const StageIO<T> &io, const Phys &p, int 
   }
 }
 
-// Sliding WENO5 window along one line of the box (one strip of S cells), in
-// the frame of the sweep.  Slots 0..5 hold cells c0-3+k .. c0+2+k for face k
-// (between slots 2 and 3); qp[s] / qm[s] cache the second-difference
-// smoothness of the 3-cell window centred at slot s for f+ / f-.
+// Sliding window of one strip, in the frame of the sweep.  For face k, which
+// lies between window slots 2 and 3 (cells c0-1+k and c0+k), it holds for each
+// carried value (split fluxes f+ and f- times sqrt 3, and the bed) the
+// differences d[s] = v(slot s) - v(slot s-1), s = 1..5, the second-difference
+// terms q[s] centred at slots 1..4, and the value last put (slot 5).
+// Components 0 and 1 (mass and normal momentum) travel as pairs, component 2
+// (tangential momentum) and the bed as scalars.
+//
+// With the face sums Fs(k) = 6 sqrt(3) Fhat(k) = 6 (f+(2) + f-(3)) + X(k)
+// (X: the WENO corrections of both sides), the difference over the cell at
+// slot 2 is Fs(k) - Fs(k-1) = 6 (d+[2] + d-[3]) + X(k) - X(k-1); for the bed,
+// 12 bhat(k) - 12 bhat(k-1) = 6 (db[2] + db[3]) + Xb(k) - Xb(k-1).
 template <typename T>
 struct Window {
-  T fp[3][6], fm[3][6], bw[6];
-  T qp[3][5], qm[3][5];
-  __device__ __forceinline__ void put(int q, const T *bha, const T *bqn, const T *bqt, const T *bb, int o, T alpha,
-                                      T g, T zref, const Phys &p) {
-    T a[3], m[3];
-    const T b = bb[o];
-    split_cell<T>(bha[o], bqn[o], bqt[o], b, alpha, g, zref, p, a, m);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) { fp[c][q] = a[c]; fm[c][q] = m[c]; }
-    bw[q] = b;
-  }
-  __device__ __forceinline__ void window_terms(int s, T eps12) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      qp[c][s] = qwin(fp[c][s - 1], fp[c][s], fp[c][s + 1], eps12);
-      qm[c][s] = qwin(fm[c][s - 1], fm[c][s], fm[c][s + 1], eps12);
+  using V2 = typename Pair<T>::type;
+  V2 lp01, lm01;
+  T lp2, lm2, lb;
+  V2 dp01[6], dm01[6];
+  T dp2[6], dm2[6], db[6];
+  V2 qp01[5], qm01[5];
+  T qp2[5], qm2[5];
+  V2 xp01;  // X of the previous face
+  T xp2, xb;
+
+  // Put the cell at box offset o into slot s.  sa = sqrt(3)/2 alpha,
+  // pg = sqrt(3)/4 g: with h = ha + d and pressure g ha (h + d)/2,
+  //   F = (qn, qn un + pressure, qt un),  Q = (ha, qn, qt),
+  //   f+- = (F +- alpha Q)/2   (carried times sqrt 3),
+  // i.e. F of Eq. (2) in x and G of Eq. (3), momentum components swapped, in y.
+  template <int s>
+  __device__ __forceinline__ void put(const T *bha, const T *bqn, const T *bqt, const T *bb, int o, T sa, T pg,
+                                      T zref, V2 eps2, T eps1, const Phys &p) {
+    const T ha = bha[o], qn = bqn[o], qt = bqt[o], b = bb[o];
+    const T d = still_depth(b, zref);
+    const T h = ha + d;
+    T un = T(0);
+    if (!Num<T>::below(h, p.h_dry32, p.h_dry)) un = qn * Num<T>::rcp(h);
+    const T f0 = T(0.8660254037844386) * qn;  // sqrt(3)/2 qn
+    const T f1 = fma(f0, un, pg * ha * (h + d));
+    const T f2 = (T(0.8660254037844386) * qt) * un;
+    const V2 F = Pair<T>::mk(f0, f1), Q = Pair<T>::mk(ha, qn);
+    const V2 up = vfma(Pair<T>::mk(sa, sa), Q, F), um = vfma(Pair<T>::mk(-sa, -sa), Q, F);
+    const T up2 = fma(sa, qt, f2), um2 = fma(-sa, qt, f2);
+    if constexpr (s >= 1) {
+      dp01[s] = vsub(up, lp01);
+      dm01[s] = vsub(um, lm01);
+      dp2[s] = up2 - lp2;
+      dm2[s] = um2 - lm2;
+      db[s] = b - lb;
+      if constexpr (s >= 2) {
+        qp01[s - 1] = qterm(dp01[s - 1], dp01[s], eps2);
+        qm01[s - 1] = qterm(dm01[s - 1], dm01[s], eps2);
+        qp2[s - 1] = qterm(dp2[s - 1], dp2[s], eps1);
+        qm2[s - 1] = qterm(dm2[s - 1], dm2[s], eps1);
+      }
     }
+    lp01 = up;
+    lm01 = um;
+    lp2 = up2;
+    lm2 = um2;
+    lb = b;
   }
+
+  // WENO corrections X of face k for components 0-1, 2 and the bed (the bed
+  // with the weights of component 1, the second lane).
+  __device__ __forceinline__ void face(V2 &x01, T &x2, T &x3) const {
+    V2 A0, A1, A2, rp, B0, B1, B2, rm;
+    const V2 Sp = weno_side<false>(dp01[1], dp01[2], dp01[3], dp01[4], qp01[1], qp01[2], qp01[3], A0, A1, A2, rp);
+    const V2 Sm = weno_side<true>(dm01[5], dm01[4], dm01[3], dm01[2], qm01[4], qm01[3], qm01[2], B0, B1, B2, rm);
+    x01 = vfma(Sm, rm, vmul(Sp, rp));
+    const T Bp = weighted_side<T>(db[1], db[2], db[3], db[4], A0.y, A1.y, A2.y);
+    const T Bm = weighted_side<T>(db[5], db[4], db[3], db[2], B0.y, B1.y, B2.y);
+    x3 = fma(Bm, rm.y, Bp * rp.y);
+    T a0, a1, a2, r2p, b0, b1, b2, r2m;
+    const T Gp = weno_side<false>(dp2[1], dp2[2], dp2[3], dp2[4], qp2[1], qp2[2], qp2[3], a0, a1, a2, r2p);
+    const T Gm = weno_side<true>(dm2[5], dm2[4], dm2[3], dm2[2], qm2[4], qm2[3], qm2[2], b0, b1, b2, r2m);
+    x2 = fma(Gm, r2m, Gp * r2p);
+  }
+
+  // Fs(k) of component 0 (mass flux times 6 sqrt 3), for the domain edges.
+  __device__ __forceinline__ T edge_flux(V2 x01) const {
+    const T fp = lp01.x - dp01[5].x - dp01[4].x - dp01[3].x;  // f+ at slot 2
+    const T fm = lm01.x - dm01[5].x - dm01[4].x;              // f- at slot 3
+    return fma(T(6), fp + fm, x01.x);
+  }
+
   __device__ __forceinline__ void shift() {
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) { fp[c][q] = fp[c][q + 1]; fm[c][q] = fm[c][q + 1]; }
-      bw[q] = bw[q + 1];
-    }
-#pragma unroll
-    for (int q = 1; q < 4; ++q)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) { qp[c][q] = qp[c][q + 1]; qm[c][q] = qm[c][q + 1]; }
-  }
-  // face between slots 2 and 3: F6[c] = 6 Fhat_c, B12 = 12 bhat (weights of c = 1)
-  __device__ __forceinline__ void face(T F6[3], T &B12) const {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T a0, a1, a2, rp, c0, c1, c2, rm;
-      const T Fp = weno5q<T>(fp[c][0], fp[c][1], fp[c][2], fp[c][3], fp[c][4], qp[c][1], qp[c][2], qp[c][3], a0,
-                             a1, a2, rp);
-      const T Fm = weno5q<T>(fm[c][5], fm[c][4], fm[c][3], fm[c][2], fm[c][1], qm[c][4], qm[c][3], qm[c][2], c0,
-                             c1, c2, rm);
-      F6[c] = Fp + Fm;
-      if (c == 1)
-        B12 = weighted6<T>(bw[0], bw[1], bw[2], bw[3], bw[4], a0, a1, a2, rp) +
-              weighted6<T>(bw[5], bw[4], bw[3], bw[2], bw[1], c0, c1, c2, rm);
-    }
-  }
-};
-
-// ------------------------------------------------- packed FP32 (f32x2) path
-// Components 0 (mass) and 1 (normal momentum) of a sweep share every stencil
-// position, so their reconstructions run as float2 pairs with the packed
-// FP32 instructions of sm_100+ (one issue slot for two lanes); component 2
-// stays scalar.  Each lane follows the same operation sequence as the scalar
-// reconstruction below, so both lanes round exactly like scalar code.
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(Num<float>::rcp(a.x), Num<float>::rcp(a.y)); }
-
-// Scalar FP32 reconstruction with the explicit operation sequence of weno5p.
-__device__ __forceinline__ float weno5s(float v0, float v1, float v2, float v3, float v4, float q0, float q1, float q2,
-                                        float &a0, float &a1, float &a2, float &rdn) {
-  const float e0 = fmaf(3.f, v2, fmaf(-4.f, v1, v0));
-  const float e1 = fmaf(-1.f, v3, v1);
-  const float e2 = fmaf(-4.f, v3, fmaf(3.f, v2, v4));
-  const float r0 = Num<float>::rcp(fmaf(3.f * e0, e0, q0));
-  const float r1 = Num<float>::rcp(fmaf(3.f * e1, e1, q1));
-  const float r2 = Num<float>::rcp(fmaf(3.f * e2, e2, q2));
-  a0 = r0 * r0;
-  a1 = r1 * r1;
-  a2 = r2 * r2;
-  rdn = Num<float>::rcp(fmaf(0.3f, a2, fmaf(0.6f, a1, 0.1f * a0)));
-  const float p0 = fmaf(1.1f, v2, fmaf(-0.7f, v1, 0.2f * v0));
-  const float p1 = fmaf(1.2f, v3, fmaf(3.0f, v2, -0.6f * v1));
-  const float p2 = fmaf(-0.3f, v4, fmaf(1.5f, v3, 0.6f * v2));
-  return fmaf(a2, p2, fmaf(a1, p1, a0 * p0)) * rdn;
-}
-
-__device__ __forceinline__ float2 weno5p(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float2 q0, float2 q1,
-                                         float2 q2, float2 &a0, float2 &a1, float2 &a2, float2 &rdn) {
-  const float2 e0 = fma2(f2(3.f), v2, fma2(f2(-4.f), v1, v0));
-  const float2 e1 = fma2(f2(-1.f), v3, v1);
-  const float2 e2 = fma2(f2(-4.f), v3, fma2(f2(3.f), v2, v4));
-  const float2 r0 = rcp2(fma2(mul2(f2(3.f), e0), e0, q0));
-  const float2 r1 = rcp2(fma2(mul2(f2(3.f), e1), e1, q1));
-  const float2 r2 = rcp2(fma2(mul2(f2(3.f), e2), e2, q2));
-  a0 = mul2(r0, r0);
-  a1 = mul2(r1, r1);
-  a2 = mul2(r2, r2);
-  rdn = rcp2(fma2(f2(0.3f), a2, fma2(f2(0.6f), a1, mul2(f2(0.1f), a0))));
-  const float2 p0 = fma2(f2(1.1f), v2, fma2(f2(-0.7f), v1, mul2(f2(0.2f), v0)));
-  const float2 p1 = fma2(f2(1.2f), v3, fma2(f2(3.0f), v2, mul2(f2(-0.6f), v1)));
-  const float2 p2 = fma2(f2(-0.3f), v4, fma2(f2(1.5f), v3, mul2(f2(0.6f), v2)));
-  return mul2(fma2(a2, p2, fma2(a1, p1, mul2(a0, p0))), rdn);
-}
-
-__device__ __forceinline__ float weighted6s(float v0, float v1, float v2, float v3, float v4, float a0, float a1,
-                                            float a2, float rdn) {
-  const float p0 = fmaf(1.1f, v2, fmaf(-0.7f, v1, 0.2f * v0));
-  const float p1 = fmaf(1.2f, v3, fmaf(3.0f, v2, -0.6f * v1));
-  const float p2 = fmaf(-0.3f, v4, fmaf(1.5f, v3, 0.6f * v2));
-  return fmaf(a2, p2, fmaf(a1, p1, a0 * p0)) * rdn;
-}
-
-__device__ __forceinline__ float qwins(float a, float b, float c, float eps12) {
-  const float d2 = fmaf(-2.f, b, a) + c;
-  return fmaf(13.f * d2, d2, eps12);
-}
-__device__ __forceinline__ float2 qwinp(float2 a, float2 b, float2 c, float2 eps12) {
-  const float2 d2 = add2(fma2(f2(-2.f), b, a), c);
-  return fma2(mul2(f2(13.f), d2), d2, eps12);
-}
-
-// Packed FP32 window: (component 0, component 1) as float2, component 2 scalar.
-struct WindowP {
-  float2 fp01[6], fm01[6];
-  float fp2[6], fm2[6], bw[6];
-  float2 qp01[5], qm01[5];
-  float qp2[5], qm2[5];
-  __device__ __forceinline__ void put(int q, const float *bha, const float *bqn, const float *bqt, const float *bb,
-                                      int o, float alpha, float g, float zref, const Phys &p) {
-    const float ha = bha[o], qn = bqn[o], qt = bqt[o], b = bb[o];
-    const float d = still_depth(b, zref);
-    const float h = ha + d;
-    float un = 0.f;
-    if (!Num<float>::below(h, p.h_dry32, p.h_dry)) un = qn * Num<float>::rcp(h);
-    const float pres = 0.5f * g * ha * (h + d);
-    // F = (qn, qn un + pres, qt un), Q = (ha, qn, qt); f+- = F/2 +- (alpha/2) Q
-    const float2 hF = mul2(f2(0.5f), make_float2(qn, fmaf(qn, un, pres)));
-    const float2 hQ = mul2(f2(0.5f * alpha), make_float2(ha, qn));
-    fp01[q] = add2(hF, hQ);
-    fm01[q] = fma2(f2(-1.f), hQ, hF);
-    const float hF2 = 0.5f * (qt * un), hQ2 = (0.5f * alpha) * qt;
-    fp2[q] = hF2 + hQ2;
-    fm2[q] = hF2 - hQ2;
-    bw[q] = b;
-  }
-  __device__ __forceinline__ void window_terms(int s, float eps12) {
-    qp01[s] = qwinp(fp01[s - 1], fp01[s], fp01[s + 1], f2(eps12));
-    qm01[s] = qwinp(fm01[s - 1], fm01[s], fm01[s + 1], f2(eps12));
-    qp2[s] = qwins(fp2[s - 1], fp2[s], fp2[s + 1], eps12);
-    qm2[s] = qwins(fm2[s - 1], fm2[s], fm2[s + 1], eps12);
-  }
-  __device__ __forceinline__ void shift() {
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      fp01[q] = fp01[q + 1];
-      fm01[q] = fm01[q + 1];
-      fp2[q] = fp2[q + 1];
-      fm2[q] = fm2[q + 1];
-      bw[q] = bw[q + 1];
+    for (int q = 1; q < 5; ++q) {
+      dp01[q] = dp01[q + 1];
+      dm01[q] = dm01[q + 1];
+      dp2[q] = dp2[q + 1];
+      dm2[q] = dm2[q + 1];
+      db[q] = db[q + 1];
     }
 #pragma unroll
     for (int q = 1; q < 4; ++q) {
@@ -591,55 +516,46 @@ struct WindowP {
       qm2[q] = qm2[q + 1];
     }
   }
-  __device__ __forceinline__ void face(float F6[3], float &B12) const {
-    float2 a0, a1, a2, rp, c0, c1, c2, rm;
-    const float2 Fp = weno5p(fp01[0], fp01[1], fp01[2], fp01[3], fp01[4], qp01[1], qp01[2], qp01[3], a0, a1, a2, rp);
-    const float2 Fm = weno5p(fm01[5], fm01[4], fm01[3], fm01[2], fm01[1], qm01[4], qm01[3], qm01[2], c0, c1, c2, rm);
-    const float2 F01 = add2(Fp, Fm);
-    F6[0] = F01.x;
-    F6[1] = F01.y;
-    // bed with the weights of component 1 (the .y lanes)
-    B12 = weighted6s(bw[0], bw[1], bw[2], bw[3], bw[4], a0.y, a1.y, a2.y, rp.y) +
-          weighted6s(bw[5], bw[4], bw[3], bw[2], bw[1], c0.y, c1.y, c2.y, rm.y);
-    float s0, s1, s2, sr, t0, t1, t2, tr;
-    const float Gp = weno5s(fp2[0], fp2[1], fp2[2], fp2[3], fp2[4], qp2[1], qp2[2], qp2[3], s0, s1, s2, sr);
-    const float Gm = weno5s(fm2[5], fm2[4], fm2[3], fm2[2], fm2[1], qm2[4], qm2[3], qm2[2], t0, t1, t2, tr);
-    F6[2] = Gp + Gm;
-  }
 };
 
-template <typename T> struct WindowOf { using type = Window<T>; };
-template <> struct WindowOf<float> { using type = WindowP; };
-
 // One strip: faces k = 0..S (face k at the left of strip cell k).  Returns
-// dF[c][k] = 6 (Fhat_c(k+1) - Fhat_c(k)) and db[k] = 12 (bhat(k+1) - bhat(k))
-// for the S cells, and adds the mass flux through the domain edges that the
-// strip owns (face -1/2 at k = 0 of the first strip, face n-1/2 at k >= 1).
+// dF[c][k] = Fs_c(k+1) - Fs_c(k) (flux differences times 6 sqrt 3) and
+// db[k] = 12 (bhat(k+1) - bhat(k)) for the S cells, and adds ew times the mass
+// flux sum Fs_0 through the domain edges that the strip owns (face -1/2 at
+// k = 0 of the first strip, face n-1/2 at k >= 1).
 template <typename T, int S>
 __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T *bqt, const T *bb, int o0, int st,
-                                            T alpha, T g, T zref, T eps12, const Phys &p, int ia, int n,
-                                            bool edge_ok, T dF[3][S], T db[S], T &edge) {
-  typename WindowOf<T>::type win;
-#pragma unroll
-  for (int q = 0; q < 5; ++q) win.put(q, bha, bqn, bqt, bb, o0 + q * st, alpha, g, zref, p);
-#pragma unroll
-  for (int q = 1; q < 4; ++q) win.window_terms(q, eps12);
-  T prevF[3], prevB = T(0);
+                                            T alpha, const Consts<T> &K, const Phys &p, int ia, int n, bool edge_ok,
+                                            T ew, T dF[3][S], T db[S], T &edge) {
+  using V2 = typename Pair<T>::type;
+  Window<T> win;
+  const T sa = T(0.8660254037844386) * alpha, pg = K.pg, zref = K.zref, eps1 = K.eps12;
+  const V2 eps2 = Pair<T>::mk(eps1, eps1);
+  win.template put<0>(bha, bqn, bqt, bb, o0, sa, pg, zref, eps2, eps1, p);
+  win.template put<1>(bha, bqn, bqt, bb, o0 + st, sa, pg, zref, eps2, eps1, p);
+  win.template put<2>(bha, bqn, bqt, bb, o0 + 2 * st, sa, pg, zref, eps2, eps1, p);
+  win.template put<3>(bha, bqn, bqt, bb, o0 + 3 * st, sa, pg, zref, eps2, eps1, p);
+  win.template put<4>(bha, bqn, bqt, bb, o0 + 4 * st, sa, pg, zref, eps2, eps1, p);
 #pragma unroll
   for (int k = 0; k <= S; ++k) {
-    win.put(5, bha, bqn, bqt, bb, o0 + (k + 5) * st, alpha, g, zref, p);
-    win.window_terms(4, eps12);
-    T F6[3], B12 = T(0);
-    win.face(F6, B12);
-    if (edge_ok && ((k == 0 && ia == 0) || (k > 0 && ia + k == n))) edge += (k == 0) ? F6[0] : -F6[0];
-    if (k > 0) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) dF[c][k - 1] = F6[c] - prevF[c];
-      db[k - 1] = B12 - prevB;
+    win.template put<5>(bha, bqn, bqt, bb, o0 + (k + 5) * st, sa, pg, zref, eps2, eps1, p);
+    V2 x01;
+    T x2, x3;
+    win.face(x01, x2, x3);
+    if (edge_ok && ((k == 0 && ia == 0) || (k > 0 && ia + k == n))) {
+      const T fe = win.edge_flux(x01) * ew;
+      edge += (k == 0) ? fe : -fe;
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) prevF[c] = F6[c];
-    prevB = B12;
+    if (k > 0) {
+      const V2 d01 = vfma(sp<V2>(6.0), vadd(win.dp01[2], win.dm01[3]), vsub(x01, win.xp01));
+      dF[0][k - 1] = d01.x;
+      dF[1][k - 1] = d01.y;
+      dF[2][k - 1] = fma(T(6), win.dp2[2] + win.dm2[3], x2 - win.xp2);
+      db[k - 1] = fma(T(6), win.db[2] + win.db[3], x3 - win.xb);
+    }
+    win.xp01 = x01;
+    win.xp2 = x2;
+    win.xb = x3;
     win.shift();
   }
 }
@@ -676,7 +592,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
   const int nx = io.nx, ny = io.ny;
   const T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
   const Consts<T> &K = consts<T>(p);
-  const T g = K.g, zref = K.zref, eps12 = K.eps12;
+  const T g = K.g, zref = K.zref;
   // x pass: lane l of warp w takes row RW*(w % (TY/RW)) + l/SW and strip SW*(w / (TY/RW)) + l%SW
   const int w = tid >> 5, l = tid & 31;
   const int xr = RW * (w % (TY / RW)) + l / SW;
@@ -704,24 +620,24 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
     }
     T dF[3][S], db[S];
     sweep_strip<T, S>(bha, X ? bhu : bhv, X ? bhv : bhu, bb, X ? (xr + 3) * G::P + xc0 : yr0 * G::P + yc + 3,
-                      X ? 1 : G::P, X ? alx : aly, g, zref, eps12, p, X ? i0 + xc0 : j0 + yr0, X ? nx : ny,
-                      X ? (j0 + xr < ny) : (i < nx), dF, db, acc.edge);
+                      X ? 1 : G::P, X ? alx : aly, K, p, X ? i0 + xc0 : j0 + yr0, X ? nx : ny,
+                      X ? (j0 + xr < ny) : (i < nx), X ? K.ewx : K.ewy, dF, db, acc.edge);
     if (X) {
-      const T inv6dx = K.inv6dx;
+      const T rfx = K.rfx;
       const T g12dx = K.g12dx;
 #pragma unroll
       for (int k = 0; k < S; ++k) {
         const int o = xr * G::LP + xc0 + k;
         const T ha = bha[(xr + 3) * G::P + xc0 + k + 3];
-        sL[o] = -dF[0][k] * inv6dx;
-        sL[G::NC + o] = -dF[1][k] * inv6dx - g12dx * ha * db[k];
-        sL[2 * G::NC + o] = -dF[2][k] * inv6dx;
+        sL[o] = -dF[0][k] * rfx;
+        sL[G::NC + o] = -dF[1][k] * rfx - g12dx * ha * db[k];
+        sL[2 * G::NC + o] = -dF[2][k] * rfx;
       }
       __syncthreads();
       continue;
     }
     // y pass epilogue: sources, RK combination, post rule (dF[1] is hv, dF[2] hu)
-    const T inv6dy = K.inv6dy;
+    const T rfy = K.rfy;
     const T g12dy = K.g12dy;
     const T gn2 = K.gn2;
     const bool friction = p.n2 > 0.0;
@@ -735,9 +651,9 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
         const T ha = bha[bo], hu = bhu[bo], hv = bhv[bo], bc = bb[bo];
         const T d = still_depth(bc, zref);
         const T h = ha + d;
-        T Lh = sL[o] - dF[0][k] * inv6dy;
-        T Lhu = sL[G::NC + o] - dF[2][k] * inv6dy;
-        T Lhv = sL[2 * G::NC + o] - dF[1][k] * inv6dy - g12dy * ha * db[k];
+        T Lh = sL[o] - dF[0][k] * rfy;
+        T Lhu = sL[G::NC + o] - dF[2][k] * rfy;
+        T Lhv = sL[2 * G::NC + o] - dF[1][k] * rfy - g12dy * ha * db[k];
         if (friction && !Num<T>::below(h, p.h_dry32, p.h_dry)) {
           const T q = Num<T>::sqrt_(hu * hu + hv * hv);
           T kap = gn2 * q * Num<T>::rcp(Num<T>::pow73(h));
@@ -868,7 +784,7 @@ __device__ __forceinline__ void publish(const Phys &p, DevScalars *sc, bool lead
     constexpr double wgt = (STAGE == 3) ? 1.0 : (STAGE == 2 ? 2.0 / 3.0 : 1.0 / 6.0);
     constexpr double wfl = (STAGE == 3) ? 2.0 / 3.0 : 1.0 / 6.0;
     if (dsum != 0.0) atomicAdd(&sc->clamp_mass, wgt * dsum * p.dx * p.dy);
-    if (fsum != 0.0) atomicAdd(&sc->boundary_mass, wfl * dt * fsum * p.dy / 6.0);
+    if (fsum != 0.0) atomicAdd(&sc->boundary_mass, wfl * dt * fsum);
     if (STAGE == 3 && rmax > 0.0) {
       const unsigned long long rb = dbits(rmax);
       atomicMax(&sc->runup_now[__ldcg(&sc->parity)], rb);

@@ -21,7 +21,11 @@ struct TileShape {
   X(2, 64, 32, 256, 8, 1, 1)       \
   X(3, 32, 64, 256, 8, 1, 1)       \
   X(4, 32, 32, 128, 8, 2, 1)       \
-  X(5, 64, 64, 256, 16, 1, 1)
+  X(5, 64, 64, 256, 16, 1, 1)      \
+  X(6, 64, 48, 384, 8, 1, 1)       \
+  X(7, 96, 32, 384, 8, 1, 1)       \
+  X(8, 64, 64, 512, 8, 1, 1)       \
+  X(9, 128, 32, 512, 8, 1, 1)
 
 template <int K>
 struct ShapeP;
