@@ -518,15 +518,16 @@ struct Window {
   }
 };
 
-// One strip: faces k = 0..S (face k at the left of strip cell k).  Returns
-// dF[c][k] = Fs_c(k+1) - Fs_c(k) (flux differences times 6 sqrt 3) and
-// db[k] = 12 (bhat(k+1) - bhat(k)) for the S cells, and adds ew times the mass
-// flux sum Fs_0 through the domain edges that the strip owns (face -1/2 at
-// k = 0 of the first strip, face n-1/2 at k >= 1).
-template <typename T, int S>
+// One strip: faces k = 0..S (face k at the left of strip cell k).  As soon as
+// both faces of strip cell k are known, emit(k, dF0, dF1, dF2, db) receives
+// dF_c = Fs_c(k+1) - Fs_c(k) (flux differences times 6 sqrt 3) and
+// db = 12 (bhat(k+1) - bhat(k)).  Adds ew times the mass flux sum Fs_0
+// through the domain edges that the strip owns (face -1/2 at k = 0 of the
+// first strip, face n-1/2 at k >= 1).
+template <typename T, int S, typename E>
 __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T *bqt, const T *bb, int o0, int st,
                                             T alpha, const Consts<T> &K, const Phys &p, int ia, int n, bool edge_ok,
-                                            T ew, T dF[3][S], T db[S], T &edge) {
+                                            T ew, const E &emit, T &edge) {
   using V2 = typename Pair<T>::type;
   Window<T> win;
   const T sa = T(0.8660254037844386) * alpha, pg = K.pg, zref = K.zref, eps1 = K.eps12;
@@ -548,10 +549,8 @@ __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T 
     }
     if (k > 0) {
       const V2 d01 = vfma(sp<V2>(6.0), vadd(win.dp01[2], win.dm01[3]), vsub(x01, win.xp01));
-      dF[0][k - 1] = d01.x;
-      dF[1][k - 1] = d01.y;
-      dF[2][k - 1] = fma(T(6), win.dp2[2] + win.dm2[3], x2 - win.xp2);
-      db[k - 1] = fma(T(6), win.db[2] + win.db[3], x3 - win.xb);
+      emit(k - 1, d01.x, d01.y, fma(T(6), win.dp2[2] + win.dm2[3], x2 - win.xp2),
+           fma(T(6), win.db[2] + win.db[3], x3 - win.xb));
     }
     win.xp01 = x01;
     win.xp2 = x2;
@@ -565,6 +564,89 @@ template <typename T>
 struct Acc {
   T ax = T(0), ay = T(0), ru = T(0), chk = T(0);
   T deficit = T(0), edge = T(0);  // diagnostics, summed in the state's precision per thread
+};
+
+// Per-cell work of a pass, done as soon as both faces of the cell are known.
+// x pass: store L_x = -dF/dx (+ the bed source of the x momentum).  y pass
+// (dF1 is hv, dF2 hu in the y frame): add L_y and the sources, combine the RK
+// stage, apply the post-stage rule, write the cell and accumulate the wave
+// speeds and diagnostics.
+template <typename T, int TX, int TY, int S, int STAGE>
+struct CellEpilogue {
+  using G = TileGeom<T, TX, TY>;
+  const StageIO<T> &io;
+  const Phys &p;
+  const Consts<T> &K;
+  const T *box;
+  T *sL;
+  bool X;
+  int xr, xc0, yc, yr0, i, j0;
+  T tdt, rcap, wrk;
+  const T (&u0)[3][S];
+  Acc<T> &acc;
+
+  __device__ __forceinline__ void operator()(int k, T dF0, T dF1, T dF2, T dbk) const {
+    const T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
+    if (X) {
+      const int o = xr * G::LP + xc0 + k;
+      const T ha = bha[(xr + 3) * G::P + xc0 + k + 3];
+      sL[o] = -dF0 * K.rfx;
+      sL[G::NC + o] = -dF1 * K.rfx - K.g12dx * ha * dbk;
+      sL[2 * G::NC + o] = -dF2 * K.rfx;
+      return;
+    }
+    const int j = j0 + yr0 + k;
+    if (i >= io.nx || j >= io.ny) return;
+    const int o = (yr0 + k) * G::LP + yc;
+    const int bo = (yr0 + k + 3) * G::P + yc + 3;
+    const T ha = bha[bo], hu = bhu[bo], hv = bhv[bo], bc = bb[bo];
+    const T d = still_depth(bc, K.zref);
+    const T h = ha + d;
+    T Lh = sL[o] - dF0 * K.rfy;
+    T Lhu = sL[G::NC + o] - dF2 * K.rfy;
+    T Lhv = sL[2 * G::NC + o] - dF1 * K.rfy - K.g12dy * ha * dbk;
+    if (p.n2 > 0.0 && !Num<T>::below(h, p.h_dry32, p.h_dry)) {
+      const T q = Num<T>::sqrt_(hu * hu + hv * hv);
+      T kap = K.gn2 * q * Num<T>::rcp(Num<T>::pow73(h));
+      kap = kap > rcap ? rcap : kap;  // rcap = 1/dt
+      Lhu -= kap * hu;
+      Lhv -= kap * hv;
+    }
+    T nha = ha + tdt * Lh, nhu = hu + tdt * Lhu, nhv = hv + tdt * Lhv;
+    const size_t go = (size_t)j * io.pitch + i;
+    if (STAGE != 1) {
+      nha = u0[0][k] + wrk * (nha - u0[0][k]);
+      nhu = u0[1][k] + wrk * (nhu - u0[1][k]);
+      nhv = u0[2][k] + wrk * (nhv - u0[2][k]);
+    }
+    if (nha < -d) { acc.deficit -= nha + d; nha = -d; }
+    const T nh = nha + d;
+    T u = T(0), v = T(0);
+    if (Num<T>::below(nh, p.h_dry32, p.h_dry)) { nhu = T(0); nhv = T(0); }
+    else {
+      if (Num<T>::below(nh, p.h_film32, p.h_film)) {  // film: bounded velocity
+        const T h2 = nh * nh;
+        const T f = T(1.4142135623730951) * h2 * Num<T>::rsqrt_(h2 * h2 + K.hf4);
+        nhu *= f;
+        nhv *= f;
+      }
+      const T rr = Num<T>::rcp(nh);
+      u = nhu * rr;
+      v = nhv * rr;
+    }
+    io.oha[go] = nha;
+    io.ohu[go] = nhu;
+    io.ohv[go] = nhv;
+    const T cel = Num<T>::sqrt_(K.g * nh);
+    const T sx = fabs(u) + cel, sy = fabs(v) + cel;
+    acc.chk += sx + sy;  // non-finite values propagate to the per-CTA check
+    acc.ax = sx > acc.ax ? sx : acc.ax;
+    acc.ay = sy > acc.ay ? sy : acc.ay;
+    if (STAGE == 3 && !Num<T>::below(nh, p.h_wet32, p.h_wet) && bc > T(0)) {
+      const T e = nh + bc;
+      acc.ru = e > acc.ru ? e : acc.ru;
+    }
+  }
 };
 
 // One RK3 stage (Eq. (8), Shu-Osher form, increment form) on one tile whose
@@ -592,7 +674,6 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
   const int nx = io.nx, ny = io.ny;
   const T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
   const Consts<T> &K = consts<T>(p);
-  const T g = K.g, zref = K.zref;
   // x pass: lane l of warp w takes row RW*(w % (TY/RW)) + l/SW and strip SW*(w / (TY/RW)) + l%SW
   const int w = tid >> 5, l = tid & 31;
   const int xr = RW * (w % (TY / RW)) + l / SW;
@@ -601,6 +682,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
   const int yc = tid % TX, yr0 = (tid / TX) * S;
   const int i = i0 + yc;
 
+  const T wrk = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
     const bool X = pass == 0;
@@ -618,85 +700,11 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
         u0[2][k] = ok ? io.hv0[go] : T(0);
       }
     }
-    T dF[3][S], db[S];
+    const CellEpilogue<T, TX, TY, S, STAGE> emit{io, p, K, box, sL, X, xr, xc0, yc, yr0, i, j0, tdt, rcap, wrk, u0, acc};
     sweep_strip<T, S>(bha, X ? bhu : bhv, X ? bhv : bhu, bb, X ? (xr + 3) * G::P + xc0 : yr0 * G::P + yc + 3,
                       X ? 1 : G::P, X ? alx : aly, K, p, X ? i0 + xc0 : j0 + yr0, X ? nx : ny,
-                      X ? (j0 + xr < ny) : (i < nx), X ? K.ewx : K.ewy, dF, db, acc.edge);
-    if (X) {
-      const T rfx = K.rfx;
-      const T g12dx = K.g12dx;
-#pragma unroll
-      for (int k = 0; k < S; ++k) {
-        const int o = xr * G::LP + xc0 + k;
-        const T ha = bha[(xr + 3) * G::P + xc0 + k + 3];
-        sL[o] = -dF[0][k] * rfx;
-        sL[G::NC + o] = -dF[1][k] * rfx - g12dx * ha * db[k];
-        sL[2 * G::NC + o] = -dF[2][k] * rfx;
-      }
-      __syncthreads();
-      continue;
-    }
-    // y pass epilogue: sources, RK combination, post rule (dF[1] is hv, dF[2] hu)
-    const T rfy = K.rfy;
-    const T g12dy = K.g12dy;
-    const T gn2 = K.gn2;
-    const bool friction = p.n2 > 0.0;
-    const T wrk = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
-#pragma unroll
-    for (int k = 0; k < S; ++k) {
-      const int j = j0 + yr0 + k;
-      if (i < nx && j < ny) {
-        const int o = (yr0 + k) * G::LP + yc;
-        const int bo = (yr0 + k + 3) * G::P + yc + 3;
-        const T ha = bha[bo], hu = bhu[bo], hv = bhv[bo], bc = bb[bo];
-        const T d = still_depth(bc, zref);
-        const T h = ha + d;
-        T Lh = sL[o] - dF[0][k] * rfy;
-        T Lhu = sL[G::NC + o] - dF[2][k] * rfy;
-        T Lhv = sL[2 * G::NC + o] - dF[1][k] * rfy - g12dy * ha * db[k];
-        if (friction && !Num<T>::below(h, p.h_dry32, p.h_dry)) {
-          const T q = Num<T>::sqrt_(hu * hu + hv * hv);
-          T kap = gn2 * q * Num<T>::rcp(Num<T>::pow73(h));
-          kap = kap > rcap ? rcap : kap;  // rcap = 1/dt
-          Lhu -= kap * hu;
-          Lhv -= kap * hv;
-        }
-        T nha = ha + tdt * Lh, nhu = hu + tdt * Lhu, nhv = hv + tdt * Lhv;
-        const size_t go = (size_t)j * io.pitch + i;
-        if (STAGE != 1) {
-          nha = u0[0][k] + wrk * (nha - u0[0][k]);
-          nhu = u0[1][k] + wrk * (nhu - u0[1][k]);
-          nhv = u0[2][k] + wrk * (nhv - u0[2][k]);
-        }
-        if (nha < -d) { acc.deficit -= nha + d; nha = -d; }
-        const T nh = nha + d;
-        T u = T(0), v = T(0);
-        if (Num<T>::below(nh, p.h_dry32, p.h_dry)) { nhu = T(0); nhv = T(0); }
-        else {
-          if (Num<T>::below(nh, p.h_film32, p.h_film)) {  // film: bounded velocity
-            const T h2 = nh * nh;
-            const T f = T(1.4142135623730951) * h2 * Num<T>::rsqrt_(h2 * h2 + K.hf4);
-            nhu *= f;
-            nhv *= f;
-          }
-          const T rr = Num<T>::rcp(nh);
-          u = nhu * rr;
-          v = nhv * rr;
-        }
-        io.oha[go] = nha;
-        io.ohu[go] = nhu;
-        io.ohv[go] = nhv;
-        const T cel = Num<T>::sqrt_(g * nh);
-        const T sx = fabs(u) + cel, sy = fabs(v) + cel;
-        acc.chk += sx + sy;  // non-finite values propagate to the per-CTA check
-        acc.ax = sx > acc.ax ? sx : acc.ax;
-        acc.ay = sy > acc.ay ? sy : acc.ay;
-        if (STAGE == 3 && !Num<T>::below(nh, p.h_wet32, p.h_wet) && bc > T(0)) {
-          const T e = nh + bc;
-          acc.ru = e > acc.ru ? e : acc.ru;
-        }
-      }
-    }
+                      X ? (j0 + xr < ny) : (i < nx), X ? K.ewx : K.ewy, emit, acc.edge);
+    if (X) __syncthreads();
   }
 }
 
