@@ -31,6 +31,7 @@
 // buffer reused by the x pass and then the y pass, the x-pass result L_x, and
 // the anomaly ha of the tile's own cells.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -80,6 +81,10 @@ struct Phys {
   int bc[4];
   Consts<float> c32;
   Consts<double> c64;
+  // derived on the host (FP64 work is slow on the device): 1/dx, 1/dy, the
+  // cell area, and the inflow wave's constants (see inflow_eta)
+  double rdx, rdy, area;
+  double in_c0, in_s0, in_o1, in_o2, in_a1, in_a2, in_k1, in_k2, in_uf;
 };
 
 template <typename T>
@@ -108,6 +113,24 @@ inline void finish_phys(Phys &p) {
   p.c64 = c;
   p.c32 = {(float)c.g,   (float)c.zref,  (float)c.eps12, (float)c.pg,  (float)c.rfx, (float)c.rfy,
            (float)c.g12dx, (float)c.g12dy, (float)c.ewx,  (float)c.ewy, (float)c.gn2, (float)c.hf4};
+  p.rdx = 1.0 / p.dx;
+  p.rdy = 1.0 / p.dy;
+  p.area = p.dx * p.dy;
+  // carrier N-wave of Eq. (20): c0 = sqrt(g d0), lambda = T c0, a1 = amp/2,
+  // a2 = a1/3, k1 = 28.416/lambda^2, k2 = 256/lambda^2, read at
+  // s = 1.3 lambda - c0 t, with centres 0.5151125 lambda and 0.2048 lambda;
+  // the inflow velocity is eta sqrt(g/d0)
+  const double c0 = p.inflow_depth > 0.0 ? std::sqrt(p.g * p.inflow_depth) : 0.0;
+  const double lam = p.inflow_period * c0;
+  p.in_c0 = c0;
+  p.in_s0 = 1.3 * lam;
+  p.in_o1 = 0.5151125 * lam;
+  p.in_o2 = 0.2048 * lam;
+  p.in_a1 = 0.5 * p.inflow_amp;
+  p.in_a2 = p.in_a1 / 3.0;
+  p.in_k1 = lam > 0.0 ? 28.416 / (lam * lam) : 0.0;
+  p.in_k2 = lam > 0.0 ? 256.0 / (lam * lam) : 0.0;
+  p.in_uf = p.inflow_depth > 0.0 ? std::sqrt(p.g / p.inflow_depth) : 0.0;
 }
 
 template <typename T>
@@ -246,17 +269,23 @@ __device__ __forceinline__ V qterm(V a, V b, V eps12) {
   return vfma(vmul(sp<V>(13.0 / 3.0), D), D, eps12);
 }
 
-// Carrier N-wave of Eq. (20) entering through the x- edge (peak elevation
-// amp, a1 = amp/2, a2 = a1/3, lambda = T sqrt(g d0)), read at
-// s = 1.3 lambda - c0 t.
-__device__ __forceinline__ double inflow_eta(const Phys &p, double t) {
-  const double c0 = sqrt(p.g * p.inflow_depth);
-  const double lam = p.inflow_period * c0;
-  const double a1 = 0.5 * p.inflow_amp, a2 = a1 / 3.0;
-  const double k1 = 28.416 / (lam * lam), k2 = 256.0 / (lam * lam);
-  const double s = 1.3 * lam - c0 * t;
-  const double q1 = s - 0.5151125 * lam, q2 = s - 0.2048 * lam;
-  return 2.0 * (a1 * exp(-k1 * q1 * q1) - a2 * exp(-k2 * q2 * q2));
+// Carrier N-wave of Eq. (20) entering through the x- edge, with the constants
+// of finish_phys: eta = 2 (a1 exp(-k1 q1^2) - a2 exp(-k2 q2^2)), q = s - centre,
+// s = 1.3 lambda - c0 t.  The phase is taken in FP64 (t is large); the
+// exponentials in the state's precision.
+template <typename T> __device__ __forceinline__ T inflow_eta(const Phys &p, double t);
+template <>
+__device__ __forceinline__ double inflow_eta<double>(const Phys &p, double t) {
+  const double s = p.in_s0 - p.in_c0 * t;
+  const double q1 = s - p.in_o1, q2 = s - p.in_o2;
+  return 2.0 * (p.in_a1 * exp(-p.in_k1 * q1 * q1) - p.in_a2 * exp(-p.in_k2 * q2 * q2));
+}
+template <>
+__device__ __forceinline__ float inflow_eta<float>(const Phys &p, double t) {
+  const double s = p.in_s0 - p.in_c0 * t;
+  const double q1 = s - p.in_o1, q2 = s - p.in_o2;
+  return 2.f * ((float)p.in_a1 * expf((float)(-p.in_k1 * q1 * q1)) -
+                (float)p.in_a2 * expf((float)(-p.in_k2 * q2 * q2)));
 }
 
 template <typename T>
@@ -273,7 +302,7 @@ template <typename T> __device__ __forceinline__ T warp_max(T v) {
   }
   return v;
 }
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -306,16 +335,25 @@ struct TileGeom {
   static constexpr size_t BYTES = sizeof(T) * (size_t)ELEMS;
 };
 
-// Reduction scratch in shared memory (per CTA).
+// Per-stage values broadcast from thread 0 to the CTA, in both precisions.
+enum { SV_DT = 0, SV_RCAP, SV_AX, SV_AY, SV_ETA, SV_UIN, SV_N };
+
+// Reduction scratch and broadcast values in shared memory (per CTA).
 struct RedSmem {
-  double a[32][2];
-  double s[32][2];
-  double r[32];
-  double dt;
-  double eta_in[3];
+  float wf[32][5];    // per-warp partials, FP32 kernels: alpha_x, alpha_y, deficit, edge flux, runup
+  double wd[32][5];   // the same, FP64 kernels
+  double dt;          // time step of the running RK step
+  float v32[SV_N];    // dt, 1/dt, alpha_x, alpha_y, inflow eta, inflow u
+  double v64[SV_N];
   unsigned bad;
   unsigned skip;
 };
+template <typename T> __device__ __forceinline__ T *red_w(RedSmem &r);
+template <> __device__ __forceinline__ float *red_w<float>(RedSmem &r) { return &r.wf[0][0]; }
+template <> __device__ __forceinline__ double *red_w<double>(RedSmem &r) { return &r.wd[0][0]; }
+template <typename T> __device__ __forceinline__ T red_v(const RedSmem &r, int k);
+template <> __device__ __forceinline__ float red_v<float>(const RedSmem &r, int k) { return r.v32[k]; }
+template <> __device__ __forceinline__ double red_v<double>(const RedSmem &r, int k) { return r.v64[k]; }
 
 // The state planes a stage reads and writes.
 template <typename T>
@@ -582,6 +620,7 @@ struct CellEpilogue {
   bool X;
   int xr, xc0, yc, yr0, i, j0;
   T tdt, rcap, wrk;
+  bool friction;  // Manning n > 0
   const T (&u0)[3][S];
   Acc<T> &acc;
 
@@ -605,7 +644,7 @@ struct CellEpilogue {
     T Lh = sL[o] - dF0 * K.rfy;
     T Lhu = sL[G::NC + o] - dF2 * K.rfy;
     T Lhv = sL[2 * G::NC + o] - dF1 * K.rfy - K.g12dy * ha * dbk;
-    if (p.n2 > 0.0 && !Num<T>::below(h, p.h_dry32, p.h_dry)) {
+    if (friction && !Num<T>::below(h, p.h_dry32, p.h_dry)) {
       const T q = Num<T>::sqrt_(hu * hu + hv * hv);
       T kap = K.gn2 * q * Num<T>::rcp(Num<T>::pow73(h));
       kap = kap > rcap ? rcap : kap;  // rcap = 1/dt
@@ -683,6 +722,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
   const int i = i0 + yc;
 
   const T wrk = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
+  const bool friction = p.n2 > 0.0;
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
     const bool X = pass == 0;
@@ -700,7 +740,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
         u0[2][k] = ok ? io.hv0[go] : T(0);
       }
     }
-    const CellEpilogue<T, TX, TY, S, STAGE> emit{io, p, K, box, sL, X, xr, xc0, yc, yr0, i, j0, tdt, rcap, wrk, u0, acc};
+    const CellEpilogue<T, TX, TY, S, STAGE> emit{io, p, K, box, sL, X, xr, xc0, yc, yr0, i, j0, tdt, rcap, wrk, friction, u0, acc};
     sweep_strip<T, S>(bha, X ? bhu : bhv, X ? bhv : bhu, bb, X ? (xr + 3) * G::P + xc0 : yr0 * G::P + yc + 3,
                       X ? 1 : G::P, X ? alx : aly, K, p, X ? i0 + xc0 : j0 + yr0, X ? nx : ny,
                       X ? (j0 + xr < ny) : (i < nx), X ? K.ewx : K.ewy, emit, acc.edge);
@@ -713,9 +753,9 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
 // reads the wave speeds of its input from slot s-1, publishes those of its
 // output to slot s mod 3 and clears slot (s+1) mod 3, which nothing reads or
 // writes during stage s.
-template <int STAGE>
-__device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, bool lead, RedSmem &red, double &ax,
-                                              double &ay) {
+template <typename T, int STAGE>
+__device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, bool lead, RedSmem &red) {
+  double ax, ay;
   // read through L2 (other CTAs wrote these before the last grid barrier or launch)
   ax = bitsd(__ldcg(&sc->alpha[STAGE - 1][0]));
   ay = bitsd(__ldcg(&sc->alpha[STAGE - 1][1]));
@@ -726,7 +766,7 @@ __device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, boo
     if (t_end > 0.0 && t_now >= t_end) skip = 1;
     if (p.fixed_dt > 0.0) dt = p.fixed_dt;
     else {
-      const double den = ax / p.dx + ay / p.dy;
+      const double den = ax * p.rdx + ay * p.rdy;
       if (den > 0.0) dt = __ldcg(&sc->cfl) / den;
       else if (!skip) { skip = 1; atomicOr(&sc->status, ST_DRY); }
     }
@@ -756,7 +796,17 @@ __device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, boo
   red.dt = dt;
   const double tst = (STAGE == 1) ? t_now : __ldcg(&sc->t_step);
   const double ts = (STAGE == 1) ? tst : (STAGE == 2 ? tst + dt : tst + 0.5 * dt);
-  red.eta_in[0] = (p.bc[0] == BC_INFLOW) ? inflow_eta(p, ts) : 0.0;
+  const bool inflow = p.bc[0] == BC_INFLOW;
+  const T eta = inflow ? inflow_eta<T>(p, ts) : T(0);
+  const T v[SV_N] = {T(dt), dt > 0.0 ? T(1) / T(dt) : T(0), T(ax), T(ay), eta, inflow ? eta * T(p.in_uf) : T(0)};
+#pragma unroll
+  for (int k = 0; k < SV_N; ++k) {
+    red.v32[k] = (float)v[k];
+    red.v64[k] = (double)v[k];
+  }
+  red.v64[SV_DT] = dt;
+  red.v64[SV_AX] = ax;
+  red.v64[SV_AY] = ay;
 }
 
 // Block reduction of the per-thread accumulators and device-scope
@@ -765,36 +815,39 @@ template <typename T, int NT, int STAGE>
 __device__ __forceinline__ void publish(const Phys &p, DevScalars *sc, bool lead, RedSmem &red, double dt,
                                         const Acc<T> &acc) {
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  // in the state's precision (FP64 arithmetic is slow on this part); one
+  // conversion per published value
   const T ax = warp_max(acc.ax), ay = warp_max(acc.ay), ru = warp_max(acc.ru);
-  const double de = warp_sum((double)acc.deficit), ef = warp_sum((double)acc.edge);
+  const T de = warp_sum(acc.deficit), ef = warp_sum(acc.edge);
   const bool bad = !(acc.chk <= T(3.0e38));
   const unsigned anybad = __any_sync(0xffffffffu, bad);
+  T *wv = red_w<T>(red);
   if (l == 0) {
-    red.a[w][0] = (double)ax;
-    red.a[w][1] = (double)ay;
-    red.s[w][0] = de;
-    red.s[w][1] = ef;
-    red.r[w] = (double)ru;
+    wv[5 * w + 0] = ax;
+    wv[5 * w + 1] = ay;
+    wv[5 * w + 2] = de;
+    wv[5 * w + 3] = ef;
+    wv[5 * w + 4] = ru;
     if (anybad) red.bad = 1u;
   }
   __syncthreads();
   if (tid == 0) {
-    double mx = 0.0, my = 0.0, dsum = 0.0, fsum = 0.0, rmax = 0.0;
+    T mx = T(0), my = T(0), dsum = T(0), fsum = T(0), rmax = T(0);
     for (int q = 0; q < NT / 32; ++q) {
-      mx = fmax(mx, red.a[q][0]);
-      my = fmax(my, red.a[q][1]);
-      dsum += red.s[q][0];
-      fsum += red.s[q][1];
-      rmax = fmax(rmax, red.r[q]);
+      mx = fmax(mx, wv[5 * q + 0]);
+      my = fmax(my, wv[5 * q + 1]);
+      dsum += wv[5 * q + 2];
+      fsum += wv[5 * q + 3];
+      rmax = fmax(rmax, wv[5 * q + 4]);
     }
-    atomicMax(&sc->alpha[STAGE % 3][0], dbits(mx));
-    atomicMax(&sc->alpha[STAGE % 3][1], dbits(my));
+    atomicMax(&sc->alpha[STAGE % 3][0], dbits((double)mx));
+    atomicMax(&sc->alpha[STAGE % 3][1], dbits((double)my));
     constexpr double wgt = (STAGE == 3) ? 1.0 : (STAGE == 2 ? 2.0 / 3.0 : 1.0 / 6.0);
     constexpr double wfl = (STAGE == 3) ? 2.0 / 3.0 : 1.0 / 6.0;
-    if (dsum != 0.0) atomicAdd(&sc->clamp_mass, wgt * dsum * p.dx * p.dy);
-    if (fsum != 0.0) atomicAdd(&sc->boundary_mass, wfl * dt * fsum);
-    if (STAGE == 3 && rmax > 0.0) {
-      const unsigned long long rb = dbits(rmax);
+    if (dsum != T(0)) atomicAdd(&sc->clamp_mass, (wgt * p.area) * (double)dsum);
+    if (fsum != T(0)) atomicAdd(&sc->boundary_mass, wfl * dt * (double)fsum);
+    if (STAGE == 3 && rmax > T(0)) {
+      const unsigned long long rb = dbits((double)rmax);
       atomicMax(&sc->runup_now[__ldcg(&sc->parity)], rb);
       atomicMax(&sc->runup_max, rb);
     }
@@ -817,20 +870,14 @@ __device__ void stage_persistent(const StageIO<T> &io, const Phys &p, DevScalars
   const int tid = threadIdx.x;
   const int tiles_x = (io.nx + TX - 1) / TX, tiles_y = (io.ny + TY - 1) / TY;
   const int ntiles = tiles_x * tiles_y;
-  if (tid == 0) {
-    double ax, ay;
-    stage_scalars<STAGE>(p, sc, lead, red, ax, ay);
-    red.a[0][0] = ax;
-    red.a[0][1] = ay;
-  }
+  if (tid == 0) stage_scalars<T, STAGE>(p, sc, lead, red);
   __syncthreads();
   if (red.skip) return;
   const double dt = red.dt;
-  const T tdt = T(dt), rcap = dt > 0.0 ? T(1.0 / dt) : T(0);
-  const T alx = T(red.a[0][0]), aly = T(red.a[0][1]);
+  const T tdt = red_v<T>(red, SV_DT), rcap = red_v<T>(red, SV_RCAP);
+  const T alx = red_v<T>(red, SV_AX), aly = red_v<T>(red, SV_AY);
   const T zref = consts<T>(p).zref;
-  const T eta_in = T(red.eta_in[0]);
-  const T u_in = (p.bc[0] == BC_INFLOW) ? T(red.eta_in[0] * sqrt(p.g / p.inflow_depth)) : T(0);
+  const T eta_in = red_v<T>(red, SV_ETA), u_in = red_v<T>(red, SV_UIN);
   T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
   Acc<T> acc;
   int t = first;
@@ -977,11 +1024,8 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
       if (tid == 0) {
         sp = sl.p;
         s_io = io_of(sl.fd, STAGE);
-        double ax, ay;
         const bool ld = (sl.first_item % G0) == (int)blockIdx.x;
-        stage_scalars<STAGE>(sp, sl.sc, ld, red, ax, ay);
-        red.a[0][0] = ax;
-        red.a[0][1] = ay;
+        stage_scalars<T, STAGE>(sp, sl.sc, ld, red);
         s_skip = red.skip;
       }
       __syncthreads();
@@ -989,12 +1033,12 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
       lead = (sl.first_item % G0) == (int)blockIdx.x;
       skip = s_skip != 0u;
       dt = red.dt;
-      tdt = T(dt);
-      rcap = dt > 0.0 ? T(1.0 / dt) : T(0);
-      alx = T(red.a[0][0]);
-      aly = T(red.a[0][1]);
-      eta_in = T(red.eta_in[0]);
-      u_in = (sp.bc[0] == BC_INFLOW) ? T(red.eta_in[0] * sqrt(sp.g / sp.inflow_depth)) : T(0);
+      tdt = red_v<T>(red, SV_DT);
+      rcap = red_v<T>(red, SV_RCAP);
+      alx = red_v<T>(red, SV_AX);
+      aly = red_v<T>(red, SV_AY);
+      eta_in = red_v<T>(red, SV_ETA);
+      u_in = red_v<T>(red, SV_UIN);
     }
     T *box = (it & 1) ? box1 : box0;
     const int nitem = item + G0;
