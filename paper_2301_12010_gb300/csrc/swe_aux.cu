@@ -70,7 +70,7 @@ __global__ void k_state_stats(Field<T> fd, Phys p, DevScalars *sc) {
   __syncthreads();
   T mx = T(0), my = T(0), ru = T(0);
   bool bad = false;
-  const T g = T(p.g);
+  const Consts<T> &K = consts<T>(p);
   const size_t n = (size_t)fd.nx * fd.ny;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
     const size_t j = q / fd.nx, i = q - j * fd.nx;
@@ -78,9 +78,9 @@ __global__ void k_state_stats(Field<T> fd, Phys p, DevScalars *sc) {
     const T b = fd.b[o];
     const T h = fd.h[0][o] + still_depth(b, T(p.z_ref)), hu = fd.hu[0][o], hv = fd.hv[0][o];
     if (!(fabs(h) <= T(3.0e38)) || !(fabs(hu) <= T(3.0e38)) || !(fabs(hv) <= T(3.0e38))) { bad = true; continue; }
-    T u = T(0), v = T(0);
-    if (!Num<T>::below(h, p.h_dry32, p.h_dry)) { const T rr = Num<T>::rcp(h); u = hu * rr; v = hv * rr; }
-    const T cel = Num<T>::sqrt_(g * (h > T(0) ? h : T(0)));
+    T u = T(0), v = T(0), rr, cel;
+    Num<T>::speed(h > T(0) ? h : T(0), K.g, K.sqg, rr, cel);
+    if (!Num<T>::below(h, p.h_dry32, p.h_dry)) { u = hu * rr; v = hv * rr; }
     const T sx = fabs(u) + cel, sy = fabs(v) + cel;
     mx = sx > mx ? sx : mx;
     my = sy > my ? sy : my;

@@ -69,6 +69,7 @@ struct Consts {
   T g12dx, g12dy;  // g / (12 dx), g / (12 dy): bed source from 12 bhat differences
   T ewx, ewy;    // dy / (6 sqrt(3)), dx / (6 sqrt(3)): edge flux sums to m^3/s
   T gn2, hf4;
+  T sqg;         // sqrt(g)
 };
 
 // Physical and numerical parameters, constant over a run.
@@ -110,9 +111,11 @@ inline void finish_phys(Phys &p) {
   c.ewy = p.dx / (6.0 * s3);
   c.gn2 = p.g * p.n2;
   c.hf4 = p.hf4;
+  c.sqg = std::sqrt(p.g);
   p.c64 = c;
   p.c32 = {(float)c.g,   (float)c.zref,  (float)c.eps12, (float)c.pg,  (float)c.rfx, (float)c.rfy,
-           (float)c.g12dx, (float)c.g12dy, (float)c.ewx,  (float)c.ewy, (float)c.gn2, (float)c.hf4};
+           (float)c.g12dx, (float)c.g12dy, (float)c.ewx,  (float)c.ewy, (float)c.gn2, (float)c.hf4,
+           (float)c.sqg};
   p.rdx = 1.0 / p.dx;
   p.rdy = 1.0 / p.dy;
   p.area = p.dx * p.dy;
@@ -157,8 +160,28 @@ template <> struct Num<float> {
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
   }
-  // h^(7/3) for h > 0 through exp2/log2 hardware approximations
-  static __device__ __forceinline__ float pow73(float h) { return exp2f(2.33333333f * __log2f(h)); }
+  static __device__ __forceinline__ float lg2(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  }
+  static __device__ __forceinline__ float ex2(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  }
+  // |q| / h^(7/3) from |q|^2 and h > 0, as 2^(lg2(q^2)/2 - 7/3 lg2(h))
+  // (three hardware approximations; q = 0 gives 2^-inf = 0)
+  static __device__ __forceinline__ float fric(float q2, float h) {
+    return ex2(fmaf(0.5f, lg2(q2), -2.3333333f * lg2(h)));
+  }
+  // 1/h and sqrt(g h) from one reciprocal square root (h >= 0; h below
+  // 1e-30 is raised to it, which leaves sqrt(g h) at ~0 and 1/h unused)
+  static __device__ __forceinline__ void speed(float h, float, float sqg, float &rh, float &cel) {
+    const float rs = rsqrt_(h > 1e-30f ? h : 1e-30f);
+    rh = rs * rs;
+    cel = sqg * (h * rs);
+  }
   static __device__ __forceinline__ bool below(float h, float thr32, double) { return h < thr32; }
   static __device__ __forceinline__ float rsqrt_(float x) {
     float r;
@@ -170,7 +193,11 @@ template <> struct Num<double> {
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double div(double a, double b) { return a / b; }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-  static __device__ __forceinline__ double pow73(double h) { return h * h * cbrt(h); }
+  static __device__ __forceinline__ double fric(double q2, double h) { return sqrt(q2) / (h * h * cbrt(h)); }
+  static __device__ __forceinline__ void speed(double h, double g, double, double &rh, double &cel) {
+    rh = 1.0 / h;
+    cel = sqrt(g * h);
+  }
   static __device__ __forceinline__ bool below(double h, float, double thr) { return h < thr; }
   static __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
 };
@@ -645,8 +672,7 @@ struct CellEpilogue {
     T Lhu = sL[G::NC + o] - dF2 * K.rfy;
     T Lhv = sL[2 * G::NC + o] - dF1 * K.rfy - K.g12dy * ha * dbk;
     if (friction && !Num<T>::below(h, p.h_dry32, p.h_dry)) {
-      const T q = Num<T>::sqrt_(hu * hu + hv * hv);
-      T kap = K.gn2 * q * Num<T>::rcp(Num<T>::pow73(h));
+      T kap = K.gn2 * Num<T>::fric(hu * hu + hv * hv, h);
       kap = kap > rcap ? rcap : kap;  // rcap = 1/dt
       Lhu -= kap * hu;
       Lhv -= kap * hv;
@@ -660,7 +686,8 @@ struct CellEpilogue {
     }
     if (nha < -d) { acc.deficit -= nha + d; nha = -d; }
     const T nh = nha + d;
-    T u = T(0), v = T(0);
+    T u = T(0), v = T(0), rr, cel;
+    Num<T>::speed(nh, K.g, K.sqg, rr, cel);
     if (Num<T>::below(nh, p.h_dry32, p.h_dry)) { nhu = T(0); nhv = T(0); }
     else {
       if (Num<T>::below(nh, p.h_film32, p.h_film)) {  // film: bounded velocity
@@ -669,14 +696,12 @@ struct CellEpilogue {
         nhu *= f;
         nhv *= f;
       }
-      const T rr = Num<T>::rcp(nh);
       u = nhu * rr;
       v = nhv * rr;
     }
     io.oha[go] = nha;
     io.ohu[go] = nhu;
     io.ohv[go] = nhv;
-    const T cel = Num<T>::sqrt_(K.g * nh);
     const T sx = fabs(u) + cel, sy = fabs(v) + cel;
     acc.chk += sx + sy;  // non-finite values propagate to the per-CTA check
     acc.ax = sx > acc.ax ? sx : acc.ax;
@@ -870,33 +895,38 @@ __device__ void stage_persistent(const StageIO<T> &io, const Phys &p, DevScalars
   const int tid = threadIdx.x;
   const int tiles_x = (io.nx + TX - 1) / TX, tiles_y = (io.ny + TY - 1) / TY;
   const int ntiles = tiles_x * tiles_y;
+  T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
+  // the first box is in flight while thread 0 takes the stage's scalars
+  int t = first;
+  if (t < ntiles) issue_box<T, TX, TY, NT>(io, (t % tiles_x) * TX, (t / tiles_x) * TY, box0);
+  cp_commit();
   if (tid == 0) stage_scalars<T, STAGE>(p, sc, lead, red);
   __syncthreads();
-  if (red.skip) return;
+  if (red.skip) {
+    cp_wait<0>();
+    return;
+  }
   const double dt = red.dt;
   const T tdt = red_v<T>(red, SV_DT), rcap = red_v<T>(red, SV_RCAP);
   const T alx = red_v<T>(red, SV_AX), aly = red_v<T>(red, SV_AY);
   const T zref = consts<T>(p).zref;
   const T eta_in = red_v<T>(red, SV_ETA), u_in = red_v<T>(red, SV_UIN);
-  T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
   Acc<T> acc;
-  int t = first;
-  if (t < ntiles) issue_box<T, TX, TY, NT>(io, (t % tiles_x) * TX, (t / tiles_x) * TY, box0);
-  cp_commit();
   for (int it = 0; t < ntiles; ++it, t += stride) {
     T *box = (it & 1) ? box1 : box0;
+    // one barrier: this tile's box has landed for every thread's copies, and
+    // every thread is done with the previous tile (whose buffer is refilled next)
+    cp_wait<0>();
+    __syncthreads();
     const int tn = t + stride;
     if (tn < ntiles) issue_box<T, TX, TY, NT>(io, (tn % tiles_x) * TX, (tn / tiles_x) * TY, (it & 1) ? box0 : box1);
     cp_commit();
-    cp_wait<1>();
-    __syncthreads();
     const int i0 = (t % tiles_x) * TX, j0 = (t / tiles_x) * TY;
     if (i0 == 0 || j0 == 0 || i0 + TX + 3 > io.nx || j0 + TY + 3 > io.ny) {
       patch_box<T, TX, TY, NT>(io, p, i0, j0, box, zref, eta_in, u_in);
       __syncthreads();
     }
     tile_compute<T, TX, TY, NT, S, STAGE>(io, p, i0, j0, box, sL, tdt, rcap, alx, aly, acc);
-    __syncthreads();
   }
   cp_wait<0>();
   publish<T, NT, STAGE>(p, sc, lead, red, dt, acc);
@@ -994,7 +1024,7 @@ __host__ __device__ __forceinline__ StageIO<T> io_of(const Field<T> &fd, int sta
 template <typename T, int TX, int TY, int NT, int S, int STAGE>
 __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T *smem, RedSmem &red, Phys &sp) {
   using G = TileGeom<T, TX, TY>;
-  __shared__ int s_slot;
+  __shared__ int s_slot[2];  // double-buffered: written one iteration ahead of the last reader
   __shared__ unsigned s_skip;
   __shared__ StageIO<T> s_io;  // planes of the current scenario (kept out of registers)
   T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
@@ -1013,9 +1043,12 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
   }
   cp_commit();
   for (int it = 0; item < total; ++it, item += G0) {
-    if (tid == 0) s_slot = slot_of_item(slots, nslots, item);
+    if (tid == 0) s_slot[it & 1] = slot_of_item(slots, nslots, item);
+    // this item's box has landed for every thread's copies, and every thread
+    // is done with the previous item (whose buffer is refilled below)
+    cp_wait<0>();
     __syncthreads();
-    const int s = s_slot;
+    const int s = s_slot[it & 1];
     const BatchSlot<T> &sl = slots[s];
     if (s != cur) {
       if (cur >= 0 && !skip) publish<T, NT, STAGE>(sp, slots[cur].sc, lead, red, dt, acc);
@@ -1049,8 +1082,6 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
                                (nt / slots[ns].tiles_x) * TY, (it & 1) ? box0 : box1);
     }
     cp_commit();
-    cp_wait<1>();
-    __syncthreads();
     if (!skip) {
       const int t = item - sl.first_item;
       const int tiles_x = sl.tiles_x;
@@ -1061,7 +1092,6 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
       }
       tile_compute<T, TX, TY, NT, S, STAGE>(s_io, sp, i0, j0, box, sL, tdt, rcap, alx, aly, acc);
     }
-    __syncthreads();
   }
   cp_wait<0>();
   if (cur >= 0 && !skip) publish<T, NT, STAGE>(sp, slots[cur].sc, lead, red, dt, acc);

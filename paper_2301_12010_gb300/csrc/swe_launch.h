@@ -25,7 +25,9 @@ struct TileShape {
   X(6, 64, 48, 384, 8, 1, 1)       \
   X(7, 96, 32, 384, 8, 1, 1)       \
   X(8, 64, 64, 512, 8, 1, 1)       \
-  X(9, 128, 32, 512, 8, 1, 1)
+  X(9, 128, 32, 512, 8, 1, 1)      \
+  X(10, 64, 24, 192, 8, 2, 1)      \
+  X(11, 96, 16, 192, 8, 2, 1)
 
 template <int K>
 struct ShapeP;

@@ -35,7 +35,9 @@ def test_single_scenario_autotune_is_cached_and_used(cache):
 
 def test_fp64_skips_shapes_that_do_not_fit(cache):
     best, ms = swe.autotune([(128, 128)], precision=swe.F64, steps=2)
-    assert ms[2] == -1.0 and best in (1, 2)
+    too_big = [3, 5, 6, 7, 8, 9]  # need more shared memory than a CTA may use in FP64
+    assert all(ms[k - 1] == -1.0 for k in too_big)
+    assert best not in too_big and ms[best - 1] > 0.0
 
 
 def test_batch_autotune_is_cached_and_used(cache):

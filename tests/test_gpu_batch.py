@@ -16,7 +16,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 import paper_2301_12010_gb300 as swe  # noqa: E402
 
 GB = 1 << 30
-ALL_TILES = list(range(1, 10))  # compiled tile shapes
+ALL_TILES = list(range(1, 12))  # compiled tile shapes
 
 
 def stream():
