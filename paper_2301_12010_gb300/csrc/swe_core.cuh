@@ -719,9 +719,8 @@ struct CellEpilogue {
 //   stage 2: U2 = U^n + 1/4 (U1 + dt L(U1) - U^n)
 //   stage 3: U^{n+1} = U^n + 2/3 (U2 + dt L(U2) - U^n)   (written over U^n)
 // followed by the post-stage rule, with L of Eq. (7).  Pass 0 sweeps x and
-// stores L_x; pass 1 sweeps y, adds L_y and the sources and updates.  Both
-// passes run the same sweep code (loop not unrolled: one copy of the WENO
-// body in the instruction stream).
+// stores L_x; pass 1 sweeps y, adds L_y and the sources and updates.  The
+// pass loop is unrolled, so each pass runs code specialised for its frame.
 template <typename T, int TX, int TY, int NT, int S, int STAGE>
 __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p, int i0, int j0, const T *box,
                                              T *sL, T tdt, T rcap, T alx, T aly, Acc<T> &acc) {
@@ -748,7 +747,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
 
   const T wrk = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
   const bool friction = p.n2 > 0.0;
-#pragma unroll 1
+#pragma unroll
   for (int pass = 0; pass < 2; ++pass) {
     const bool X = pass == 0;
     // U^n of the y-pass cells (stages 2, 3), fetched before the sweep so that
