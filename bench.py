@@ -39,6 +39,35 @@ FLOPS_PER_CELL_STAGE = 1007.0
 BYTES_PER_CELL_STAGE = {1: 28.0, 2: 40.0, 3: 40.0}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop/FMA x max SM clock
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
+# RK stage from one ncu capture of the stage kernel on the 2048x2048 case of
+# the same workload (96x32 tile), per cell; reported for the 4096x4096 launch
+# scaled by its cells, and only while the kernel sources are those captured.
+NCU_TRAFFIC = {"tile": 7, "cells": 2048 * 2048,
+               "bytes": {1: 67.343104e6 + 14.923264e6, 2: 117.827584e6 + 28.346112e6, 3: 117.678848e6 + 19.223808e6},
+               "sources": ("swe_core.cuh", "swe_kernels.cu", "swe_launch.h"),
+               "sha256": "98dd9097a76d225e83c10823432a92f34c923912936de22f38a68939d5edfbd5"}
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in NCU_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_2301_12010_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(tile: int, stage: int, cells: int):
+    """Captured DRAM bytes of one stage launch scaled to `cells`, or None if
+    the tile differs or the kernel changed since the capture."""
+    try:
+        if tile != NCU_TRAFFIC["tile"] or kernel_sources_sha256() != NCU_TRAFFIC["sha256"]:
+            return None
+    except OSError:
+        return None
+    return NCU_TRAFFIC["bytes"][stage] / NCU_TRAFFIC["cells"] * cells
+
 
 def peaks():
     try:
@@ -338,7 +367,8 @@ def main():
                        "l2": "inputs larger than L2 (10 planes x %.0f MB)" % (cells * 4 / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single", "tile": diag["tile"]},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": ncu_traffic(diag["tile"], dom, cells),
+                         "traffic_unit": "bytes per launch (ncu, 2048x2048 capture scaled by cells)",
                          "kernel": "stage_kernel<float> RK stage %d" % dom,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                          "flops_per_cell_stage": FLOPS_PER_CELL_STAGE},
