@@ -64,6 +64,25 @@ def synolakis_runup(H_over_d: float, cot_beta: float, d: float) -> float:
     return d * 2.831 * math.sqrt(cot_beta) * H_over_d ** 1.25
 
 
+def standing_wave_on_slope(r: np.ndarray, t: float, amp: float, L: float, slope: float, g: float = G):
+    """Linear SWE on still-water depth slope * r (r = distance from the
+    shoreline, x = L - r) with a wall at r = L: eta = amp J0(xi) cos(w t),
+    xi = 2 w sqrt(r/(g slope)), solves eta_tt = g slope (r eta_r)_r (Bessel's
+    equation of order 0 in xi), and the wall condition eta_r(L) = 0 asks
+    J1(xi_L) = 0, so 2 w sqrt(L/(g slope)) = j11.  The x-velocity follows
+    from u_t = -g eta_x = g eta_r: u = (g amp / w) dJ0(xi)/dr sin(w t), with
+    dJ0/dr = -J1(xi) w / sqrt(g slope r).  Returns (eta, hu = slope r u, w)."""
+    from scipy.special import j0, j1, jn_zeros
+    j11 = float(jn_zeros(1, 1)[0])
+    w = 0.5 * j11 * math.sqrt(g * slope / L)
+    rr = np.maximum(r, 0.0)
+    xi = 2.0 * w * np.sqrt(rr / (g * slope))
+    eta = amp * j0(xi) * math.cos(w * t)
+    # slope r dJ0/dr = -J1(xi) w slope r / sqrt(g slope r) = -J1(xi) w sqrt(slope r / g)
+    hu = (g * amp / w) * (-j1(xi) * w * np.sqrt(slope * rr / g)) * math.sin(w * t)
+    return eta, hu, w
+
+
 def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
     """Relative L2 error of Eq. (9)."""
     return float(np.sqrt(np.sum((a - ref) ** 2) / np.sum(ref ** 2)))

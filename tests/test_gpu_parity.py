@@ -130,7 +130,24 @@ def test_fp64_planar_beach_full_5000_steps():
     assert d["runup_max"] == pytest.approx(ref.diag()["runup_max"], abs=1e-10)
 
 
+def test_fp64_standing_wave_on_slope():
+    # 2 mm standing wave over a 1:20 beach with dry land beyond the shore
+    sc = W.standing_wave_slope(nx_sea=100, nx_land=20, dx=10.0, amp=0.002)
+    ref = run_oracle(sc, 400)
+    h, hu, hv, d, _ = run_gpu(sc, 400, swe.F64)
+    assert np.abs((h + sc.b) - (ref.h + sc.b)).max() <= 1e-10
+    assert np.abs(hu - ref.hu).max() <= 1e-10
+
+
 # ------------------------------------------------------------------ FP32
+def test_fp32_standing_wave_on_slope():
+    sc = W.standing_wave_slope(nx_sea=100, nx_land=20, dx=10.0, amp=0.002)
+    ref = run_oracle(sc, 400)
+    h, hu, hv, d, _ = run_gpu(sc, 400, swe.F32)
+    assert rel_l2(eta_tilde(h, sc.b), eta_tilde(ref.h, sc.b)) <= 1e-4
+    assert rel_l2(hu, ref.hu) <= 1e-4
+
+
 @pytest.mark.parametrize("tile", ALL_TILES)
 def test_fp32_hump_128(tile):
     sc = W.gaussian_hump()

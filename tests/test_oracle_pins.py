@@ -241,3 +241,46 @@ def test_solitary_wave_runup_follows_synolakis_law():
     R = sim.diag()["runup_max"]
     law = A.synolakis_runup(0.02, 20.0, 10.0)
     assert abs(R - law) / law <= 0.10, (R, law)
+
+
+def _standing_wave_case():
+    amp, dx, nx_sea, slope = 0.002, 10.0, 100, 0.05
+    sc = W.standing_wave_slope(nx_sea=nx_sea, nx_land=20, dx=dx, slope=slope, amp=amp)
+    L = nx_sea * dx
+    r = L - (np.arange(sc.b.shape[1]) + 0.5) * dx
+    _, _, w = A.standing_wave_on_slope(r, 0.0, amp, L, slope)
+    return sc, amp, L, slope, r, 2.0 * math.pi / w
+
+
+def test_standing_wave_on_a_slope_follows_linear_theory():
+    """Small-amplitude standing wave on a plane beach, the linear limit of the
+    Carrier-Greenspan problem: eta = A J0(2 w sqrt(r/(g s))) cos(w t) with the
+    wall mode w.  Until the shoreline's influence arrives (t <= T/4) the
+    offshore half follows it to the O(A/h) nonlinearity (A/h ~ 4e-5): this fixes
+    the pressure flux, the bed source on a slope, the wave speed and the wall."""
+    sc, amp, L, slope, r, T = _standing_wave_case()
+    sim = oracle.Simulation(sc)
+    off = r >= 0.5 * L
+    for frac in (0.125, 0.25):
+        sim.run_until(frac * T)
+        eta, hu = sim.h[1] + sc.b[1], sim.hu[1]
+        ex, hux, _ = A.standing_wave_on_slope(r, frac * T, amp, L, slope)
+        assert np.sqrt(np.mean((eta[off] - ex[off]) ** 2)) <= 1e-4 * amp
+        assert np.sqrt(np.mean((hu[off] - hux[off]) ** 2)) <= 2e-4 * np.abs(hux[off]).max()
+        assert np.abs(sim.hv).max() == 0.0
+
+
+def test_standing_wave_shoreline_error_stays_bounded():
+    """Over a half period the shoreline cells leave the linear solution: with the
+    water level away from z_ref the flux/source pairing is not exactly balanced
+    next to dry land (the stencils mix wet and dry cells), and for a wave this
+    small that imbalance rivals the physical force at the shore.  Recorded
+    bound, not agreement with a closed form: rms over the wet side <= 15 % of A
+    at T/2 (observed 9.7 % at dx = 10 m, 7.5 % at 5 m)."""
+    sc, amp, L, slope, r, T = _standing_wave_case()
+    sim = oracle.Simulation(sc)
+    sim.run_until(0.5 * T)
+    eta = sim.h[1] + sc.b[1]
+    ex, _, _ = A.standing_wave_on_slope(r, 0.5 * T, amp, L, slope)
+    wet = r > 0.0
+    assert np.sqrt(np.mean((eta[wet] - ex[wet]) ** 2)) <= 0.15 * amp

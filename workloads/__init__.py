@@ -271,6 +271,28 @@ def serving_requests(rate: float, count: int, seed: int = 5, dx: float = 2.0,
 
 
 # ----------------------------------------------------- verification cases
+def standing_wave_slope(nx_sea: int = 200, nx_land: int = 40, ny: int = 4, dx: float = 5.0,
+                        slope: float = 0.05, amp: float = 0.002) -> Scenario:
+    """Small-amplitude standing wave on a plane beach (the linear limit of the
+    Carrier-Greenspan problem): offshore wall at x = 0, shoreline at
+    x = L = nx_sea dx, bed b = -slope (L - x) everywhere (land rising beyond
+    the shoreline), at rest with eta = amp J0(j11 sqrt(r / L)) on the wet side,
+    r = L - x the distance from the shoreline and j11 the first zero of J1
+    (the mode whose velocity vanishes at the offshore wall)."""
+    from scipy.special import j0, jn_zeros
+    nx = nx_sea + nx_land
+    L = nx_sea * dx
+    x = _centres(nx, dx)
+    r = L - x
+    bx = -slope * r
+    j11 = float(jn_zeros(1, 1)[0])
+    eta = np.where(r > 0.0, amp * j0(j11 * np.sqrt(np.maximum(r, 0.0) / L)), amp)
+    h1 = np.maximum(eta - bx, 0.0)
+    b = np.repeat(bx[None, :], ny, axis=0)
+    h = np.repeat(h1[None, :], ny, axis=0)
+    return Scenario("standing_wave_slope_%dx%d" % (nx, ny), dx, dx, b, h, np.zeros_like(b), np.zeros_like(b))
+
+
 def lake_at_rest(nx: int = 32, ny: int = 32, dx: float = 1.0, eta0: float = 0.5, depth: float = 10.0,
                  rms: float = 3.0, seed: int = 11, islands: bool = False) -> Scenario:
     """Still water over a seeded rough bed (slope -2 spectrum).  With islands,
