@@ -258,6 +258,22 @@ def run_reference(args):
     return 0
 
 
+def replica_throughput(ms_local: float, cells: int, steps: int, dist=None):
+    """Whole-job throughput of independent replicas, one per rank: the job
+    takes as long as its slowest rank (all-reduce MAX of the timed region over
+    the process group), and value = the cell-updates of all ranks / that time.
+    Returns (value, ms_max)."""
+    ws, ms_max = 1, float(ms_local)
+    if dist is not None and dist.is_initialized():
+        import torch
+        ws = dist.get_world_size()
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms_max], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    return cells * steps * ws / (ms_max / 1e3), ms_max
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,13 +334,8 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     solver.sync()
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
     cells = sc.cells
-    value = cells * args.steps * ws / (ms_max / 1e3)
+    value, ms_max = replica_throughput(ms, cells, args.steps, dist)
 
     # per-stage kernel durations (CUDA events on the launching stream)
     nst = 30
