@@ -95,25 +95,36 @@ int device_status(swe_handle *s) {
 
 // Host FP64 [ny][nx] -> device plane; depth fields (is_depth) are stored as
 // the anomaly ha (the bed must already be on the device).
+// A page-locked host array is read by the conversion kernel directly (one
+// pass across the host link); pageable memory goes through the staging plane.
 int upload_field(swe_handle *s, const double *src, void *dst, bool is_depth) {
-  cudaError_t e = cudaMemcpyAsync(s->staging, src, sizeof(double) * (size_t)s->nx * s->ny, cudaMemcpyHostToDevice,
-                                  s->stream);
-  if (e != cudaSuccess) return cuda_check(s, e);
+  const size_t bytes = sizeof(double) * (size_t)s->nx * s->ny;
+  const void *in = pinned_device_ptr(src, bytes);
+  cudaError_t e = cudaSuccess;
+  if (!in) {
+    e = cudaMemcpyAsync(s->staging, src, bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_check(s, e);
+    in = s->staging;
+  }
   if (s->prec == SWE_F64)
-    e = import_plane<double>(s->staging, true, (double *)dst, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
+    e = import_plane<double>(in, true, (double *)dst, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
   else
-    e = import_plane<float>(s->staging, true, (float *)dst, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
+    e = import_plane<float>(in, true, (float *)dst, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
   return cuda_check(s, e);
 }
 
+// The converse: the conversion kernel writes a page-locked host array
+// directly; a pageable one is filled from the staging plane.
 int download_field(swe_handle *s, const void *src, double *dst, bool is_depth) {
+  const size_t bytes = sizeof(double) * (size_t)s->nx * s->ny;
+  void *out = const_cast<void *>(pinned_device_ptr(dst, bytes));
+  void *target = out ? out : s->staging;
   cudaError_t e;
   if (s->prec == SWE_F64)
-    e = export_plane<double>((const double *)src, s->staging, true, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
+    e = export_plane<double>((const double *)src, target, true, is_depth ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
   else
-    e = export_plane<float>((const float *)src, s->staging, true, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dst, s->staging, sizeof(double) * (size_t)s->nx * s->ny, cudaMemcpyDeviceToHost, s->stream);
+    e = export_plane<float>((const float *)src, target, true, is_depth ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
+  if (e == cudaSuccess && !out) e = cudaMemcpyAsync(dst, s->staging, bytes, cudaMemcpyDeviceToHost, s->stream);
   return cuda_check(s, e);
 }
 

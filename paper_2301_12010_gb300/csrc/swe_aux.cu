@@ -8,30 +8,48 @@
 namespace swe {
 namespace {
 
-// Host-format FP64 [ny][nx] -> pitched planes.  With bed != nullptr the
-// field is a depth h stored as the anomaly ha = h - max(z_ref - b, 0).
+// Host-format [ny][nx] -> pitched planes.  With bed != nullptr the field is
+// a depth h stored as the anomaly ha = h - max(z_ref - b, 0) (in FP64).  CTA
+// b takes rows b, b + gridDim.x, ...; the source may be device memory or
+// page-locked host memory read across the host link (four loads in flight
+// per thread).
 template <typename T, typename S>
 __global__ void k_import(const S *__restrict__ src, T *__restrict__ dst, const T *__restrict__ bed, double zref,
                          int nx, int ny, int pitch) {
-  const size_t n = (size_t)nx * ny;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = q / nx, i = q - j * nx;
-    double v = (double)src[q];
-    if (bed) v -= fmax(zref - (double)bed[j * pitch + i], 0.0);
-    dst[j * pitch + i] = (T)v;
+  for (int j = blockIdx.x; j < ny; j += gridDim.x) {
+    const S *srow = src + (size_t)j * nx;
+    T *drow = dst + (size_t)j * pitch;
+    const T *brow = bed ? bed + (size_t)j * pitch : nullptr;
+    for (int i0 = threadIdx.x; i0 < nx; i0 += 4 * blockDim.x) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        v[u] = i < nx ? (double)srow[i] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < nx) drow[i] = (T)(brow ? v[u] - fmax(zref - (double)brow[i], 0.0) : v[u]);
+      }
+    }
   }
 }
 
-// Pitched planes -> contiguous [ny][nx]; with bed != nullptr, h = ha + d.
+// Pitched planes -> contiguous [ny][nx] (device memory or page-locked host
+// memory written across the host link); with bed != nullptr, h = ha + d.
 template <typename T, typename S>
 __global__ void k_export(const T *__restrict__ src, S *__restrict__ dst, const T *__restrict__ bed, double zref,
                          int nx, int ny, int pitch) {
-  const size_t n = (size_t)nx * ny;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = q / nx, i = q - j * nx;
-    double v = (double)src[j * pitch + i];
-    if (bed) v += fmax(zref - (double)bed[j * pitch + i], 0.0);
-    dst[q] = (S)v;
+  for (int j = blockIdx.x; j < ny; j += gridDim.x) {
+    const T *srow = src + (size_t)j * pitch;
+    const T *brow = bed ? bed + (size_t)j * pitch : nullptr;
+    S *drow = dst + (size_t)j * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      double v = (double)srow[i];
+      if (brow) v += fmax(zref - (double)brow[i], 0.0);
+      drow[i] = (S)v;
+    }
   }
 }
 
@@ -162,7 +180,7 @@ static int blocks_for(size_t n, int threads) {
 template <typename T>
 cudaError_t import_plane(const void *src, bool src_f64, T *dst, const T *bed_for_depth, double zref, int nx, int ny,
                          int pitch, cudaStream_t st) {
-  const int nb = blocks_for((size_t)nx * ny, 256);
+  const int nb = ny < 4096 ? ny : 4096;
   if (src_f64) k_import<T, double><<<nb, 256, 0, st>>>((const double *)src, dst, bed_for_depth, zref, nx, ny, pitch);
   else k_import<T, T><<<nb, 256, 0, st>>>((const T *)src, dst, bed_for_depth, zref, nx, ny, pitch);
   return cudaGetLastError();
@@ -171,10 +189,28 @@ cudaError_t import_plane(const void *src, bool src_f64, T *dst, const T *bed_for
 template <typename T>
 cudaError_t export_plane(const T *src, void *dst, bool dst_f64, const T *bed_for_depth, double zref, int nx, int ny,
                          int pitch, cudaStream_t st) {
-  const int nb = blocks_for((size_t)nx * ny, 256);
+  const int nb = ny < 4096 ? ny : 4096;
   if (dst_f64) k_export<T, double><<<nb, 256, 0, st>>>(src, (double *)dst, bed_for_depth, zref, nx, ny, pitch);
   else k_export<T, T><<<nb, 256, 0, st>>>(src, (T *)dst, bed_for_depth, zref, nx, ny, pitch);
   return cudaGetLastError();
+}
+
+const void *pinned_device_ptr(const void *p, size_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  cudaPointerAttributes a0, a1;
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || !a0.devicePointer) return nullptr;
+  const char *last = (const char *)p + (bytes - 1);
+  if (cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (a1.type != cudaMemoryTypeHost || !a1.devicePointer) return nullptr;
+  if ((const char *)a1.devicePointer - (const char *)a0.devicePointer != (ptrdiff_t)(bytes - 1)) return nullptr;
+  return a0.devicePointer;
 }
 
 cudaError_t reset_scalars(DevScalars *sc, double t, double cfl, double t_end, cudaStream_t st) {

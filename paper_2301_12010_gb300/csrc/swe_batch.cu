@@ -229,14 +229,19 @@ int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, co
   const size_t nb = sizeof(double) * (size_t)sl.nx * sl.ny;
   const double zr = sl.p.z_ref;
   e = cudaMemsetAsync(sl.mem, 0, plane * 10, b->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(sl.staging, bathymetry, nb, cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = import_plane<float>(sl.staging, true, bplane, nullptr, zr, sl.nx, sl.ny, sl.pitch, b->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(sl.staging, h, nb, cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = import_plane<float>(sl.staging, true, sl.fd.h[0], bplane, zr, sl.nx, sl.ny, sl.pitch, b->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(sl.staging, hu, nb, cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = import_plane<float>(sl.staging, true, sl.fd.hu[0], nullptr, zr, sl.nx, sl.ny, sl.pitch, b->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(sl.staging, hv, nb, cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = import_plane<float>(sl.staging, true, sl.fd.hv[0], nullptr, zr, sl.nx, sl.ny, sl.pitch, b->stream);
+  // page-locked host arrays are read by the conversion kernel directly,
+  // pageable ones through the slot's staging plane
+  const double *srcs[4] = {bathymetry, h, hu, hv};
+  float *dsts[4] = {bplane, sl.fd.h[0], sl.fd.hu[0], sl.fd.hv[0]};
+  for (int f = 0; f < 4 && e == cudaSuccess; ++f) {
+    const void *in = pinned_device_ptr(srcs[f], nb);
+    if (!in) {
+      e = cudaMemcpyAsync(sl.staging, srcs[f], nb, cudaMemcpyHostToDevice, b->stream);
+      in = sl.staging;
+    }
+    if (e == cudaSuccess)
+      e = import_plane<float>(in, true, dsts[f], f == 1 ? bplane : nullptr, zr, sl.nx, sl.ny, sl.pitch, b->stream);
+  }
   if (e == cudaSuccess) e = reset_scalars(b->d_sc + s, 0.0, b->cfl, t_end, b->stream);
   if (e == cudaSuccess) e = state_stats<float>(sl.fd, sl.p, b->d_sc + s, b->stream);
   if (e != cudaSuccess) {
@@ -345,9 +350,10 @@ int swe_batch_get_state(swe_batch *b, int32_t slot, double *h, double *hu, doubl
   const float *src[3] = {sl.fd.h[0], sl.fd.hu[0], sl.fd.hv[0]};
   cudaError_t e = cudaSuccess;
   for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
-    e = export_plane<float>(src[f], sl.staging, true, f == 0 ? sl.fd.b : nullptr, sl.p.z_ref, sl.nx, sl.ny, sl.pitch,
-                            b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dst[f], sl.staging, nb, cudaMemcpyDeviceToHost, b->stream);
+    void *out = const_cast<void *>(pinned_device_ptr(dst[f], nb));
+    e = export_plane<float>(src[f], out ? out : sl.staging, true, f == 0 ? sl.fd.b : nullptr, sl.p.z_ref, sl.nx,
+                            sl.ny, sl.pitch, b->stream);
+    if (e == cudaSuccess && !out) e = cudaMemcpyAsync(dst[f], sl.staging, nb, cudaMemcpyDeviceToHost, b->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   return bfail(b, e);

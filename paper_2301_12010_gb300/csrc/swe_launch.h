@@ -63,6 +63,13 @@ cudaError_t import_plane(const void *src, bool src_f64, T *dst, const T *bed_for
 template <typename T>
 cudaError_t export_plane(const T *src, void *dst, bool dst_f64, const T *bed_for_depth, double zref, int nx, int ny,
                          int pitch, cudaStream_t st);
+// Device-accessible address of a host array of `bytes` bytes when its first
+// and last bytes lie in page-locked memory mapped for the device (cudaHostAlloc,
+// cudaHostRegister, a pinned torch tensor) at the same offset, i.e. one pinned
+// allocation or registration: the conversion kernels then read or write it
+// directly across the host link, with no staging copy.  nullptr otherwise
+// (pageable memory takes the staging copy).
+const void *pinned_device_ptr(const void *p, size_t bytes);
 cudaError_t reset_scalars(DevScalars *sc, double t, double cfl, double t_end, cudaStream_t st);
 cudaError_t set_cfl(DevScalars *sc, double cfl, cudaStream_t st);
 template <typename T>

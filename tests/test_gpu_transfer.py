@@ -1,0 +1,60 @@
+"""Host transfers through the C ABI: page-locked host arrays are read and
+written by the conversion kernels directly, pageable ones through a staging
+plane; both must give the same device state bit for bit."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+pytestmark = pytest.mark.gpu
+
+import paper_2301_12010_gb300 as swe  # noqa: E402
+
+
+def stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def pinned_like(a):
+    t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+    t.numpy()[...] = a
+    return t
+
+
+@pytest.mark.parametrize("precision", [swe.F32, swe.F64])
+def test_pinned_and_pageable_host_arrays_agree(precision):
+    sc = W.lake_at_rest(131, 77, eta0=0.0, depth=4.0, rms=1.0, seed=5)  # ragged sizes
+    rng = np.random.default_rng(11)
+    sc.h = sc.h + 0.1 * rng.uniform(size=sc.h.shape)
+    sc.hu = 0.2 * rng.normal(size=sc.h.shape)
+    sc.hv = 0.2 * rng.normal(size=sc.h.shape)
+    keep = [pinned_like(x) for x in (sc.h, sc.hu, sc.hv)]
+    outs = [torch.empty(sc.h.shape, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    with swe.Solver(sc, precision=precision, stream=stream()) as a, \
+            swe.Solver(sc, precision=precision, stream=stream()) as b:
+        a.set_state(sc.h, sc.hu, sc.hv)                   # pageable in
+        b.set_state(*(t.numpy() for t in keep))           # page-locked in
+        assert all(np.array_equal(x, y) for x, y in zip(a.get_state(), b.get_state()))
+        a.step(7)
+        b.step(7)
+        ref = a.get_state()                               # pageable out
+        got = b.get_state(tuple(t.numpy() for t in outs))  # page-locked out
+        for x, y in zip(ref, got):
+            assert np.array_equal(x, y)
+
+
+def test_batch_admit_from_page_locked_arrays():
+    ens = W.mitigation_ensemble(count=1, seed=3, nx_range=(160, 160), ny_range=(96, 96), land_width=90.0)
+    sc = ens[0]
+    pinned = sc.copy(b=pinned_like(sc.b).numpy(), h=pinned_like(sc.h).numpy(), hu=pinned_like(sc.hu).numpy(),
+                     hv=pinned_like(sc.hv).numpy())
+    with swe.Batch(2, 1 << 30, sc, stream=stream()) as bt:
+        s0 = bt.admit(sc.copy(t_end=1e6))
+        s1 = bt.admit(pinned.copy(t_end=1e6))
+        bt.run(10)
+        x, y = bt.get_state(s0), bt.get_state(s1)
+        for u, v in zip(x, y):
+            assert np.array_equal(u, v)
