@@ -129,6 +129,22 @@ int swe_sync(swe_handle *s);
 /* Copy the current state to host FP64 arrays [ny][nx].  Synchronises. */
 int swe_get_state(swe_handle *s, double *h, double *hu, double *hv);
 
+/* Start copying the current state to host FP64 arrays [ny][nx] and return at
+ * once: the state is snapshot on the device (in stream order after the steps
+ * enqueued so far) and converted into the arrays on a second stream, so that
+ * later calls (swe_set_state, swe_step) overlap the read-back.  The arrays
+ * must each be one page-locked allocation (cudaHostAlloc, cudaHostRegister, a
+ * pinned torch tensor); they hold the state once swe_wait_state returns and
+ * must not be read or freed before.  With pageable arrays this is
+ * swe_get_state (synchronous).  A second call waits on the device for the
+ * first read-back before it snapshots again.  No counterpart in the paper:
+ * an interface for pipelining input upload and result read-back. */
+int swe_get_state_async(swe_handle *s, double *h, double *hu, double *hv);
+
+/* Wait for the read-back started by swe_get_state_async (no-op if none);
+ * returns the handle's first error, if any. */
+int swe_wait_state(swe_handle *s);
+
 /* Copy the current state into caller device arrays of the handle's
  * precision (contiguous [ny][nx]).  Synchronises. */
 int swe_get_state_device(swe_handle *s, void *h, void *hu, void *hv);

@@ -71,6 +71,8 @@ def _load() -> ctypes.CDLL:
         "swe_step": (ip, [H, ctypes.c_int32, ctypes.c_double]),
         "swe_sync": (ip, [H]),
         "swe_get_state": (ip, [H, dp, dp, dp]),
+        "swe_get_state_async": (ip, [H, dp, dp, dp]),
+        "swe_wait_state": (ip, [H]),
         "swe_get_state_device": (ip, [H, vp, vp, vp]),
         "swe_mass": (ip, [H, dp, dp]),
         "swe_runup": (ip, [H, dp, dp]),
@@ -205,6 +207,20 @@ class Solver:
             out = tuple(np.empty((self.ny, self.nx), dtype=np.float64) for _ in range(3))
         _check(lib.swe_get_state(self._h, *[_dp(x) for x in out]), "swe_get_state")
         return out
+
+    def get_state_async(self, out) -> None:
+        """Start the read-back of the state into `out` (three contiguous
+        float64 arrays, page-locked for the asynchronous path); the arrays
+        hold the state once wait_state() returns."""
+        for x in out:
+            if x.dtype != np.float64 or not x.flags.c_contiguous or x.shape != (self.ny, self.nx):
+                raise ValueError("get_state_async needs contiguous float64 arrays of shape (ny, nx)")
+        self._async_out = out  # keep the arrays alive until wait_state
+        _check(lib.swe_get_state_async(self._h, *[_dp(x) for x in out]), "swe_get_state_async")
+
+    def wait_state(self) -> None:
+        _check(lib.swe_wait_state(self._h), "swe_wait_state")
+        self._async_out = None
 
     def get_state_device(self, h, hu, hv) -> None:
         _check(lib.swe_get_state_device(self._h, h.data_ptr(), hu.data_ptr(), hv.data_ptr()),

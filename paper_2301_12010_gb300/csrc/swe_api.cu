@@ -43,6 +43,14 @@ struct swe_handle {
   cudaGraphExec_t graph = nullptr;
   double cfl_dev = -1.0;          // CFL value last written to the device scalars
   int sticky = SWE_OK;            // first host-visible error
+  // asynchronous read-back (swe_get_state_async): U^n is copied to snap on the
+  // caller's stream and converted into the host arrays on the read-back stream
+  void *snap = nullptr;           // three planes of U^n
+  double *xstage = nullptr;       // three FP64 [ny][nx] planes: the read-back's host format
+  cudaStream_t xfer = nullptr;    // read-back stream (non-blocking)
+  cudaEvent_t ev_snap = nullptr;  // snapshot taken
+  cudaEvent_t ev_done = nullptr;  // read-back finished (snapshot free again)
+  bool pending = false;
 };
 
 namespace {
@@ -96,10 +104,23 @@ int device_status(swe_handle *s) {
 // Host FP64 [ny][nx] -> device plane; depth fields (is_depth) are stored as
 // the anomaly ha (the bed must already be on the device).
 // A page-locked host array is read by the conversion kernel directly (one
-// pass across the host link); pageable memory goes through the staging plane.
+// pass across the host link); pageable memory goes through the staging plane,
+// and so does any array while an asynchronous read-back is in flight: the
+// copy engines carry both directions of the link at once, a kernel reading
+// host memory beside them does not.
+bool readback_in_flight(swe_handle *s) {
+  if (!s->pending) return false;
+  const cudaError_t e = cudaEventQuery(s->ev_done);
+  if (e == cudaErrorNotReady) {
+    (void)cudaGetLastError();
+    return true;
+  }
+  return false;
+}
+
 int upload_field(swe_handle *s, const double *src, void *dst, bool is_depth) {
   const size_t bytes = sizeof(double) * (size_t)s->nx * s->ny;
-  const void *in = pinned_device_ptr(src, bytes);
+  const void *in = readback_in_flight(s) ? nullptr : pinned_device_ptr(src, bytes);
   cudaError_t e = cudaSuccess;
   if (!in) {
     e = cudaMemcpyAsync(s->staging, src, bytes, cudaMemcpyHostToDevice, s->stream);
@@ -333,7 +354,6 @@ int swe_set_state(swe_handle *s, const double *h, const double *hu, const double
   if (rc == SWE_OK) rc = after_state_change(s);
   return rc;
 }
-
 int swe_set_state_device(swe_handle *s, const void *h, const void *hu, const void *hv) {
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
   int rc = import_device(s, h, s->h[0], true);
@@ -396,6 +416,64 @@ int swe_get_state(swe_handle *s, double *h, double *hu, double *hv) {
   if (rc == SWE_OK) rc = cuda_check(s, cudaStreamSynchronize(s->stream));
   if (rc == SWE_OK) rc = swe_sync(s);
   return rc;
+}
+
+int swe_get_state_async(swe_handle *s, double *h, double *hu, double *hv) {
+  if (!s || !h || !hu || !hv) return SWE_EINVAL;
+  if (s->sticky != SWE_OK) return s->sticky;
+  const size_t bytes = sizeof(double) * (size_t)s->nx * s->ny;
+  void *out[3] = {const_cast<void *>(pinned_device_ptr(h, bytes)), const_cast<void *>(pinned_device_ptr(hu, bytes)),
+                  const_cast<void *>(pinned_device_ptr(hv, bytes))};
+  if (!out[0] || !out[1] || !out[2]) return swe_get_state(s, h, hu, hv);  // pageable: synchronous
+  const size_t plane = s->elem * (size_t)s->pitch * s->ny;
+  cudaError_t e = cudaSuccess;
+  const size_t nb = sizeof(double) * (size_t)s->nx * s->ny;
+  if (!s->snap) {
+    e = cudaMalloc(&s->snap, 3 * plane);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->xstage, 3 * nb);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->xfer, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_snap, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_check(s, e);
+  }
+  // the previous read-back must be done with the snapshot
+  if (s->pending) e = cudaStreamWaitEvent(s->stream, s->ev_done, 0);
+  char *snap = (char *)s->snap;
+  const void *src[3] = {s->h[0], s->hu[0], s->hv[0]};
+  for (int f = 0; f < 3 && e == cudaSuccess; ++f)
+    e = cudaMemcpyAsync(snap + f * plane, src[f], plane, cudaMemcpyDeviceToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_snap, s->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->xfer, s->ev_snap, 0);
+  // convert on the device, then let a copy engine carry the bytes (it
+  // overlaps an upload in the other direction better than a kernel writing
+  // host memory)
+  double *xs = s->xstage;
+  const size_t n = (size_t)s->nx * s->ny;
+  for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
+    if (s->prec == SWE_F64)
+      e = export_plane<double>((const double *)(snap + f * plane), xs + f * n, true,
+                               f == 0 ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->xfer);
+    else
+      e = export_plane<float>((const float *)(snap + f * plane), xs + f * n, true,
+                              f == 0 ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->xfer);
+  }
+  double *hosts[3] = {h, hu, hv};
+  for (int f = 0; f < 3 && e == cudaSuccess; ++f)
+    e = cudaMemcpyAsync(hosts[f], xs + f * n, nb, cudaMemcpyDeviceToHost, s->xfer);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_done, s->xfer);
+  if (e != cudaSuccess) return cuda_check(s, e);
+  s->pending = true;
+  return SWE_OK;
+}
+
+int swe_wait_state(swe_handle *s) {
+  if (!s) return SWE_EINVAL;
+  if (s->pending) {
+    const cudaError_t e = cudaEventSynchronize(s->ev_done);
+    s->pending = false;
+    if (e != cudaSuccess) return cuda_check(s, e);
+  }
+  return s->sticky;
 }
 
 int swe_get_state_device(swe_handle *s, void *h, void *hu, void *hv) {
@@ -481,6 +559,14 @@ int swe_set_time(swe_handle *s, double t) {
 int swe_destroy(swe_handle *s) {
   if (!s) return SWE_OK;
   if (s->stream || s->mem) cudaStreamSynchronize(s->stream);
+  if (s->xfer) {
+    cudaStreamSynchronize(s->xfer);
+    cudaStreamDestroy(s->xfer);
+  }
+  if (s->ev_snap) cudaEventDestroy(s->ev_snap);
+  if (s->ev_done) cudaEventDestroy(s->ev_done);
+  if (s->snap) cudaFree(s->snap);
+  if (s->xstage) cudaFree(s->xstage);
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->cap) cudaStreamDestroy(s->cap);
   if (s->mem) cudaFree(s->mem);

@@ -177,10 +177,27 @@ static int blocks_for(size_t n, int threads) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// Conversion grids: four 256-thread CTAs per SM keep enough loads in flight to
+// fill the host link, and leave room for a second conversion (an upload and a
+// read-back on two streams) to run beside it.
+static int conversion_blocks(int ny) {
+  static int sms = 0;
+  if (sms <= 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0) {
+      (void)cudaGetLastError();
+      sms = 152;
+    }
+  }
+  const int cap = 4 * sms;
+  return ny < cap ? ny : cap;
+}
+
 template <typename T>
 cudaError_t import_plane(const void *src, bool src_f64, T *dst, const T *bed_for_depth, double zref, int nx, int ny,
                          int pitch, cudaStream_t st) {
-  const int nb = ny < 4096 ? ny : 4096;
+  const int nb = conversion_blocks(ny);
   if (src_f64) k_import<T, double><<<nb, 256, 0, st>>>((const double *)src, dst, bed_for_depth, zref, nx, ny, pitch);
   else k_import<T, T><<<nb, 256, 0, st>>>((const T *)src, dst, bed_for_depth, zref, nx, ny, pitch);
   return cudaGetLastError();
@@ -189,7 +206,7 @@ cudaError_t import_plane(const void *src, bool src_f64, T *dst, const T *bed_for
 template <typename T>
 cudaError_t export_plane(const T *src, void *dst, bool dst_f64, const T *bed_for_depth, double zref, int nx, int ny,
                          int pitch, cudaStream_t st) {
-  const int nb = ny < 4096 ? ny : 4096;
+  const int nb = conversion_blocks(ny);
   if (dst_f64) k_export<T, double><<<nb, 256, 0, st>>>(src, (double *)dst, bed_for_depth, zref, nx, ny, pitch);
   else k_export<T, T><<<nb, 256, 0, st>>>(src, (T *)dst, bed_for_depth, zref, nx, ny, pitch);
   return cudaGetLastError();

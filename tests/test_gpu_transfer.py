@@ -58,3 +58,47 @@ def test_batch_admit_from_page_locked_arrays():
         x, y = bt.get_state(s0), bt.get_state(s1)
         for u, v in zip(x, y):
             assert np.array_equal(u, v)
+
+
+def _wavy(nx=131, ny=77, seed=11):
+    sc = W.lake_at_rest(nx, ny, eta0=0.0, depth=4.0, rms=1.0, seed=5)
+    rng = np.random.default_rng(seed)
+    sc.h = sc.h + 0.1 * rng.uniform(size=sc.h.shape)
+    sc.hu = 0.2 * rng.normal(size=sc.h.shape)
+    sc.hv = 0.2 * rng.normal(size=sc.h.shape)
+    return sc
+
+
+@pytest.mark.parametrize("precision", [swe.F32, swe.F64])
+def test_async_read_back_overlaps_the_next_upload(precision):
+    sc, other = _wavy(seed=11), _wavy(seed=12)
+    outs = [torch.empty(sc.h.shape, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    out = tuple(t.numpy() for t in outs)
+    with swe.Solver(sc, precision=precision, stream=stream()) as s:
+        s.step(5)
+        ref = s.get_state()
+        s.get_state_async(out)
+        # a new upload and more steps while the read-back is in flight
+        s.set_state(other.h, other.hu, other.hv)
+        s.step(3)
+        s.wait_state()
+        for x, y in zip(out, ref):
+            assert np.array_equal(x, y)
+        now = s.get_state()
+        s.get_state_async(out)
+        s.get_state_async(out)  # the second waits for the first on the device
+        s.wait_state()
+        for x, y in zip(out, now):
+            assert np.array_equal(x, y)
+
+
+def test_async_read_back_into_pageable_arrays_is_synchronous():
+    sc = _wavy()
+    with swe.Solver(sc, precision=swe.F32, stream=stream()) as s:
+        s.step(4)
+        ref = s.get_state()
+        out = tuple(np.empty(sc.h.shape) for _ in range(3))
+        s.get_state_async(out)
+        for x, y in zip(out, ref):  # already filled
+            assert np.array_equal(x, y)
+        s.wait_state()
