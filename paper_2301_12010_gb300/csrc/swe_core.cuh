@@ -746,7 +746,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
   const int i = i0 + yc;
 
   const T wrk = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
-  const bool friction = p.n2 > 0.0;
+  const bool friction = K.gn2 > T(0);  // FP32 compare (g n^2 > 0 iff n > 0)
 #pragma unroll
   for (int pass = 0; pass < 2; ++pass) {
     const bool X = pass == 0;
@@ -1016,10 +1016,12 @@ __host__ __device__ __forceinline__ StageIO<T> io_of(const Field<T> &fd, int sta
   return io;
 }
 
-// One RK stage over the work list of a batch: CTA b handles items b,
-// b + gridDim.x, ...  Per-scenario scalars are taken when the CTA enters a
-// scenario and its accumulators are published when it leaves it; the lead
-// CTA of a scenario is the one that owns its tile 0.
+// One RK stage over the work list of a batch (scenario after scenario, tiles
+// in order): CTA b handles the contiguous chunk of items [b W, (b+1) W),
+// W = ceil(total / gridDim.x), so that it meets one or two scenarios rather
+// than a new one at every item.  Per-scenario scalars are taken when the CTA
+// enters a scenario and its accumulators are published when it leaves it;
+// the lead CTA of a scenario is the one whose chunk holds its tile 0.
 template <typename T, int TX, int TY, int NT, int S, int STAGE>
 __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T *smem, RedSmem &red, Phys &sp) {
   using G = TileGeom<T, TX, TY>;
@@ -1028,20 +1030,21 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
   __shared__ StageIO<T> s_io;  // planes of the current scenario (kept out of registers)
   T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
   const int tid = threadIdx.x;
-  const int G0 = gridDim.x;
+  const int W = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int item_end = min((int)(blockIdx.x + 1) * W, total);
   int cur = -1;
   bool lead = false, skip = true;
   double dt = 0.0;
   T tdt = T(0), rcap = T(0), alx = T(0), aly = T(0), eta_in = T(0), u_in = T(0);
   Acc<T> acc;
-  int item = blockIdx.x;
-  if (item < total) {
+  int item = (int)blockIdx.x * W;
+  if (item < item_end) {
     const int s0 = slot_of_item(slots, nslots, item);
     const int t0 = item - slots[s0].first_item;
     issue_box<T, TX, TY, NT>(io_of(slots[s0].fd, STAGE), (t0 % slots[s0].tiles_x) * TX, (t0 / slots[s0].tiles_x) * TY, box0);
   }
   cp_commit();
-  for (int it = 0; item < total; ++it, item += G0) {
+  for (int it = 0; item < item_end; ++it, ++item) {
     if (tid == 0) s_slot[it & 1] = slot_of_item(slots, nslots, item);
     // this item's box has landed for every thread's copies, and every thread
     // is done with the previous item (whose buffer is refilled below)
@@ -1056,13 +1059,13 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
       if (tid == 0) {
         sp = sl.p;
         s_io = io_of(sl.fd, STAGE);
-        const bool ld = (sl.first_item % G0) == (int)blockIdx.x;
+        const bool ld = sl.first_item / W == (int)blockIdx.x;
         stage_scalars<T, STAGE>(sp, sl.sc, ld, red);
         s_skip = red.skip;
       }
       __syncthreads();
       cur = s;
-      lead = (sl.first_item % G0) == (int)blockIdx.x;
+      lead = sl.first_item / W == (int)blockIdx.x;
       skip = s_skip != 0u;
       dt = red.dt;
       tdt = red_v<T>(red, SV_DT);
@@ -1073,8 +1076,8 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
       u_in = red_v<T>(red, SV_UIN);
     }
     T *box = (it & 1) ? box1 : box0;
-    const int nitem = item + G0;
-    if (nitem < total) {
+    const int nitem = item + 1;
+    if (nitem < item_end) {
       const int ns = slot_of_item(slots, nslots, nitem);
       const int nt = nitem - slots[ns].first_item;
       issue_box<T, TX, TY, NT>(io_of(slots[ns].fd, STAGE), (nt % slots[ns].tiles_x) * TX,
