@@ -231,6 +231,8 @@ template <> __device__ __forceinline__ float2 sp<float2>(double c) { return make
 template <> __device__ __forceinline__ double2 sp<double2>(double c) { return make_double2(c, c); }
 template <typename V> __device__ __forceinline__ V vsub(V a, V b) { return vfma(sp<V>(-1.0), b, a); }
 
+template <bool B> struct BoolC { static constexpr bool value = B; };
+
 // Pair type of a precision: components 0 and 1 of a sweep travel together.
 template <typename T> struct Pair;
 template <> struct Pair<float> {
@@ -344,22 +346,35 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Shared-memory geometry of one tile.
+// Shared-memory geometry of one tile.  The halo box covers columns
+// i0-4 .. i0+TX+3 (OX = 4: a 16-byte aligned start for the chunked copies;
+// the stencils read i0-3 .. i0+TX+2) and rows j0-3 .. j0+TY+2 (OY = 3).
 template <typename T, int TX, int TY>
 struct TileGeom {
-  static constexpr int BW = TX + 6;  // halo box width (cells i0-3 .. i0+TX+2)
+  static constexpr int OX = 4, OY = 3;
+  static constexpr int BW = TX + 8;  // halo box width
   static constexpr int BH = TY + 6;  // halo box height
-  // row pitch: = 1 mod 8 floats (x-pass lanes on 8 rows x 4 strips hit distinct banks)
-  static constexpr int P = ((BW + 7) / 8) * 8 + 1;
+  static constexpr int CH = 16 / (int)sizeof(T);  // elements per 16-byte chunk
+  // row pitch: 16-byte rows; FP32: P/4 odd, so that the x-pass 16-byte window
+  // loads of a quarter-warp (2 rows x 4 strips of 8, or 4 rows x 2 strips of
+  // 16) fall in distinct bank groups; FP64: P = 2 mod 8 (2-way at most for the
+  // scalar x-pass loads)
+  static constexpr int P = sizeof(T) == 4 ? ((((BW + 3) / 4) % 2) ? (BW + 3) / 4 * 4 : (BW + 3) / 4 * 4 + 4)
+                                          : ((BW + 1) / 2 * 2 + ((10 - (BW + 1) / 2 * 2 % 8) % 8));
   static constexpr int FIELD = BH * P;  // one field of the box
   static constexpr int BOX = 4 * FIELD; // ha, hu, hv, b
   static constexpr int LP = TX + 1;        // L_x row pitch (x-pass lanes on 8 rows hit distinct banks)
   static constexpr int NC = TY * LP;       // one L_x component
   static constexpr int ELEMS = 2 * BOX + 3 * NC;  // two boxes (double buffer) + L_x
   static constexpr size_t BYTES = sizeof(T) * (size_t)ELEMS;
+  static_assert(TX % 4 == 0 && P % CH == 0 && P >= BW, "16-byte aligned box rows");
 };
 
 // Per-stage values broadcast from thread 0 to the CTA, in both precisions.
@@ -392,26 +407,27 @@ struct StageIO {
   int nx, ny, pitch;
 };
 
-// Issue the asynchronous copies of the halo box of tile (i0, j0) into box:
-// interior cells only; ghost positions are patched after arrival.
+// Issue the asynchronous copies of the halo box of tile (i0, j0) into box, in
+// 16-byte chunks: a chunk starts at a multiple of CH columns (the tile origin
+// is one), so none straddles the domain edge; chunks that start inside the
+// domain may run into the row's padding (the plane pitch is a multiple of 32
+// elements), and those positions are ghosts that patch_box fills.
 template <typename T, int TX, int TY, int NT>
 __device__ __forceinline__ void issue_box(const StageIO<T> &io, int i0, int j0, T *box) {
   using G = TileGeom<T, TX, TY>;
+  constexpr int NCH = G::BW / G::CH;  // chunks per row
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const T *src[4] = {io.ha, io.hu, io.hv, io.b};
   for (int r = warp; r < G::BH; r += NT / 32) {
-    const int j = j0 - 3 + r;
+    const int j = j0 - G::OY + r;
     if (j < 0 || j >= io.ny) continue;
 #pragma unroll
-    for (int c = lane; c < ((G::BW + 31) / 32) * 32; c += 32) {
-      const int i = i0 - 3 + c;
-      if (c < G::BW && i >= 0 && i < io.nx) {
+    for (int m = lane; m < ((NCH + 31) / 32) * 32; m += 32) {
+      const int i = i0 - G::OX + m * G::CH;
+      if (m < NCH && i >= 0 && i < io.nx) {
         const size_t go = (size_t)j * io.pitch + i;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          if (sizeof(T) == 4) cp_async4(box + f * G::FIELD + r * G::P + c, src[f] + go);
-          else cp_async8(box + f * G::FIELD + r * G::P + c, src[f] + go);
-        }
+        for (int f = 0; f < 4; ++f) cp_async16(box + f * G::FIELD + r * G::P + m * G::CH, src[f] + go);
       }
     }
   }
@@ -430,7 +446,7 @@ __device__ __noinline__ void patch_box(const StageIO<T> &io, const Phys &p, int 
   T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
   for (int q = threadIdx.x; q < G::BH * G::BW; q += NT) {
     const int r = q / G::BW, c = q - r * G::BW;
-    const int i = i0 - 3 + c, j = j0 - 3 + r;
+    const int i = i0 - G::OX + c, j = j0 - G::OY + r;
     const bool in_i = i >= 0 && i < nx, in_j = j >= 0 && j < ny;
     if (in_i && in_j) continue;  // a real cell, already loaded
     const int o = r * G::P + c;
@@ -457,8 +473,8 @@ __device__ __noinline__ void patch_box(const StageIO<T> &io, const Phys &p, int 
     }
     // mirror source: a real cell of the same box
     int mc = c, mr = r;
-    if (xg) mc = (i < 0 ? (-1 - i) : (2 * nx - 1 - i)) - (i0 - 3);
-    else mr = (j < 0 ? (-1 - j) : (2 * ny - 1 - j)) - (j0 - 3);
+    if (xg) mc = (i < 0 ? (-1 - i) : (2 * nx - 1 - i)) - (i0 - G::OX);
+    else mr = (j < 0 ? (-1 - j) : (2 * ny - 1 - j)) - (j0 - G::OY);
     const int m = mr * G::P + mc;
     const T cb = bb[m];
     bb[o] = cb;
@@ -508,9 +524,7 @@ struct Window {
   //   f+- = (F +- alpha Q)/2   (carried times sqrt 3),
   // i.e. F of Eq. (2) in x and G of Eq. (3), momentum components swapped, in y.
   template <int s>
-  __device__ __forceinline__ void put(const T *bha, const T *bqn, const T *bqt, const T *bb, int o, T sa, T pg,
-                                      T zref, V2 eps2, T eps1, const Phys &p) {
-    const T ha = bha[o], qn = bqn[o], qt = bqt[o], b = bb[o];
+  __device__ __forceinline__ void put(T ha, T qn, T qt, T b, T sa, T pg, T zref, V2 eps2, T eps1, const Phys &p) {
     const T d = still_depth(b, zref);
     const T h = ha + d;
     T un = T(0);
@@ -589,7 +603,7 @@ struct Window {
 // db = 12 (bhat(k+1) - bhat(k)).  Adds ew times the mass flux sum Fs_0
 // through the domain edges that the strip owns (face -1/2 at k = 0 of the
 // first strip, face n-1/2 at k >= 1).
-template <typename T, int S, typename E>
+template <typename T, int S, bool XP, typename E>
 __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T *bqt, const T *bb, int o0, int st,
                                             T alpha, const Consts<T> &K, const Phys &p, int ia, int n, bool edge_ok,
                                             T ew, const E &emit, T &edge) {
@@ -597,14 +611,51 @@ __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T 
   Window<T> win;
   const T sa = T(0.8660254037844386) * alpha, pg = K.pg, zref = K.zref, eps1 = K.eps12;
   const V2 eps2 = Pair<T>::mk(eps1, eps1);
-  win.template put<0>(bha, bqn, bqt, bb, o0, sa, pg, zref, eps2, eps1, p);
-  win.template put<1>(bha, bqn, bqt, bb, o0 + st, sa, pg, zref, eps2, eps1, p);
-  win.template put<2>(bha, bqn, bqt, bb, o0 + 2 * st, sa, pg, zref, eps2, eps1, p);
-  win.template put<3>(bha, bqn, bqt, bb, o0 + 3 * st, sa, pg, zref, eps2, eps1, p);
-  win.template put<4>(bha, bqn, bqt, bb, o0 + 4 * st, sa, pg, zref, eps2, eps1, p);
+  // Window slot q is box offset o0 + q st.  FP32 x pass: the slots lie along
+  // one box row and o0 - 1 is 16-byte aligned, so slot q is element (q+1) % 4
+  // of the 16-byte chunk (q+1) / 4 of each field, loaded once before its first
+  // use (four fields per chunk).
+  constexpr bool VEC = XP && sizeof(T) == 4;
+  constexpr int NCH = (S + 9) / 4;
+  float4 ch[4][NCH];
+  auto cell = [&](int q, T &ha, T &qn, T &qt, T &b) {
+    if constexpr (VEC) {
+      const int m = (q + 1) >> 2, e = (q + 1) & 3;
+      if (q == 0 || e == 0) {
+        const int c0 = o0 - 1 + 4 * m;
+        ch[0][m] = *reinterpret_cast<const float4 *>(bha + c0);
+        ch[1][m] = *reinterpret_cast<const float4 *>(bqn + c0);
+        ch[2][m] = *reinterpret_cast<const float4 *>(bqt + c0);
+        ch[3][m] = *reinterpret_cast<const float4 *>(bb + c0);
+      }
+      const auto pick = [e](const float4 &v) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); };
+      ha = pick(ch[0][m]);
+      qn = pick(ch[1][m]);
+      qt = pick(ch[2][m]);
+      b = pick(ch[3][m]);
+    } else {
+      const int o = o0 + q * st;
+      ha = bha[o];
+      qn = bqn[o];
+      qt = bqt[o];
+      b = bb[o];
+    }
+  };
+  T ha, qn, qt, b;
+  cell(0, ha, qn, qt, b);
+  win.template put<0>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
+  cell(1, ha, qn, qt, b);
+  win.template put<1>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
+  cell(2, ha, qn, qt, b);
+  win.template put<2>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
+  cell(3, ha, qn, qt, b);
+  win.template put<3>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
+  cell(4, ha, qn, qt, b);
+  win.template put<4>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
 #pragma unroll
   for (int k = 0; k <= S; ++k) {
-    win.template put<5>(bha, bqn, bqt, bb, o0 + (k + 5) * st, sa, pg, zref, eps2, eps1, p);
+    cell(k + 5, ha, qn, qt, b);
+    win.template put<5>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
     V2 x01;
     T x2, x3;
     win.face(x01, x2, x3);
@@ -655,7 +706,7 @@ struct CellEpilogue {
     const T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
     if (X) {
       const int o = xr * G::LP + xc0 + k;
-      const T ha = bha[(xr + 3) * G::P + xc0 + k + 3];
+      const T ha = bha[(xr + G::OY) * G::P + xc0 + k + G::OX];
       sL[o] = -dF0 * K.rfx;
       sL[G::NC + o] = -dF1 * K.rfx - K.g12dx * ha * dbk;
       sL[2 * G::NC + o] = -dF2 * K.rfx;
@@ -664,7 +715,7 @@ struct CellEpilogue {
     const int j = j0 + yr0 + k;
     if (i >= io.nx || j >= io.ny) return;
     const int o = (yr0 + k) * G::LP + yc;
-    const int bo = (yr0 + k + 3) * G::P + yc + 3;
+    const int bo = (yr0 + k + G::OY) * G::P + yc + G::OX;
     const T ha = bha[bo], hu = bhu[bo], hv = bhv[bo], bc = bb[bo];
     const T d = still_depth(bc, K.zref);
     const T h = ha + d;
@@ -747,9 +798,9 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
 
   const T wrk = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
   const bool friction = K.gn2 > T(0);  // FP32 compare (g n^2 > 0 iff n > 0)
-#pragma unroll
-  for (int pass = 0; pass < 2; ++pass) {
-    const bool X = pass == 0;
+  // one body per pass, specialised at compile time (X: the x pass)
+  auto pass = [&](auto xflag) {
+    constexpr bool X = decltype(xflag)::value;
     // U^n of the y-pass cells (stages 2, 3), fetched before the sweep so that
     // the global-memory latency hides behind it
     T u0[3][S];
@@ -765,11 +816,14 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
       }
     }
     const CellEpilogue<T, TX, TY, S, STAGE> emit{io, p, K, box, sL, X, xr, xc0, yc, yr0, i, j0, tdt, rcap, wrk, friction, u0, acc};
-    sweep_strip<T, S>(bha, X ? bhu : bhv, X ? bhv : bhu, bb, X ? (xr + 3) * G::P + xc0 : yr0 * G::P + yc + 3,
-                      X ? 1 : G::P, X ? alx : aly, K, p, X ? i0 + xc0 : j0 + yr0, X ? nx : ny,
-                      X ? (j0 + xr < ny) : (i < nx), X ? K.ewx : K.ewy, emit, acc.edge);
-    if (X) __syncthreads();
-  }
+    sweep_strip<T, S, X>(bha, X ? bhu : bhv, X ? bhv : bhu, bb,
+                         X ? (xr + G::OY) * G::P + xc0 + G::OX - 3 : yr0 * G::P + yc + G::OX,
+                         X ? 1 : G::P, X ? alx : aly, K, p, X ? i0 + xc0 : j0 + yr0, X ? nx : ny,
+                         X ? (j0 + xr < ny) : (i < nx), X ? K.ewx : K.ewy, emit, acc.edge);
+  };
+  pass(BoolC<true>{});
+  __syncthreads();
+  pass(BoolC<false>{});
 }
 
 // Per-stage scalars and the skip decision, taken by thread 0 of every CTA;
