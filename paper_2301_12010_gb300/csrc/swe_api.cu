@@ -40,6 +40,7 @@ struct swe_handle {
   double *staging = nullptr;      // ny*nx doubles: host-format transfers
   DevScalars *sc = nullptr;
   double *partials = nullptr;     // kMassBlocks + 1 (last: mass result)
+  BoxMaps maps[3] = {};           // tensor maps of the halo-box copies, per RK stage
   cudaGraphExec_t graph = nullptr;
   double cfl_dev = -1.0;          // CFL value last written to the device scalars
   int sticky = SWE_OK;            // first host-visible error
@@ -84,8 +85,8 @@ Field<T> field_of(const swe_handle *s) {
 cudaError_t enqueue_step(swe_handle *s, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
-    if (s->prec == SWE_F64) e = launch_stage<double>(s->tile, field_of<double>(s), s->phys, s->sc, stage, st);
-    else e = launch_stage<float>(s->tile, field_of<float>(s), s->phys, s->sc, stage, st);
+    if (s->prec == SWE_F64) e = launch_stage<double>(s->tile, field_of<double>(s), s->phys, s->sc, stage, st, s->maps);
+    else e = launch_stage<float>(s->tile, field_of<float>(s), s->phys, s->sc, stage, st, s->maps);
   }
   return e;
 }
@@ -331,6 +332,11 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   if (rc == SWE_OK && cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) rc = SWE_ECUDA;
   if (rc == SWE_OK) {
     e = s->prec == SWE_F64 ? prepare_shape<double>(s->tile) : prepare_shape<float>(s->tile);
+    rc = cuda_check(s, e);
+  }
+  if (rc == SWE_OK) {
+    e = s->prec == SWE_F64 ? make_maps<double>(s->tile, field_of<double>(s), s->maps)
+                           : make_maps<float>(s->tile, field_of<float>(s), s->maps);
     rc = cuda_check(s, e);
   }
   if (rc == SWE_OK) rc = cuda_check(s, cudaMemsetAsync(s->mem, 0, plane_al * 10, s->stream));
@@ -586,8 +592,9 @@ int swe_time_stages(swe_handle *s, int32_t n, double cfl, double *ms_total, doub
   for (int32_t it = 0; it < n && e == cudaSuccess; ++it) {
     e = cudaEventRecord(ev[0], s->stream);
     for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
-      if (s->prec == SWE_F64) e = launch_stage<double>(s->tile, field_of<double>(s), s->phys, s->sc, stage, s->stream);
-      else e = launch_stage<float>(s->tile, field_of<float>(s), s->phys, s->sc, stage, s->stream);
+      if (s->prec == SWE_F64)
+        e = launch_stage<double>(s->tile, field_of<double>(s), s->phys, s->sc, stage, s->stream, s->maps);
+      else e = launch_stage<float>(s->tile, field_of<float>(s), s->phys, s->sc, stage, s->stream, s->maps);
       if (e == cudaSuccess) e = cudaEventRecord(ev[stage], s->stream);
     }
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);

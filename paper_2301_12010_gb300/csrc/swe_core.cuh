@@ -31,9 +31,11 @@
 // buffer reused by the x pass and then the y pass, the x-pass result L_x, and
 // the anomaly ha of the tile's own cells.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the descriptor type only; no driver calls here)
+#include <cuda_runtime.h>
+
 #include <cmath>
 #include <cstdint>
-#include <cuda_runtime.h>
 
 namespace swe {
 
@@ -353,6 +355,48 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// ------------------------------------------- tensor copies (TMA) + mbarrier
+// The single-scenario stage kernels load each tile's halo box with one 2D
+// tensor copy per field (box P x BH at (i0 - 4, j0 - 3); elements outside the
+// plane read as zero), completing on an mbarrier of the destination buffer.
+struct BoxMaps {
+  CUtensorMap m[4];  // ha, hu, hv, b of the stage input
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes));
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// Bounded wait for phase `parity` of bar: false if it did not complete within
+// ~2^31 SM cycles (~1 s).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Shared-memory geometry of one tile.  The halo box covers columns
 // i0-4 .. i0+TX+3 (OX = 4: a 16-byte aligned start for the chunked copies;
 // the stencils read i0-3 .. i0+TX+2) and rows j0-3 .. j0+TY+2 (OY = 3).
@@ -368,7 +412,8 @@ struct TileGeom {
   // scalar x-pass loads)
   static constexpr int P = sizeof(T) == 4 ? ((((BW + 3) / 4) % 2) ? (BW + 3) / 4 * 4 : (BW + 3) / 4 * 4 + 4)
                                           : ((BW + 1) / 2 * 2 + ((10 - (BW + 1) / 2 * 2 % 8) % 8));
-  static constexpr int FIELD = BH * P;  // one field of the box
+  static constexpr int FA = 128 / (int)sizeof(T);  // 128-byte alignment of each field (tensor copies)
+  static constexpr int FIELD = (BH * P + FA - 1) / FA * FA;  // one field of the box
   static constexpr int BOX = 4 * FIELD; // ha, hu, hv, b
   static constexpr int LP = TX + 1;        // L_x row pitch (x-pass lanes on 8 rows hit distinct banks)
   static constexpr int NC = TY * LP;       // one L_x component
@@ -939,24 +984,42 @@ __device__ __forceinline__ void publish(const Phys &p, DevScalars *sc, bool lead
 }
 
 // Persistent stage over all tiles of one scenario: CTA b handles tiles
-// b, b + gridDim.x, ...; the halo box of the next tile is copied
-// asynchronously while the current one is computed.
+// b, b + gridDim.x, ...; the halo box of the next tile arrives by tensor
+// copies (thread 0 issues one per field) into the second buffer while the
+// current tile is computed.  Each buffer has an mbarrier; every thread waits
+// on it with a bounded spin (on expiry the CTA flags ST_TIMEOUT and returns,
+// no other copy being in flight at that point).
 template <typename T, int TX, int TY, int NT, int S, int STAGE>
-__device__ void stage_persistent(const StageIO<T> &io, const Phys &p, DevScalars *sc, T *smem, RedSmem &red,
-                                 int first, int stride, bool lead) {
+__device__ void stage_persistent(const StageIO<T> &io, const BoxMaps &maps, const Phys &p, DevScalars *sc, T *smem,
+                                 RedSmem &red, int first, int stride, bool lead) {
   using G = TileGeom<T, TX, TY>;
+  constexpr unsigned kBoxBytes = 4u * G::BH * G::P * (unsigned)sizeof(T);
+  __shared__ unsigned long long bar[2];
+  __shared__ unsigned s_fail;
   const int tid = threadIdx.x;
   const int tiles_x = (io.nx + TX - 1) / TX, tiles_y = (io.ny + TY - 1) / TY;
   const int ntiles = tiles_x * tiles_y;
   T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
+  auto issue = [&](int tile, T *dst, unsigned long long *b) {
+    const int x = (tile % tiles_x) * TX - G::OX, y = (tile / tiles_x) * TY - G::OY;
+    mbar_expect_tx(b, kBoxBytes);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) tma_load_2d(dst + f * G::FIELD, &maps.m[f], x, y, b);
+  };
   // the first box is in flight while thread 0 takes the stage's scalars
   int t = first;
-  if (t < ntiles) issue_box<T, TX, TY, NT>(io, (t % tiles_x) * TX, (t / tiles_x) * TY, box0);
-  cp_commit();
-  if (tid == 0) stage_scalars<T, STAGE>(p, sc, lead, red);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1u);
+    mbar_init(&bar[1], 1u);
+    mbar_fence_init();
+    s_fail = 0u;
+    if (t < ntiles) issue(t, box0, &bar[0]);
+    stage_scalars<T, STAGE>(p, sc, lead, red);
+  }
   __syncthreads();
   if (red.skip) {
-    cp_wait<0>();
+    if (tid == 0 && t < ntiles && !mbar_wait(&bar[0], 0u)) atomicOr(&sc->status, ST_TIMEOUT);
+    __syncthreads();
     return;
   }
   const double dt = red.dt;
@@ -965,15 +1028,24 @@ __device__ void stage_persistent(const StageIO<T> &io, const Phys &p, DevScalars
   const T zref = consts<T>(p).zref;
   const T eta_in = red_v<T>(red, SV_ETA), u_in = red_v<T>(red, SV_UIN);
   Acc<T> acc;
+  unsigned phase = 0u;  // bit b: parity of the next wait on bar[b]
   for (int it = 0; t < ntiles; ++it, t += stride) {
-    T *box = (it & 1) ? box1 : box0;
-    // one barrier: this tile's box has landed for every thread's copies, and
-    // every thread is done with the previous tile (whose buffer is refilled next)
-    cp_wait<0>();
+    const int b = it & 1;
+    T *box = b ? box1 : box0;
+    if (!mbar_wait(&bar[b], (phase >> b) & 1u)) s_fail = 1u;
+    phase ^= 1u << b;
+    // one barrier: this tile's box has landed, and every thread is done with
+    // the previous tile (whose buffer is refilled next)
     __syncthreads();
+    if (s_fail) {
+      if (tid == 0) atomicOr(&sc->status, ST_TIMEOUT);
+      return;
+    }
     const int tn = t + stride;
-    if (tn < ntiles) issue_box<T, TX, TY, NT>(io, (tn % tiles_x) * TX, (tn / tiles_x) * TY, (it & 1) ? box0 : box1);
-    cp_commit();
+    if (tid == 0 && tn < ntiles) {
+      fence_proxy_async();  // order the generic writes into that buffer (ghost patching) before the copies
+      issue(tn, b ? box0 : box1, &bar[b ^ 1]);
+    }
     const int i0 = (t % tiles_x) * TX, j0 = (t / tiles_x) * TY;
     if (i0 == 0 || j0 == 0 || i0 + TX + 3 > io.nx || j0 + TY + 3 > io.ny) {
       patch_box<T, TX, TY, NT>(io, p, i0, j0, box, zref, eta_in, u_in);
@@ -981,7 +1053,6 @@ __device__ void stage_persistent(const StageIO<T> &io, const Phys &p, DevScalars
     }
     tile_compute<T, TX, TY, NT, S, STAGE>(io, p, i0, j0, box, sL, tdt, rcap, alx, aly, acc);
   }
-  cp_wait<0>();
   publish<T, NT, STAGE>(p, sc, lead, red, dt, acc);
 }
 

@@ -24,12 +24,13 @@ constexpr int MINB = SWE_PREC == 32 ? P::MINB32 : P::MINB64;
 // Templated on the shape index and precision so that every unit's kernels have
 // distinct names.
 template <int K, typename R, int STAGE>
-__global__ void __launch_bounds__(ShapeP<K>::NT, MINB) stage_kernel(StageIO<R> io, Phys p, DevScalars *sc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(ShapeP<K>::NT, MINB)
+    stage_kernel(StageIO<R> io, const __grid_constant__ BoxMaps maps, Phys p, DevScalars *sc) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ RedSmem red;
   using Q = ShapeP<K>;
-  stage_persistent<R, Q::TX, Q::TY, Q::NT, Q::S, STAGE>(io, p, sc, reinterpret_cast<R *>(smem_raw), red, blockIdx.x,
-                                                        gridDim.x, blockIdx.x == 0);
+  stage_persistent<R, Q::TX, Q::TY, Q::NT, Q::S, STAGE>(io, maps, p, sc, reinterpret_cast<R *>(smem_raw), red,
+                                                        blockIdx.x, gridDim.x, blockIdx.x == 0);
 }
 
 namespace {
@@ -56,17 +57,42 @@ cudaError_t SWE_CAT(prepare_shape_, SWE_SHAPE)<Real>() {
 
 template <>
 cudaError_t SWE_CAT(launch_shape_, SWE_SHAPE)<Real>(const Field<Real> &fd, const Phys &p, DevScalars *sc, int stage,
-                                                     cudaStream_t st) {
+                                                     cudaStream_t st, const BoxMaps *maps) {
   const int ntiles = ((fd.nx + P::TX - 1) / P::TX) * ((fd.ny + P::TY - 1) / P::TY);
   int grid = g_resident * (g_sms > 0 ? g_sms : 1);
   if (grid > ntiles) grid = ntiles;
   const StageIO<Real> io = io_of(fd, stage);
+  const BoxMaps &m = maps[stage - 1];
   switch (stage) {
-    case 1: stage_kernel<SWE_SHAPE, Real, 1><<<grid, P::NT, kSmem, st>>>(io, p, sc); break;
-    case 2: stage_kernel<SWE_SHAPE, Real, 2><<<grid, P::NT, kSmem, st>>>(io, p, sc); break;
-    default: stage_kernel<SWE_SHAPE, Real, 3><<<grid, P::NT, kSmem, st>>>(io, p, sc); break;
+    case 1: stage_kernel<SWE_SHAPE, Real, 1><<<grid, P::NT, kSmem, st>>>(io, m, p, sc); break;
+    case 2: stage_kernel<SWE_SHAPE, Real, 2><<<grid, P::NT, kSmem, st>>>(io, m, p, sc); break;
+    default: stage_kernel<SWE_SHAPE, Real, 3><<<grid, P::NT, kSmem, st>>>(io, m, p, sc); break;
   }
   return cudaGetLastError();
+}
+
+// 2D tensor maps over the planes (nx x ny elements, row pitch in bytes), one
+// box P x BH per copy; elements outside the plane read as zero.
+template <>
+cudaError_t SWE_CAT(make_maps_, SWE_SHAPE)<Real>(const Field<Real> &fd, BoxMaps out[3]) {
+  using G = TileGeom<Real, P::TX, P::TY>;
+  const EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const CUtensorMapDataType dtype = sizeof(Real) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const cuuint64_t dims[2] = {(cuuint64_t)fd.nx, (cuuint64_t)fd.ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)fd.pitch * sizeof(Real)};
+  const cuuint32_t box[2] = {(cuuint32_t)G::P, (cuuint32_t)G::BH};
+  const cuuint32_t estr[2] = {1u, 1u};
+  for (int s = 0; s < 3; ++s) {
+    const void *planes[4] = {fd.h[s], fd.hu[s], fd.hv[s], fd.b};
+    for (int f = 0; f < 4; ++f) {
+      const CUresult r = enc(&out[s].m[f], dtype, 2, const_cast<void *>(planes[f]), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+  }
+  return cudaSuccess;
 }
 
 }  // namespace swe

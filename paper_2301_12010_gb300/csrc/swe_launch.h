@@ -44,7 +44,9 @@ SWE_SHAPES(SWE_PICK)
   cudaError_t prepare_shape_##K();                                                               \
   template <typename T>                                                                          \
   cudaError_t launch_shape_##K(const Field<T> &fd, const Phys &p, DevScalars *sc, int stage,      \
-                               cudaStream_t st);                                                 \
+                               cudaStream_t st, const BoxMaps *maps);                            \
+  template <typename T>                                                                          \
+  cudaError_t make_maps_##K(const Field<T> &fd, BoxMaps out[3]);                                 \
   cudaError_t batch_resident_##K(int *per_sm);                                                   \
   cudaError_t batch_launch_##K(const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, cudaStream_t st);
 SWE_SHAPES(SWE_DECL)
@@ -81,8 +83,19 @@ float thr32(double thr);
 
 template <typename T>
 cudaError_t prepare_shape(int k);
+// Tensor maps of the halo-box copies for shape k: out[s] covers the input
+// planes of RK stage s + 1 (ha, hu, hv of U^n, U1, U2 and the bed).
 template <typename T>
-cudaError_t launch_stage(int k, const Field<T> &fd, const Phys &p, DevScalars *sc, int stage, cudaStream_t st);
+cudaError_t make_maps(int k, const Field<T> &fd, BoxMaps out[3]);
+template <typename T>
+cudaError_t launch_stage(int k, const Field<T> &fd, const Phys &p, DevScalars *sc, int stage, cudaStream_t st,
+                         const BoxMaps *maps);
+// cuTensorMapEncodeTiled from the driver (resolved once through the runtime;
+// nullptr if unavailable)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder();
 // CTAs per SM of the batch kernel for a shape, and one cooperative launch.
 cudaError_t batch_resident(int shape, int *per_sm);
 cudaError_t batch_launch(int shape, const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, cudaStream_t st);

@@ -36,10 +36,38 @@ cudaError_t prepare_shape(int k) {
 }
 
 template <typename T>
-cudaError_t launch_stage(int k, const Field<T> &fd, const Phys &p, DevScalars *sc, int stage, cudaStream_t st) {
+cudaError_t make_maps(int k, const Field<T> &fd, BoxMaps out[3]) {
   switch (k) {
 #define SWE_CASE(K, TX, TY, NT, S, M32, M64) \
-  case K: return launch_shape_##K<T>(fd, p, sc, stage, st);
+  case K: return make_maps_##K<T>(fd, out);
+    SWE_SHAPES(SWE_CASE)
+#undef SWE_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+    else
+      (void)cudaGetLastError();
+  }
+  return fn;
+}
+
+template <typename T>
+cudaError_t launch_stage(int k, const Field<T> &fd, const Phys &p, DevScalars *sc, int stage, cudaStream_t st,
+                         const BoxMaps *maps) {
+  switch (k) {
+#define SWE_CASE(K, TX, TY, NT, S, M32, M64) \
+  case K: return launch_shape_##K<T>(fd, p, sc, stage, st, maps);
     SWE_SHAPES(SWE_CASE)
 #undef SWE_CASE
   }
@@ -68,7 +96,11 @@ cudaError_t batch_launch(int k, const BatchSlot<float> *slots, BatchCtl *ctl, in
 
 template cudaError_t prepare_shape<float>(int);
 template cudaError_t prepare_shape<double>(int);
-template cudaError_t launch_stage<float>(int, const Field<float> &, const Phys &, DevScalars *, int, cudaStream_t);
-template cudaError_t launch_stage<double>(int, const Field<double> &, const Phys &, DevScalars *, int, cudaStream_t);
+template cudaError_t make_maps<float>(int, const Field<float> &, BoxMaps[3]);
+template cudaError_t make_maps<double>(int, const Field<double> &, BoxMaps[3]);
+template cudaError_t launch_stage<float>(int, const Field<float> &, const Phys &, DevScalars *, int, cudaStream_t,
+                                         const BoxMaps *);
+template cudaError_t launch_stage<double>(int, const Field<double> &, const Phys &, DevScalars *, int, cudaStream_t,
+                                          const BoxMaps *);
 
 }  // namespace swe
