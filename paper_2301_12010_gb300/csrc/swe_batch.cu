@@ -27,6 +27,7 @@ struct Slot {
   double *staging = nullptr;
   Field<float> fd{};
   Phys p{};
+  BoxMaps maps[3] = {};  // tensor maps of the halo-box copies (the batch's tile shape)
 };
 
 size_t plane_bytes(int nx, int ny, int *pitch_out) {
@@ -107,6 +108,7 @@ int upload_table(swe_batch *b) {
     const Slot &sl = b->slots[s];
     if (!sl.live) continue;
     BatchSlot<float> e{};
+    for (int k = 0; k < 3; ++k) e.maps[k] = sl.maps[k];
     e.fd = sl.fd;
     e.p = sl.p;
     e.sc = b->d_sc + s;
@@ -225,6 +227,12 @@ int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, co
   sl.fd.nx = sl.nx;
   sl.fd.ny = sl.ny;
   sl.fd.pitch = sl.pitch;
+  e = make_maps<float>(b->tile, sl.fd, sl.maps);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(sl.mem, b->stream);
+    sl = Slot();
+    return bfail(b, e);
+  }
   sl.p = phys_of(b->prm, dx, dy);
   const size_t nb = sizeof(double) * (size_t)sl.nx * sl.ny;
   const double zr = sl.p.z_ref;

@@ -17,18 +17,18 @@ template <int K>
 __global__ void __launch_bounds__(ShapeP<K>::NT, ShapeP<K>::MINB32)
     batch_kernel(const BatchSlot<float> *slots, BatchCtl *ctl, int k_steps) {
   using P = ShapeP<K>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ RedSmem red;
   __shared__ Phys sp;
   float *smem = reinterpret_cast<float *>(smem_raw);
   const int nslots = *(volatile int *)&ctl->nslots;
   const int total = *(volatile int *)&ctl->total_items;
   for (int k = 0; k < k_steps; ++k) {
-    batch_stage<float, P::TX, P::TY, P::NT, P::S, 1>(slots, nslots, total, smem, red, sp);
+    batch_stage<float, P::TX, P::TY, P::NT, P::S, 1>(slots, nslots, total, smem, red, sp, ctl);
     if (!grid_barrier(ctl, gridDim.x)) return;
-    batch_stage<float, P::TX, P::TY, P::NT, P::S, 2>(slots, nslots, total, smem, red, sp);
+    batch_stage<float, P::TX, P::TY, P::NT, P::S, 2>(slots, nslots, total, smem, red, sp, ctl);
     if (!grid_barrier(ctl, gridDim.x)) return;
-    batch_stage<float, P::TX, P::TY, P::NT, P::S, 3>(slots, nslots, total, smem, red, sp);
+    batch_stage<float, P::TX, P::TY, P::NT, P::S, 3>(slots, nslots, total, smem, red, sp, ctl);
     if (!grid_barrier(ctl, gridDim.x)) return;
   }
 }

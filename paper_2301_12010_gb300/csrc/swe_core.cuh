@@ -339,22 +339,6 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// ------------------------------------------------------- asynchronous copies
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
 // ------------------------------------------- tensor copies (TMA) + mbarrier
 // The single-scenario stage kernels load each tile's halo box with one 2D
 // tensor copy per field (box P x BH at (i0 - 4, j0 - 3); elements outside the
@@ -451,32 +435,6 @@ struct StageIO {
   T *oha, *ohu, *ohv;        // stage output
   int nx, ny, pitch;
 };
-
-// Issue the asynchronous copies of the halo box of tile (i0, j0) into box, in
-// 16-byte chunks: a chunk starts at a multiple of CH columns (the tile origin
-// is one), so none straddles the domain edge; chunks that start inside the
-// domain may run into the row's padding (the plane pitch is a multiple of 32
-// elements), and those positions are ghosts that patch_box fills.
-template <typename T, int TX, int TY, int NT>
-__device__ __forceinline__ void issue_box(const StageIO<T> &io, int i0, int j0, T *box) {
-  using G = TileGeom<T, TX, TY>;
-  constexpr int NCH = G::BW / G::CH;  // chunks per row
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const T *src[4] = {io.ha, io.hu, io.hv, io.b};
-  for (int r = warp; r < G::BH; r += NT / 32) {
-    const int j = j0 - G::OY + r;
-    if (j < 0 || j >= io.ny) continue;
-#pragma unroll
-    for (int m = lane; m < ((NCH + 31) / 32) * 32; m += 32) {
-      const int i = i0 - G::OX + m * G::CH;
-      if (m < NCH && i >= 0 && i < io.nx) {
-        const size_t go = (size_t)j * io.pitch + i;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) cp_async16(box + f * G::FIELD + r * G::P + m * G::CH, src[f] + go);
-      }
-    }
-  }
-}
 
 // Fill every box position outside the domain (tiles whose box crosses the
 // domain edge): cells within 3 of the edge along one axis get ghost values,
@@ -1060,6 +1018,7 @@ __device__ void stage_persistent(const StageIO<T> &io, const BoxMaps &maps, cons
 // One scenario of a batch as the kernels see it (device memory).
 template <typename T>
 struct BatchSlot {
+  BoxMaps maps[3];  // tensor maps of the halo-box copies, per RK stage
   Field<T> fd;
   Phys p;
   DevScalars *sc;
@@ -1148,8 +1107,12 @@ __host__ __device__ __forceinline__ StageIO<T> io_of(const Field<T> &fd, int sta
 // enters a scenario and its accumulators are published when it leaves it;
 // the lead CTA of a scenario is the one whose chunk holds its tile 0.
 template <typename T, int TX, int TY, int NT, int S, int STAGE>
-__device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T *smem, RedSmem &red, Phys &sp) {
+__device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T *smem, RedSmem &red, Phys &sp,
+                            BatchCtl *ctl) {
   using G = TileGeom<T, TX, TY>;
+  constexpr unsigned kBoxBytes = 4u * G::BH * G::P * (unsigned)sizeof(T);
+  __shared__ unsigned long long bar[2];
+  __shared__ unsigned s_fail;
   __shared__ int s_slot[2];  // double-buffered: written one iteration ahead of the last reader
   __shared__ unsigned s_skip;
   __shared__ StageIO<T> s_io;  // planes of the current scenario (kept out of registers)
@@ -1163,18 +1126,38 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
   T tdt = T(0), rcap = T(0), alx = T(0), aly = T(0), eta_in = T(0), u_in = T(0);
   Acc<T> acc;
   int item = (int)blockIdx.x * W;
-  if (item < item_end) {
-    const int s0 = slot_of_item(slots, nslots, item);
-    const int t0 = item - slots[s0].first_item;
-    issue_box<T, TX, TY, NT>(io_of(slots[s0].fd, STAGE), (t0 % slots[s0].tiles_x) * TX, (t0 / slots[s0].tiles_x) * TY, box0);
+  // halo box of an item by tensor copies (thread 0), with the tensor maps of
+  // its scenario from the slot table
+  auto issue = [&](int itm, T *dst, unsigned long long *b) {
+    const int s0 = slot_of_item(slots, nslots, itm);
+    const int t0 = itm - slots[s0].first_item;
+    const int x = (t0 % slots[s0].tiles_x) * TX - G::OX, y = (t0 / slots[s0].tiles_x) * TY - G::OY;
+    mbar_expect_tx(b, kBoxBytes);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) tma_load_2d(dst + f * G::FIELD, &slots[s0].maps[STAGE - 1].m[f], x, y, b);
+  };
+  if (tid == 0) {
+    mbar_init(&bar[0], 1u);
+    mbar_init(&bar[1], 1u);
+    mbar_fence_init();
+    s_fail = 0u;
+    if (item < item_end) issue(item, box0, &bar[0]);
   }
-  cp_commit();
+  __syncthreads();
+  unsigned phase = 0u;  // bit b: parity of the next wait on bar[b]
   for (int it = 0; item < item_end; ++it, ++item) {
     if (tid == 0) s_slot[it & 1] = slot_of_item(slots, nslots, item);
-    // this item's box has landed for every thread's copies, and every thread
-    // is done with the previous item (whose buffer is refilled below)
-    cp_wait<0>();
+    const int bsel = it & 1;
+    if (!mbar_wait(&bar[bsel], (phase >> bsel) & 1u)) s_fail = 1u;
+    phase ^= 1u << bsel;
+    // this item's box has landed, and every thread is done with the previous
+    // item (whose buffer is refilled below); a copy that never completed ends
+    // the CTA (no other copy is in flight) and the batch reports ST_TIMEOUT
     __syncthreads();
+    if (s_fail) {
+      if (tid == 0) atomicOr(&ctl->status, ST_TIMEOUT);
+      return;
+    }
     const int s = s_slot[it & 1];
     const BatchSlot<T> &sl = slots[s];
     if (s != cur) {
@@ -1201,14 +1184,10 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
       u_in = red_v<T>(red, SV_UIN);
     }
     T *box = (it & 1) ? box1 : box0;
-    const int nitem = item + 1;
-    if (nitem < item_end) {
-      const int ns = slot_of_item(slots, nslots, nitem);
-      const int nt = nitem - slots[ns].first_item;
-      issue_box<T, TX, TY, NT>(io_of(slots[ns].fd, STAGE), (nt % slots[ns].tiles_x) * TX,
-                               (nt / slots[ns].tiles_x) * TY, (it & 1) ? box0 : box1);
+    if (tid == 0 && item + 1 < item_end) {
+      fence_proxy_async();  // order the ghost patching's generic writes into that buffer before the copies
+      issue(item + 1, (it & 1) ? box0 : box1, &bar[bsel ^ 1]);
     }
-    cp_commit();
     if (!skip) {
       const int t = item - sl.first_item;
       const int tiles_x = sl.tiles_x;
@@ -1220,7 +1199,6 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
       tile_compute<T, TX, TY, NT, S, STAGE>(s_io, sp, i0, j0, box, sL, tdt, rcap, alx, aly, acc);
     }
   }
-  cp_wait<0>();
   if (cur >= 0 && !skip) publish<T, NT, STAGE>(sp, slots[cur].sc, lead, red, dt, acc);
 }
 
