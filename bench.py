@@ -44,9 +44,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop/F
 # the same workload (96x32 tile), per cell; reported for the 4096x4096 launch
 # scaled by its cells, and only while the kernel sources are those captured.
 NCU_TRAFFIC = {"tile": 7, "cells": 2048 * 2048,
-               "bytes": {1: 67.343104e6 + 14.923264e6, 2: 117.827584e6 + 28.346112e6, 3: 117.678848e6 + 19.223808e6},
+               "bytes": {1: 67.338496e6 + 15.203072e6, 2: 117.747456e6 + 28.155648e6, 3: 117.66144e6 + 19.03872e6},
                "sources": ("swe_core.cuh", "swe_kernels.cu", "swe_launch.h"),
-               "sha256": "98dd9097a76d225e83c10823432a92f34c923912936de22f38a68939d5edfbd5"}
+               "sha256": "b60f8d7542ab0b81f1208db327312dc5725c4600ced8ab9d8784db48fb4caad7"}
 
 
 def kernel_sources_sha256() -> str:
