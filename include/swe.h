@@ -141,6 +141,16 @@ int swe_get_state(swe_handle *s, double *h, double *hu, double *hv);
  * an interface for pipelining input upload and result read-back. */
 int swe_get_state_async(swe_handle *s, double *h, double *hu, double *hv);
 
+/* Bounded-wait settings of the halo-box copies of the stage kernels: a wait
+ * gives up after timeout_s seconds (default 1, at most 60), the kernel flags
+ * a timeout, and later calls report SWE_ETIMEOUT until the state is set again
+ * (swe_set_state); the step in which it happened did not complete.
+ * extra_copy_bytes > 0 (at most 65536) is a test hook that makes every wait
+ * expect bytes that never arrive, so that the timeout path can be exercised
+ * without a fault; 0 for normal use.  Synchronises.  No counterpart in the
+ * paper. */
+int swe_set_wait(swe_handle *s, double timeout_s, int32_t extra_copy_bytes);
+
 /* Wait for the read-back started by swe_get_state_async (no-op if none);
  * returns the handle's first error, if any. */
 int swe_wait_state(swe_handle *s);

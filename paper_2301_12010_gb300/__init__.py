@@ -73,6 +73,7 @@ def _load() -> ctypes.CDLL:
         "swe_get_state": (ip, [H, dp, dp, dp]),
         "swe_get_state_async": (ip, [H, dp, dp, dp]),
         "swe_wait_state": (ip, [H]),
+        "swe_set_wait": (ip, [H, ctypes.c_double, ctypes.c_int32]),
         "swe_get_state_device": (ip, [H, vp, vp, vp]),
         "swe_mass": (ip, [H, dp, dp]),
         "swe_runup": (ip, [H, dp, dp]),
@@ -217,6 +218,11 @@ class Solver:
                 raise ValueError("get_state_async needs contiguous float64 arrays of shape (ny, nx)")
         self._async_out = out  # keep the arrays alive until wait_state
         _check(lib.swe_get_state_async(self._h, *[_dp(x) for x in out]), "swe_get_state_async")
+
+    def set_wait(self, timeout_s: float = 1.0, extra_copy_bytes: int = 0) -> None:
+        """Bounded waits of the halo-box copies (see swe_set_wait); a positive
+        extra_copy_bytes is a test hook that makes the waits run out."""
+        _check(lib.swe_set_wait(self._h, float(timeout_s), int(extra_copy_bytes)), "swe_set_wait")
 
     def wait_state(self) -> None:
         _check(lib.swe_wait_state(self._h), "swe_wait_state")

@@ -292,6 +292,8 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   ph.h_dry32 = thr32(params->h_dry);
   ph.h_wet32 = thr32(params->h_wet);
   for (int k = 0; k < 4; ++k) ph.bc[k] = params->bc[k];
+  ph.wait_cycles = kDefaultWaitCycles;
+  ph.copy_extra = 0u;
   finish_phys(ph);
 
   const size_t plane = (size_t)s->pitch * s->ny * s->elem;
@@ -560,6 +562,21 @@ int swe_set_time(swe_handle *s, double t) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(&s->sc->steps, &zero, sizeof(long long), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   return cuda_check(s, e);
+}
+
+int swe_set_wait(swe_handle *s, double timeout_s, int32_t extra_copy_bytes) {
+  if (!s || !(timeout_s > 0.0 && timeout_s <= 60.0) || extra_copy_bytes < 0 || extra_copy_bytes > 65536)
+    return SWE_EINVAL;
+  const cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_check(s, e);
+  s->phys.wait_cycles = (long long)(timeout_s * 2.2e9);  // SM clock at most ~2.1 GHz
+  s->phys.copy_extra = (unsigned)extra_copy_bytes;
+  if (s->graph) {  // the step graph holds the old values: capture again at the next step
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  if (s->sticky == SWE_ETIMEOUT) s->sticky = SWE_OK;
+  return SWE_OK;
 }
 
 int swe_destroy(swe_handle *s) {

@@ -95,6 +95,8 @@ Phys phys_of(const swe_params &q, double dx, double dy) {
   ph.h_dry32 = thr32(q.h_dry);
   ph.h_wet32 = thr32(q.h_wet);
   for (int k = 0; k < 4; ++k) ph.bc[k] = q.bc[k];
+  ph.wait_cycles = kDefaultWaitCycles;
+  ph.copy_extra = 0u;
   finish_phys(ph);
   return ph;
 }

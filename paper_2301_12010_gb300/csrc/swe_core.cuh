@@ -88,7 +88,14 @@ struct Phys {
   // cell area, and the inflow wave's constants (see inflow_eta)
   double rdx, rdy, area;
   double in_c0, in_s0, in_o1, in_o2, in_a1, in_a2, in_k1, in_k2, in_uf;
+  // bounded waits for the halo-box copies: give up after wait_cycles SM
+  // cycles; copy_extra > 0 (test hook) makes each wait expect bytes that never
+  // arrive, so that the timeout path runs
+  long long wait_cycles;
+  unsigned copy_extra, pad_;
 };
+
+constexpr long long kDefaultWaitCycles = 1ll << 31;  // ~1 s at the maximum SM clock
 
 template <typename T>
 __host__ __device__ __forceinline__ const Consts<T> &consts(const Phys &p);
@@ -365,11 +372,11 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
   return ok != 0u;
 }
 // Bounded wait for phase `parity` of bar: false if it did not complete within
-// ~2^31 SM cycles (~1 s).
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+// `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -960,7 +967,7 @@ __device__ void stage_persistent(const StageIO<T> &io, const BoxMaps &maps, cons
   T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
   auto issue = [&](int tile, T *dst, unsigned long long *b) {
     const int x = (tile % tiles_x) * TX - G::OX, y = (tile / tiles_x) * TY - G::OY;
-    mbar_expect_tx(b, kBoxBytes);
+    mbar_expect_tx(b, kBoxBytes + p.copy_extra);
 #pragma unroll
     for (int f = 0; f < 4; ++f) tma_load_2d(dst + f * G::FIELD, &maps.m[f], x, y, b);
   };
@@ -976,7 +983,7 @@ __device__ void stage_persistent(const StageIO<T> &io, const BoxMaps &maps, cons
   }
   __syncthreads();
   if (red.skip) {
-    if (tid == 0 && t < ntiles && !mbar_wait(&bar[0], 0u)) atomicOr(&sc->status, ST_TIMEOUT);
+    if (tid == 0 && t < ntiles && !mbar_wait(&bar[0], 0u, p.wait_cycles)) atomicOr(&sc->status, ST_TIMEOUT);
     __syncthreads();
     return;
   }
@@ -990,7 +997,7 @@ __device__ void stage_persistent(const StageIO<T> &io, const BoxMaps &maps, cons
   for (int it = 0; t < ntiles; ++it, t += stride) {
     const int b = it & 1;
     T *box = b ? box1 : box0;
-    if (!mbar_wait(&bar[b], (phase >> b) & 1u)) s_fail = 1u;
+    if (!mbar_wait(&bar[b], (phase >> b) & 1u, p.wait_cycles)) s_fail = 1u;
     phase ^= 1u << b;
     // one barrier: this tile's box has landed, and every thread is done with
     // the previous tile (whose buffer is refilled next)
@@ -1148,7 +1155,7 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
   for (int it = 0; item < item_end; ++it, ++item) {
     if (tid == 0) s_slot[it & 1] = slot_of_item(slots, nslots, item);
     const int bsel = it & 1;
-    if (!mbar_wait(&bar[bsel], (phase >> bsel) & 1u)) s_fail = 1u;
+    if (!mbar_wait(&bar[bsel], (phase >> bsel) & 1u, ctl->bar_cycles)) s_fail = 1u;
     phase ^= 1u << bsel;
     // this item's box has landed, and every thread is done with the previous
     // item (whose buffer is refilled below); a copy that never completed ends
