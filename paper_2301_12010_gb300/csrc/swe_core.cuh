@@ -198,8 +198,19 @@ template <> struct Num<float> {
     return r;
   }
 };
+// 1/x for positive normal x in FP64 by Newton-Raphson: the hardware seed
+// (relative error below 2^-20) and two steps r <- r + r (1 - x r), each of
+// which squares the relative error, end within an ulp or two of 1/x, at a
+// fraction of the cost of an IEEE division on this part's FP64 pipe.
+__device__ __forceinline__ double rcp_newton(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
 template <> struct Num<double> {
-  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double rcp(double x) { return rcp_newton(x); }  // x >= h_dry > 0 at every use
   static __device__ __forceinline__ double div(double a, double b) { return a / b; }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double fric(double q2, double h) { return sqrt(q2) / (h * h * cbrt(h)); }
@@ -222,7 +233,7 @@ __device__ __forceinline__ float vrcp(float a) { return Num<float>::rcp(a); }
 __device__ __forceinline__ double vadd(double a, double b) { return a + b; }
 __device__ __forceinline__ double vmul(double a, double b) { return a * b; }
 __device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ double vrcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ double vrcp(double a) { return rcp_newton(a); }  // WENO terms: positive normal
 __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -232,7 +243,7 @@ __device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
   return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
 }
-__device__ __forceinline__ double2 vrcp(double2 a) { return make_double2(1.0 / a.x, 1.0 / a.y); }
+__device__ __forceinline__ double2 vrcp(double2 a) { return make_double2(rcp_newton(a.x), rcp_newton(a.y)); }
 template <typename V> __device__ __forceinline__ V sp(double c);
 template <> __device__ __forceinline__ float sp<float>(double c) { return (float)c; }
 template <> __device__ __forceinline__ double sp<double>(double c) { return c; }
