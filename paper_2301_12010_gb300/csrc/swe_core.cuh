@@ -10,7 +10,7 @@
 // device-scope atomic max on the order-preserving bits of a double.
 //
 // One stage kernel fuses, per tile of TX x TY cells:
-//   ghost values (walls / inflow / periodic) computed while loading the halo,
+//   ghost values (walls / inflow / periodic) patched into the halo box,
 //   the dry rule, split fluxes f+- = (F +- alpha Q)/2, six WENO5
 //   reconstructions per face and direction, the bed source with the
 //   normal-momentum weights, explicit Manning friction, the RK combination,
@@ -27,9 +27,10 @@
 // combinations are written in increment form U0 + w (U' - U0), whose weights
 // sum to one exactly in any precision.
 //
-// Shared-memory plan (per CTA): the bed over the halo box, one split-flux
-// buffer reused by the x pass and then the y pass, the x-pass result L_x, and
-// the anomaly ha of the tile's own cells.
+// Shared-memory plan (per CTA, persistent over its tiles): two halo boxes of
+// (ha, hu, hv, b), double-buffered and filled by tensor copies while the
+// other tile is computed, and the x-pass result L_x; split fluxes and their
+// differences live in registers, in sliding windows along each strip.
 #pragma once
 #include <cuda.h>  // CUtensorMap (the descriptor type only; no driver calls here)
 #include <cuda_runtime.h>
@@ -799,9 +800,9 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
   using G = TileGeom<T, TX, TY>;
   static_assert(TX % S == 0 && TY % S == 0, "strip length must divide the tile");
   static_assert((TX / S) * TY == NT && (TY / S) * TX == NT, "one strip per thread in both passes");
-  // x pass: a warp covers RW rows x SW strips; with the box row pitch = 1 mod 8
-  // the lanes' window loads hit distinct banks (8 rows x 4 strips of 8 cells,
-  // or 16 rows x 2 strips of 16 cells)
+  // x pass: a warp covers RW rows x SW strips (8 rows x 4 strips of 8 cells, or
+  // 16 rows x 2 strips of 16 cells); with the box row pitch P/4 odd, the
+  // 16-byte window loads of each quarter-warp fall in distinct bank groups
   constexpr int SW = (S >= 16) ? 2 : 4, RW = 32 / SW;
   static_assert(TY % RW == 0 && (TX / S) % SW == 0 && (TY / RW) * ((TX / S) / SW) == NT / 32,
                 "x-pass warps tile the rows and strips");
