@@ -44,9 +44,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop/F
 # the same workload (96x32 tile), per cell; reported for the 4096x4096 launch
 # scaled by its cells, and only while the kernel sources are those captured.
 NCU_TRAFFIC = {"tile": 7, "cells": 2048 * 2048,
-               "bytes": {1: 67.338496e6 + 15.203072e6, 2: 117.747456e6 + 28.155648e6, 3: 117.66144e6 + 19.03872e6},
+               "bytes": {1: 67.338496e6 + 15.380736e6, 2: 117.749248e6 + 28.33536e6, 3: 117.662464e6 + 18.999808e6},
                "sources": ("swe_core.cuh", "swe_kernels.cu", "swe_launch.h"),
-               "sha256": "b60f8d7542ab0b81f1208db327312dc5725c4600ced8ab9d8784db48fb4caad7"}
+               "sha256": "f8e1cb78c420cf2e37b7fa883a25010b4f560778400467e0066c932183abbd81"}
 
 
 def kernel_sources_sha256() -> str:
