@@ -1133,16 +1133,15 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
   __shared__ unsigned long long bar[2];
   __shared__ unsigned s_fail;
   __shared__ int s_slot[2];  // double-buffered: written one iteration ahead of the last reader
-  __shared__ unsigned s_skip;
+  __shared__ unsigned s_skip, s_lead;  // the current scenario's skip and lead flags (CTA-uniform)
   __shared__ StageIO<T> s_io;  // planes of the current scenario (kept out of registers)
   T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
   const int tid = threadIdx.x;
   const int W = (total + (int)gridDim.x - 1) / (int)gridDim.x;
   const int item_end = min((int)(blockIdx.x + 1) * W, total);
+  // the current scenario's per-stage values stay in shared memory (red, s_skip,
+  // s_lead) rather than in registers across the item loop
   int cur = -1;
-  bool lead = false, skip = true;
-  double dt = 0.0;
-  T tdt = T(0), rcap = T(0), alx = T(0), aly = T(0), eta_in = T(0), u_in = T(0);
   Acc<T> acc;
   int item = (int)blockIdx.x * W;
   // halo box of an item by tensor copies (thread 0), with the tensor maps of
@@ -1180,7 +1179,7 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
     const int s = s_slot[it & 1];
     const BatchSlot<T> &sl = slots[s];
     if (s != cur) {
-      if (cur >= 0 && !skip) publish<T, NT, STAGE>(sp, slots[cur].sc, lead, red, dt, acc);
+      if (cur >= 0 && !s_skip) publish<T, NT, STAGE>(sp, slots[cur].sc, s_lead != 0u, red, red.dt, acc);
       acc = Acc<T>();
       __syncthreads();
       if (tid == 0) {
@@ -1189,36 +1188,30 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
         const bool ld = sl.first_item / W == (int)blockIdx.x;
         stage_scalars<T, STAGE>(sp, sl.sc, ld, red);
         s_skip = red.skip;
+        s_lead = ld ? 1u : 0u;
       }
       __syncthreads();
       cur = s;
-      lead = sl.first_item / W == (int)blockIdx.x;
-      skip = s_skip != 0u;
-      dt = red.dt;
-      tdt = red_v<T>(red, SV_DT);
-      rcap = red_v<T>(red, SV_RCAP);
-      alx = red_v<T>(red, SV_AX);
-      aly = red_v<T>(red, SV_AY);
-      eta_in = red_v<T>(red, SV_ETA);
-      u_in = red_v<T>(red, SV_UIN);
     }
     T *box = (it & 1) ? box1 : box0;
     if (tid == 0 && item + 1 < item_end) {
       fence_proxy_async();  // order the ghost patching's generic writes into that buffer before the copies
       issue(item + 1, (it & 1) ? box0 : box1, &bar[bsel ^ 1]);
     }
-    if (!skip) {
+    if (!s_skip) {
       const int t = item - sl.first_item;
       const int tiles_x = sl.tiles_x;
       const int i0 = (t % tiles_x) * TX, j0 = (t / tiles_x) * TY;
       if (i0 == 0 || j0 == 0 || i0 + TX + 3 > s_io.nx || j0 + TY + 3 > s_io.ny) {
-        patch_box<T, TX, TY, NT>(s_io, sp, i0, j0, box, consts<T>(sp).zref, eta_in, u_in);
+        patch_box<T, TX, TY, NT>(s_io, sp, i0, j0, box, consts<T>(sp).zref, red_v<T>(red, SV_ETA),
+                                 red_v<T>(red, SV_UIN));
         __syncthreads();
       }
-      tile_compute<T, TX, TY, NT, S, STAGE>(s_io, sp, i0, j0, box, sL, tdt, rcap, alx, aly, acc);
+      tile_compute<T, TX, TY, NT, S, STAGE>(s_io, sp, i0, j0, box, sL, red_v<T>(red, SV_DT), red_v<T>(red, SV_RCAP),
+                                            red_v<T>(red, SV_AX), red_v<T>(red, SV_AY), acc);
     }
   }
-  if (cur >= 0 && !skip) publish<T, NT, STAGE>(sp, slots[cur].sc, lead, red, dt, acc);
+  if (cur >= 0 && !s_skip) publish<T, NT, STAGE>(sp, slots[cur].sc, s_lead != 0u, red, red.dt, acc);
 }
 
 }  // namespace swe
