@@ -198,7 +198,8 @@ def fp64_bench(swe, W, torch, sc, steps: int = 10):
     parity path; GB300's FP64 rate is a small fraction of FP32)."""
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with swe.Solver(sc, precision=swe.F64, stream=stream.cuda_stream) as s:
+    best, ms_shapes = swe.autotune([(sc.nx, sc.ny)], precision=swe.F64, steps=2)
+    with swe.Solver(sc, precision=swe.F64, stream=stream.cuda_stream, tile=best) as s:
         s.step(2)
         s.sync()
         e0.record(stream)
@@ -208,7 +209,8 @@ def fp64_bench(swe, W, torch, sc, steps: int = 10):
         s.sync()
     ms = e0.elapsed_time(e1)
     return {"value": sc.cells * steps / (ms / 1e3), "unit": "cell-updates/s", "steps": steps,
-            "ms_per_step": ms / steps, "dtype": "f64"}
+            "ms_per_step": ms / steps, "dtype": "f64", "tile": best,
+            "autotune_ms": [round(x, 3) for x in ms_shapes]}
 
 
 def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: float = 20.0):
