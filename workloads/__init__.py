@@ -293,6 +293,81 @@ def standing_wave_slope(nx_sea: int = 200, nx_land: int = 40, ny: int = 4, dx: f
     return Scenario("standing_wave_slope_%dx%d" % (nx, ny), dx, dx, b, h, np.zeros_like(b), np.zeros_like(b))
 
 
+# ------------------------------------------------------------ real DEMs
+def read_esri_ascii(path: str):
+    """Read an ESRI ASCII grid (header keys ncols, nrows, xllcorner|xllcenter,
+    yllcorner|yllcenter, cellsize or dx and dy, optional NODATA_value; then
+    nrows rows of ncols values, northernmost row first).
+
+    Returns (z, dx, dy, x0, y0, nodata): z float64 (ny, nx) with row j at
+    y = y0 + (j + 0.5) dy, i.e. flipped so that y grows with the row index as
+    in every array of this module; (x0, y0) the lower-left corner; nodata a
+    bool mask of the cells that held the NODATA value."""
+    with open(path) as f:
+        tokens = f.read().split()
+    head, k = {}, 0
+    while k + 1 < len(tokens) and not _is_number(tokens[k]):
+        head[tokens[k].lower()] = float(tokens[k + 1])
+        k += 2
+    nx, ny = int(head["ncols"]), int(head["nrows"])
+    if "cellsize" in head:
+        dx = dy = head["cellsize"]
+    else:
+        dx, dy = head["dx"], head["dy"]
+    if "xllcorner" in head:
+        x0 = head["xllcorner"]
+    else:
+        x0 = head["xllcenter"] - 0.5 * dx
+    if "yllcorner" in head:
+        y0 = head["yllcorner"]
+    else:
+        y0 = head["yllcenter"] - 0.5 * dy
+    vals = np.array([float(t) for t in tokens[k:k + nx * ny]], dtype=np.float64)
+    if vals.size != nx * ny or not (dx > 0 and dy > 0):
+        raise ValueError("%s: expected %d x %d values and positive cell sizes" % (path, ny, nx))
+    z = vals.reshape(ny, nx)[::-1].copy()
+    nodata = np.zeros(z.shape, dtype=bool)
+    if "nodata_value" in head:
+        nodata = z == head["nodata_value"]
+    return z, float(dx), float(dy), float(x0), float(y0), nodata
+
+
+def _is_number(t: str) -> bool:
+    try:
+        float(t)
+        return True
+    except ValueError:
+        return False
+
+
+def dem_scenario(path: str, sea_level: float = 0.0, nodata_elevation: Optional[float] = None,
+                 crop: Optional[Tuple[int, int, int, int]] = None, stride: int = 1, **settings) -> Scenario:
+    """Still water at sea_level over the bed of an ESRI ASCII grid of
+    elevations (m, positive up).  NODATA cells take nodata_elevation (default:
+    the highest valid elevation, i.e. dry land behind walls).  crop =
+    (j0, j1, i0, i1) selects rows j0..j1-1 and columns i0..i1-1 (after the
+    flip to y-up order) and stride keeps every stride-th cell.  Further keyword
+    arguments set Scenario fields (boundary types, inflow wave, friction ...);
+    z_ref defaults to sea_level."""
+    z, dx, dy, _, _, nodata = read_esri_ascii(path)
+    if nodata.any():
+        if nodata.all():
+            raise ValueError("%s holds no valid elevation" % path)
+        fill = float(z[~nodata].max()) if nodata_elevation is None else float(nodata_elevation)
+        z = np.where(nodata, fill, z)
+    if crop is not None:
+        j0, j1, i0, i1 = crop
+        z = z[j0:j1, i0:i1]
+    if stride > 1:
+        z = z[::stride, ::stride]
+        dx, dy = dx * stride, dy * stride
+    b = np.ascontiguousarray(z)
+    h, hu, hv = _still(b, sea_level)
+    settings.setdefault("z_ref", sea_level)
+    name = settings.pop("name", "dem_%dx%d" % (b.shape[1], b.shape[0]))
+    return Scenario(name, dx, dy, b, h, hu, hv, **settings)
+
+
 def lake_at_rest(nx: int = 32, ny: int = 32, dx: float = 1.0, eta0: float = 0.5, depth: float = 10.0,
                  rms: float = 3.0, seed: int = 11, islands: bool = False) -> Scenario:
     """Still water over a seeded rough bed (slope -2 spectrum).  With islands,
