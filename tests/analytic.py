@@ -83,6 +83,21 @@ def standing_wave_on_slope(r: np.ndarray, t: float, amp: float, L: float, slope:
     return eta, hu, w
 
 
+def golden(name: str) -> dict:
+    """Values of a cited text fixture under tests/golden/ ("key value" lines;
+    '#' starts a comment)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    out = {}
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split()
+                out[k] = float(v)
+    return out
+
+
 def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
     """Relative L2 error of Eq. (9)."""
     return float(np.sqrt(np.sum((a - ref) ** 2) / np.sum(ref ** 2)))

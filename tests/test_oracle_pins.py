@@ -179,12 +179,14 @@ def test_x_and_y_sweeps_agree_under_transposition():
 
 # ------------------------------------------------------ closed-form solutions
 def test_stoker_dam_break():
+    vt = A.golden("verification_times.txt")  # comparison times printed in Section 2.1
+    times = (vt["dam_break_t1"], vt["dam_break_t2"])
     errs = {}
     for nx in (200, 400):
         sc = W.dam_break(nx=nx)
         sim = oracle.Simulation(sc)
         x = (np.arange(nx) + 0.5) * sc.dx
-        for t in (2.5, 9.0):
+        for t in times:
             sim.run_until(t)
             ha, x3 = A.stoker(x, t, 50.0, 2.0, 1.0)
             keep = np.abs(x - x3) > 5 * sc.dx  # away from the shock front
@@ -194,7 +196,7 @@ def test_stoker_dam_break():
             x_num = x[np.where(hc > hm)[0].max()]
             assert abs(x_num - x3) <= 2 * sc.dx
             assert np.all(sim.h == sim.h[0])  # stays one-dimensional
-    for t in (2.5, 9.0):
+    for t in times:
         assert errs[(400, t)] <= 2e-2
         assert errs[(400, t)] < errs[(200, t)]
 
@@ -204,7 +206,8 @@ def test_thacker_planar_bowl():
     sim = oracle.Simulation(sc)
     x = (np.arange(sc.nx) + 0.5) * sc.dx
     om = math.sqrt(2 * 9.81 * 1.0) / 100.0
-    for t in (3.5, 12.5, 2 * math.pi / om):
+    vt = A.golden("verification_times.txt")  # comparison times printed in Section 2.2
+    for t in (vt["bowl_t1"], vt["bowl_t2"], 2 * math.pi / om):
         sim.run_until(t)
         ha, ua = A.thacker(x, t, 400.0, 100.0, 1.0)
         assert A.rel_l2(sim.h[0], ha) <= 1e-2
@@ -216,12 +219,13 @@ def test_thacker_planar_bowl():
 
 @pytest.mark.parametrize("frac", [1.0, 0.8])
 def test_manning_normal_flow(frac):
-    qn = A.manning_normal_discharge(0.5, 1.0 / 20.0, 0.033)
-    sc = W.manning_slope(q=frac * qn)
+    case = A.golden("manning_slope.txt")  # the paper's printed case (Section 2.3)
+    qn = A.manning_normal_discharge(case["h"], case["slope"], case["n"])
+    sc = W.manning_slope(slope=case["slope"], depth=case["h"], n=case["n"], q=frac * qn)
     sim = oracle.Simulation(sc)
-    sim.run_until(200.0)
+    sim.run_until(case["t_compare"])
     assert np.abs(sim.hu - qn).max() / qn <= 1e-10
-    assert np.abs(sim.h - 0.5).max() <= 1e-10
+    assert np.abs(sim.h - case["h"]).max() <= 1e-10
 
 
 def test_inflow_wave_peak_and_quiet_start():
@@ -231,6 +235,22 @@ def test_inflow_wave_peak_and_quiet_start():
     assert e.max() == pytest.approx(sc.inflow_amp, rel=1e-6)
     assert abs(e[0]) < 1e-6 * sc.inflow_amp and abs(e[-1]) < 1e-6 * sc.inflow_amp
     assert ts[np.argmax(e)] < ts[np.argmin(e)]  # the crest leads, the trough follows
+
+
+def test_inflow_wave_uses_the_printed_constants():
+    # Eq. (20) with the constants printed in the paper (tests/golden/carrier_nwave.txt),
+    # read in time as s = 1.3 lambda - c0 t with a1 = amp/2 (reading R9)
+    c = A.golden("carrier_nwave.txt")
+    sc = W.coastal_dem(n=32, dx=100.0)
+    c0 = math.sqrt(sc.g * sc.inflow_depth)
+    lam = sc.inflow_period * c0
+    a1 = 0.5 * sc.inflow_amp
+    a2 = c["a2_over_a1"] * a1
+    for t in np.linspace(0.0, 2.0 * sc.inflow_period, 41):
+        s = 1.3 * lam - c0 * t
+        want = 2.0 * (a1 * math.exp(-c["k1_lambda2"] / lam ** 2 * (s - c["x1_over_lambda"] * lam) ** 2)
+                      - a2 * math.exp(-c["k2_lambda2"] / lam ** 2 * (s - c["x2_over_lambda"] * lam) ** 2))
+        assert oracle.inflow_eta(sc, t) == pytest.approx(want, rel=1e-12, abs=1e-12 * sc.inflow_amp)
 
 
 def test_solitary_wave_runup_follows_synolakis_law():
