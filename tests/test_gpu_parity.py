@@ -206,6 +206,20 @@ def test_fp32_coastal_dem_full_size_two_steps():
 
 
 # ------------------------------------------------------------- edge cases
+def test_fp32_large_grid_rows_agree_and_match_the_oracle():
+    # 16384 x 4096 cells (67 M): a y-uniform solitary wave on the 1:20 beach.
+    # Far tile indices and tensor-copy coordinates: every row must stay equal
+    # to row 0 bit for bit, and row 0 must match the FP64 oracle on 16384 x 4.
+    big = W.planar_beach(nx=16384, ny=4096, manning_n=0.0)
+    small = W.planar_beach(nx=16384, ny=4, manning_n=0.0)
+    steps = 20
+    ref = run_oracle(small, steps)
+    h, hu, hv, d, _ = run_gpu(big, steps, swe.F32)
+    assert np.all(h == h[0]) and np.all(hu == hu[0]) and not hv.any()
+    assert rel_l2(eta_tilde(h[0], big.b[0]), eta_tilde(ref.h[0], small.b[0])) <= 1e-4
+    assert rel_l2(hu[0], ref.hu[0]) <= 1e-4
+
+
 def test_dry_still_domain_reports_einval():
     sc = W.lake_at_rest(16, 16, eta0=-100.0, depth=10.0, rms=1.0)
     assert sc.h.max() == 0.0
