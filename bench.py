@@ -218,14 +218,23 @@ def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: fl
     coast and hills as the ensemble, 150 GB budget, continuous batching."""
     from paper_2301_12010_gb300.serve import Server
     stream = torch.cuda.current_stream().cuda_stream
+    # the batch tile shape, tuned on grids of the request mix
+    mix = W.serving_requests(rate=rates[0], count=count, horizon=horizon)
+    tile, _ = swe.autotune([(r.scenario.nx, r.scenario.ny) for r in mix[:8]], precision=swe.F32, batch=True, steps=3)
     out = {}
-    for rate in rates:
-        reqs = W.serving_requests(rate=rate, count=count, horizon=horizon)
-        with Server(reqs[0].scenario, nslots=64, budget_bytes=150 << 30, k_steps=50, stream=stream) as srv:
-            rep = srv.serve(reqs)
-        out["%g_req_per_s" % rate] = rep.summary()
+    for policy in ("srpt", "all"):
+        res = {}
+        for rate in rates:
+            reqs = W.serving_requests(rate=rate, count=count, horizon=horizon)
+            with Server(reqs[0].scenario, nslots=64, budget_bytes=150 << 30, k_steps=50, stream=stream,
+                        policy=policy, tile=tile) as srv:
+                rep = srv.serve(reqs)
+            res["%g_req_per_s" % rate] = rep.summary()
+        out[policy] = res
     return {"sample": "%d requests per rate, %g s simulated horizon (config horizon 600 s)" % (count, horizon),
-            "rates": out}
+            "policies": {"srpt": "shortest remaining work first, enough requests per launch to fill the GPU",
+                         "all": "every live request advances each launch"},
+            "batch_tile": tile, "rates": out["srpt"], "rates_all": out["all"]}
 
 
 def run_reference(args):

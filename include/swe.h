@@ -258,6 +258,17 @@ int swe_batch_diagnostics(swe_batch *b, int32_t slot, swe_diag *d);
 int swe_batch_retire(swe_batch *b, int32_t slot, double *h, double *hu, double *hv, double *mass,
                      double *runup_max);
 
+/* Restrict the following runs to the n live slots listed (the others keep
+ * their state and resume when selected again); slots == NULL or n <= 0
+ * selects every live slot, as after swe_batch_create.  Admitted slots are
+ * selected.  EINVAL if a listed slot is not live.  Call between runs.  No
+ * counterpart in the paper: a scheduling hook for the serving loop. */
+int swe_batch_select(swe_batch *b, const int32_t *slots, int32_t n);
+
+/* Simulated time of every slot (t[0 .. nslots-1]; NaN for free slots) in one
+ * read-back.  Synchronises. */
+int swe_batch_times(swe_batch *b, double *t);
+
 /* Device bytes in use by live slots and the budget. */
 int swe_batch_memory(swe_batch *b, size_t *used, size_t *budget);
 

@@ -93,6 +93,8 @@ def _load() -> ctypes.CDLL:
                                  ctypes.c_double, ctypes.POINTER(ctypes.c_int32)]),
         "swe_batch_run": (ip, [H, ctypes.c_int32, ctypes.c_double]),
         "swe_batch_poll": (ip, [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+        "swe_batch_select": (ip, [H, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+        "swe_batch_times": (ip, [H, dp]),
         "swe_batch_get_state": (ip, [H, ctypes.c_int32, dp, dp, dp]),
         "swe_batch_diagnostics": (ip, [H, ctypes.c_int32, ctypes.POINTER(Diag)]),
         "swe_batch_retire": (ip, [H, ctypes.c_int32, dp, dp, dp, dp, dp]),
@@ -340,6 +342,20 @@ class Batch:
                                    *[_dp(a) for a in arrs], float(te), ctypes.byref(slot)), "swe_batch_admit")
         self.shapes[slot.value] = (sc.ny, sc.nx)
         return slot.value
+
+    def select(self, slots=None) -> None:
+        """Advance only these live slots in the following runs (None: all)."""
+        if slots is None:
+            _check(lib.swe_batch_select(self._b, None, 0), "swe_batch_select")
+            return
+        arr = (ctypes.c_int32 * len(slots))(*[int(x) for x in slots])
+        _check(lib.swe_batch_select(self._b, arr, len(slots)), "swe_batch_select")
+
+    def times(self) -> np.ndarray:
+        """Simulated time of every slot (NaN for free slots)."""
+        t = np.empty(self.nslots, dtype=np.float64)
+        _check(lib.swe_batch_times(self._b, _dp(t)), "swe_batch_times")
+        return t
 
     def try_admit(self, sc, t_end: Optional[float] = None) -> Optional[int]:
         try:

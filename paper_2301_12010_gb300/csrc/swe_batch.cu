@@ -20,6 +20,7 @@ namespace {
 
 struct Slot {
   bool live = false;
+  bool selected = true;  // advanced by the runs (swe_batch_select)
   int nx = 0, ny = 0, pitch = 0;
   double dx = 0, dy = 0, t_end = 0;
   size_t bytes = 0;
@@ -101,14 +102,15 @@ Phys phys_of(const swe_params &q, double dx, double dy) {
   return ph;
 }
 
-// Rebuild the work list (live slots in index order) and the control block.
+// Rebuild the work list (live, selected slots in index order) and the
+// control block.
 int upload_table(swe_batch *b) {
   std::vector<BatchSlot<float>> tab;
   int total = 0;
   const TileShape *ts = shape(b->tile);
   for (int s = 0; s < b->nslots; ++s) {
     const Slot &sl = b->slots[s];
-    if (!sl.live) continue;
+    if (!sl.live || !sl.selected) continue;
     BatchSlot<float> e{};
     for (int k = 0; k < 3; ++k) e.maps[k] = sl.maps[k];
     e.fd = sl.fd;
@@ -326,6 +328,29 @@ int swe_batch_poll(swe_batch *b, int32_t *done_slots, int32_t *ndone) {
   }
   *ndone = n;
   return swe_batch_status(b);
+}
+
+int swe_batch_select(swe_batch *b, const int32_t *slots, int32_t n) {
+  if (!b) return SWE_EINVAL;
+  if (slots && n > 0) {
+    for (int32_t k = 0; k < n; ++k)
+      if (!valid_slot(b, slots[k])) return SWE_EINVAL;
+    for (auto &sl : b->slots) sl.selected = false;
+    for (int32_t k = 0; k < n; ++k) b->slots[slots[k]].selected = true;
+  } else {
+    for (auto &sl : b->slots) sl.selected = true;
+  }
+  return upload_table(b);
+}
+
+int swe_batch_times(swe_batch *b, double *t) {
+  if (!b || !t) return SWE_EINVAL;
+  std::vector<DevScalars> h(b->nslots);
+  cudaError_t e = cudaMemcpyAsync(h.data(), b->d_sc, sizeof(DevScalars) * b->nslots, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, e);
+  for (int s = 0; s < b->nslots; ++s) t[s] = b->slots[s].live ? h[s].t : NAN;
+  return SWE_OK;
 }
 
 int swe_batch_diagnostics(swe_batch *b, int32_t slot, swe_diag *d) {

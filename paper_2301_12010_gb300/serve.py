@@ -8,6 +8,16 @@ live scenario (swe_batch_run), and retires the scenarios that reached their
 horizon (swe_batch_retire: result copied to the host).  Work of requests that
 arrive while others run overlaps on the device.  Latency is arrival ->
 result on the host.
+
+Scheduling policy between macro-launches:
+  * "all": every live request advances K steps per launch (processor
+    sharing by steps: a small request takes as many launches as its steps,
+    each as long as the largest live request makes it);
+  * "srpt": shortest remaining work first.  The live requests are ordered by
+    remaining work (cells x remaining simulated time / cell size: the step is
+    proportional to the cell size at similar wave speeds) and the launch
+    advances the smallest ones, adding requests until their cells fill the
+    GPU (fill_cells); the others wait in their slots (swe_batch_select).
 """
 from __future__ import annotations
 
@@ -61,11 +71,33 @@ class Server:
     """A serving loop with nslots slots and an HBM budget (bytes)."""
 
     def __init__(self, template, nslots: int = 64, budget_bytes: int = 150 << 30, k_steps: int = 50,
-                 cfl: float = 0.4, stream: Optional[int] = None, tile: int = 0, keep_state: bool = False):
+                 cfl: float = 0.4, stream: Optional[int] = None, tile: int = 0, keep_state: bool = False,
+                 policy: str = "all", fill_cells: int = 152 * 4 * 3072):
+        if policy not in ("all", "srpt"):
+            raise ValueError("policy must be 'all' or 'srpt'")
         self.batch = Batch(nslots, budget_bytes, template, stream=stream, tile=tile)
         self.k = int(k_steps)
         self.cfl = float(cfl)
         self.keep_state = keep_state
+        self.policy = policy
+        self.fill_cells = int(fill_cells)
+
+    def _choose(self, requests, live) -> List[int]:
+        """Slots to advance in the next launch under the SRPT policy."""
+        t = self.batch.times()
+        work = []
+        for slot, (k, _) in live.items():
+            sc = requests[k].scenario
+            rem = max(float(sc.t_end) - float(t[slot]), 0.0)
+            work.append((sc.cells * rem / min(sc.dx, sc.dy), slot, sc.cells))
+        work.sort()
+        chosen, cells = [], 0
+        for _, slot, c in work:
+            chosen.append(slot)
+            cells += c
+            if cells >= self.fill_cells:
+                break
+        return sorted(chosen)
 
     def close(self):
         self.batch.close()
@@ -88,6 +120,7 @@ class Server:
         max_live = 0
         cell_updates = 0.0
         steps_seen: Dict[int, int] = {}
+        selected: Optional[List[int]] = None
         t0 = time.perf_counter()
         while incoming or waiting or live:
             now = time.perf_counter() - t0
@@ -112,9 +145,15 @@ class Server:
                     if wait > 0:
                         time.sleep(min(wait, 0.05))
                 continue
+            if self.policy == "srpt":
+                chosen = self._choose(requests, live) if len(live) > 1 else sorted(live)
+                if chosen != selected:
+                    self.batch.select(chosen)
+                    selected = chosen
             self.batch.run(self.k, self.cfl)
             launches += 1
             for slot in self.batch.poll():
+                selected = None  # the work list changes with the retirement
                 k, adm = live.pop(slot)
                 d = self.batch.diagnostics(slot, check=False)
                 st, m, r = self.batch.retire(slot, want_state=self.keep_state)

@@ -43,10 +43,12 @@ def alone_in_batch(sc, k):
     return st, d
 
 
-def test_served_results_equal_alone_and_overlap():
+@pytest.mark.parametrize("policy", ["all", "srpt"])
+def test_served_results_equal_alone_and_overlap(policy):
     reqs = small_requests(7, rate=200.0)
+    # srpt with a fill of one small grid: launches advance only part of the live requests
     with Server(reqs[0].scenario, nslots=3, budget_bytes=1 << 30, k_steps=7, stream=stream(),
-                keep_state=True) as srv:
+                keep_state=True, policy=policy, fill_cells=100 * 100) as srv:
         rep = srv.serve(reqs)
     assert len(rep.results) == len(reqs)
     assert rep.max_live >= 2  # work of different requests overlapped on the device
@@ -75,3 +77,28 @@ def test_admission_respects_the_hbm_budget():
     assert len(rep.results) == len(reqs)
     assert rep.max_live == 2 and used == 0 and cap == budget
     assert budget_for(reqs) > budget
+
+
+def test_paused_slot_keeps_its_state_and_resumes_bit_for_bit():
+    reqs = small_requests(2, rate=200.0)
+    a, b = reqs[0].scenario.copy(t_end=1e6), reqs[1].scenario.copy(t_end=1e6)
+    with swe.Batch(2, 1 << 30, a, stream=stream()) as bt:
+        sa, sb = bt.admit(a), bt.admit(b)
+        before = bt.get_state(sb)
+        bt.select([sa])
+        bt.run(6)
+        t = bt.times()
+        assert t[sa] > 0.0 and t[sb] == 0.0
+        for x, y in zip(before, bt.get_state(sb)):
+            assert np.array_equal(x, y)
+        bt.select(None)
+        bt.run(9)
+        got = bt.get_state(sb)
+        steps_b = bt.diagnostics(sb)["steps"]
+    with swe.Batch(2, 1 << 30, b, stream=stream()) as ref:
+        s = ref.admit(b)
+        ref.run(9)
+        want = ref.get_state(s)
+        assert ref.diagnostics(s)["steps"] == steps_b == 9
+    for x, y in zip(got, want):
+        assert np.array_equal(x, y)
