@@ -44,9 +44,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop/F
 # the same workload (96x32 tile), per cell; reported for the 4096x4096 launch
 # scaled by its cells, and only while the kernel sources are those captured.
 NCU_TRAFFIC = {"tile": 7, "cells": 2048 * 2048,
-               "bytes": {1: 67.338496e6 + 15.380736e6, 2: 117.749248e6 + 28.33536e6, 3: 117.662464e6 + 18.999808e6},
+               "bytes": {1: 67.337728e6 + 15.208448e6, 2: 117.754112e6 + 28.455424e6, 3: 117.664512e6 + 19.184896e6},
                "sources": ("swe_core.cuh", "swe_kernels.cu", "swe_launch.h"),
-               "sha256": "f8e1cb78c420cf2e37b7fa883a25010b4f560778400467e0066c932183abbd81"}
+               "sha256": "89ed2a303e564cc1ae5a3c0e2025bd180db489354f6303d04d195822b8d62d5e"}
 
 
 def kernel_sources_sha256() -> str:

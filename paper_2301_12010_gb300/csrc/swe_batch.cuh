@@ -1,0 +1,191 @@
+// swe_batch.cuh -- device code of the batch path: the slot table, the
+// bounded grid barrier and one RK stage over the (scenario, tile) work list
+// of a batch, built on the tile arithmetic of swe_core.cuh.  Kept apart from
+// the single-scenario driver so that the two evolve separately.
+#pragma once
+#include "swe_core.cuh"
+
+namespace swe {
+
+// ------------------------------------------------------------ batch driver
+// One scenario of a batch as the kernels see it (device memory).
+template <typename T>
+struct BatchSlot {
+  BoxMaps maps[3];  // tensor maps of the halo-box copies, per RK stage
+  Field<T> fd;
+  Phys p;
+  DevScalars *sc;
+  int tiles_x, ntiles, first_item, pad;
+};
+
+// Batch control block (device memory).
+struct BatchCtl {
+  int nslots;               // entries of the slot table
+  int total_items;          // tiles over all entries (the work list)
+  unsigned bar_count;       // grid barrier: arrivals in the current round
+  unsigned bar_gen;         // grid barrier: completed rounds
+  unsigned status;          // ST_TIMEOUT when a barrier wait ran out
+  unsigned bar_extra;       // test hook: arrivals expected beyond the grid (0)
+  long long bar_cycles;     // bounded wait: SM clock cycles before giving up
+};
+
+// Grid-wide barrier of a cooperative launch with a bounded wait.  Returns
+// false (and sets ST_TIMEOUT) if the other CTAs did not arrive in time; the
+// caller then leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(BatchCtl *ctl, unsigned nblocks) {
+  __shared__ unsigned ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1u;
+    volatile unsigned *gen = &ctl->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned expect = nblocks + ctl->bar_extra;
+    if (atomicAdd(&ctl->bar_count, 1u) == expect - 1u) {
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > ctl->bar_cycles || *(volatile unsigned *)&ctl->status) {
+          atomicOr(&ctl->status, ST_TIMEOUT);
+          ok = 0u;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();  // acquire: later loads see what other CTAs wrote before the barrier
+  }
+  __syncthreads();
+  return ok != 0u;
+}
+
+template <typename T>
+__device__ __forceinline__ int slot_of_item(const BatchSlot<T> *slots, int n, int item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (slots[mid].first_item <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ StageIO<T> io_of(const Field<T> &fd, int stage) {
+  StageIO<T> io;
+  const int in = stage - 1, out = stage % 3;
+  io.b = fd.b;
+  io.ha = fd.h[in];
+  io.hu = fd.hu[in];
+  io.hv = fd.hv[in];
+  io.ha0 = fd.h[0];
+  io.hu0 = fd.hu[0];
+  io.hv0 = fd.hv[0];
+  io.oha = fd.h[out];
+  io.ohu = fd.hu[out];
+  io.ohv = fd.hv[out];
+  io.nx = fd.nx;
+  io.ny = fd.ny;
+  io.pitch = fd.pitch;
+  return io;
+}
+
+// One RK stage over the work list of a batch (scenario after scenario, tiles
+// in order): CTA b handles the contiguous chunk of items [b W, (b+1) W),
+// W = ceil(total / gridDim.x), so that it meets one or two scenarios rather
+// than a new one at every item.  Per-scenario scalars are taken when the CTA
+// enters a scenario and its accumulators are published when it leaves it;
+// the lead CTA of a scenario is the one whose chunk holds its tile 0.
+template <typename T, int TX, int TY, int NT, int S, int STAGE>
+__device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T *smem, RedSmem &red, Phys &sp,
+                            BatchCtl *ctl) {
+  using G = TileGeom<T, TX, TY>;
+  constexpr unsigned kBoxBytes = 4u * G::BH * G::P * (unsigned)sizeof(T);
+  __shared__ unsigned long long bar[2];
+  __shared__ unsigned s_fail;
+  __shared__ int s_slot[2];  // double-buffered: written one iteration ahead of the last reader
+  __shared__ unsigned s_skip, s_lead;  // the current scenario's skip and lead flags (CTA-uniform)
+  __shared__ StageIO<T> s_io;  // planes of the current scenario (kept out of registers)
+  T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
+  const int tid = threadIdx.x;
+  const int W = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int item_end = min((int)(blockIdx.x + 1) * W, total);
+  // the current scenario's per-stage values stay in shared memory (red, s_skip,
+  // s_lead) rather than in registers across the item loop
+  int cur = -1;
+  Acc<T> acc;
+  int item = (int)blockIdx.x * W;
+  // halo box of an item by tensor copies (thread 0), with the tensor maps of
+  // its scenario from the slot table
+  auto issue = [&](int itm, T *dst, unsigned long long *b) {
+    const int s0 = slot_of_item(slots, nslots, itm);
+    const int t0 = itm - slots[s0].first_item;
+    const int x = (t0 % slots[s0].tiles_x) * TX - G::OX, y = (t0 / slots[s0].tiles_x) * TY - G::OY;
+    mbar_expect_tx(b, kBoxBytes);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) tma_load_2d(dst + f * G::FIELD, &slots[s0].maps[STAGE - 1].m[f], x, y, b);
+  };
+  if (tid == 0) {
+    mbar_init(&bar[0], 1u);
+    mbar_init(&bar[1], 1u);
+    mbar_fence_init();
+    s_fail = 0u;
+    if (item < item_end) issue(item, box0, &bar[0]);
+  }
+  __syncthreads();
+  unsigned phase = 0u;  // bit b: parity of the next wait on bar[b]
+  for (int it = 0; item < item_end; ++it, ++item) {
+    if (tid == 0) s_slot[it & 1] = slot_of_item(slots, nslots, item);
+    const int bsel = it & 1;
+    if (!mbar_wait(&bar[bsel], (phase >> bsel) & 1u, ctl->bar_cycles)) s_fail = 1u;
+    phase ^= 1u << bsel;
+    // this item's box has landed, and every thread is done with the previous
+    // item (whose buffer is refilled below); a copy that never completed ends
+    // the CTA (no other copy is in flight) and the batch reports ST_TIMEOUT
+    __syncthreads();
+    if (s_fail) {
+      if (tid == 0) atomicOr(&ctl->status, ST_TIMEOUT);
+      return;
+    }
+    const int s = s_slot[it & 1];
+    const BatchSlot<T> &sl = slots[s];
+    if (s != cur) {
+      if (cur >= 0 && !s_skip) publish<T, NT, STAGE>(sp, slots[cur].sc, s_lead != 0u, red, red.dt, acc);
+      acc = Acc<T>();
+      __syncthreads();
+      if (tid == 0) {
+        sp = sl.p;
+        s_io = io_of(sl.fd, STAGE);
+        const bool ld = sl.first_item / W == (int)blockIdx.x;
+        stage_scalars<T, STAGE>(sp, sl.sc, ld, red);
+        s_skip = red.skip;
+        s_lead = ld ? 1u : 0u;
+      }
+      __syncthreads();
+      cur = s;
+    }
+    T *box = (it & 1) ? box1 : box0;
+    if (tid == 0 && item + 1 < item_end) {
+      fence_proxy_async();  // order the ghost patching's generic writes into that buffer before the copies
+      issue(item + 1, (it & 1) ? box0 : box1, &bar[bsel ^ 1]);
+    }
+    if (!s_skip) {
+      const int t = item - sl.first_item;
+      const int tiles_x = sl.tiles_x;
+      const int i0 = (t % tiles_x) * TX, j0 = (t / tiles_x) * TY;
+      if (i0 == 0 || j0 == 0 || i0 + TX + 3 > s_io.nx || j0 + TY + 3 > s_io.ny) {
+        patch_box<T, TX, TY, NT>(s_io, sp, i0, j0, box, consts<T>(sp).zref, red_v<T>(red, SV_ETA),
+                                 red_v<T>(red, SV_UIN));
+        __syncthreads();
+      }
+      tile_compute<T, TX, TY, NT, S, STAGE>(s_io, sp, i0, j0, box, sL, red_v<T>(red, SV_DT), red_v<T>(red, SV_RCAP),
+                                            red_v<T>(red, SV_AX), red_v<T>(red, SV_AY), acc);
+    }
+  }
+  if (cur >= 0 && !s_skip) publish<T, NT, STAGE>(sp, slots[cur].sc, s_lead != 0u, red, red.dt, acc);
+}
+
+}  // namespace swe

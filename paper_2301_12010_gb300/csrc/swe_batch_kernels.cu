@@ -5,7 +5,7 @@
 #ifndef SWE_SHAPE
 #define SWE_SHAPE 1
 #endif
-#include "swe_core.cuh"
+#include "swe_batch.cuh"
 #include "swe_launch.h"
 
 namespace swe {

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cuda_runtime.h>
 
+#include "swe_batch.cuh"
 #include "swe_core.cuh"
 
 namespace swe {
