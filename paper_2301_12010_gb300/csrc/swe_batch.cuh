@@ -99,6 +99,10 @@ __host__ __device__ __forceinline__ StageIO<T> io_of(const Field<T> &fd, int sta
 // than a new one at every item.  Per-scenario scalars are taken when the CTA
 // enters a scenario and its accumulators are published when it leaves it;
 // the lead CTA of a scenario is the one whose chunk holds its tile 0.
+// Thread 0 walks the chunk with a cursor (slot, tile column, tile row) that
+// advances without searching the slot table, and hands each item's slot and
+// tile origin to the CTA through shared memory when it issues the item's
+// halo-box copies: no thread reads the slot table on the way to a tile.
 template <typename T, int TX, int TY, int NT, int S, int STAGE>
 __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T *smem, RedSmem &red, Phys &sp,
                             BatchCtl *ctl) {
@@ -106,7 +110,7 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
   constexpr unsigned kBoxBytes = 4u * G::BH * G::P * (unsigned)sizeof(T);
   __shared__ unsigned long long bar[2];
   __shared__ unsigned s_fail;
-  __shared__ int s_slot[2];  // double-buffered: written one iteration ahead of the last reader
+  __shared__ int4 s_item[2];  // (slot, i0, j0) of the item in each box buffer, written when its copies are issued
   __shared__ unsigned s_skip, s_lead;  // the current scenario's skip and lead flags (CTA-uniform)
   __shared__ StageIO<T> s_io;  // planes of the current scenario (kept out of registers)
   T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
@@ -118,45 +122,71 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
   int cur = -1;
   Acc<T> acc;
   int item = (int)blockIdx.x * W;
-  // halo box of an item by tensor copies (thread 0), with the tensor maps of
-  // its scenario from the slot table
-  auto issue = [&](int itm, T *dst, unsigned long long *b) {
-    const int s0 = slot_of_item(slots, nslots, itm);
-    const int t0 = itm - slots[s0].first_item;
-    const int x = (t0 % slots[s0].tiles_x) * TX - G::OX, y = (t0 / slots[s0].tiles_x) * TY - G::OY;
+  // thread 0's cursor, kept in shared memory (not in every thread's
+  // registers): slot of the next item to issue, its tile column and row,
+  // that slot's tile columns, and the tiles left in that slot
+  struct Cursor {
+    int slot, i, j, tx, left;
+  };
+  __shared__ Cursor q;
+  // halo box of the cursor's item by tensor copies into buffer bb, with the
+  // tensor maps of its scenario; then the cursor moves to the next item
+  auto issue = [&](int bb, unsigned long long *b) {
+    Cursor c = q;
+    const int i0 = c.i * TX, j0 = c.j * TY;
+    s_item[bb] = make_int4(c.slot, i0, j0, 0);
     mbar_expect_tx(b, kBoxBytes);
+    const CUtensorMap *m = slots[c.slot].maps[STAGE - 1].m;
+    T *dst = bb ? box1 : box0;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) tma_load_2d(dst + f * G::FIELD, &slots[s0].maps[STAGE - 1].m[f], x, y, b);
+    for (int f = 0; f < 4; ++f) tma_load_2d(dst + f * G::FIELD, &m[f], i0 - G::OX, j0 - G::OY, b);
+    if (--c.left == 0) {  // next scenario
+      if (++c.slot < nslots) {
+        c.tx = slots[c.slot].tiles_x;
+        c.left = slots[c.slot].ntiles;
+      }
+      c.i = c.j = 0;
+    } else if (++c.i == c.tx) {
+      c.i = 0;
+      ++c.j;
+    }
+    q = c;
   };
   if (tid == 0) {
     mbar_init(&bar[0], 1u);
     mbar_init(&bar[1], 1u);
     mbar_fence_init();
     s_fail = 0u;
-    if (item < item_end) issue(item, box0, &bar[0]);
+    if (item < item_end) {
+      const int s0 = slot_of_item(slots, nslots, item);
+      const int t = item - slots[s0].first_item, tx = slots[s0].tiles_x;
+      q = Cursor{s0, t % tx, t / tx, tx, slots[s0].ntiles - t};
+      issue(0, &bar[0]);
+    }
   }
   __syncthreads();
   unsigned phase = 0u;  // bit b: parity of the next wait on bar[b]
   for (int it = 0; item < item_end; ++it, ++item) {
-    if (tid == 0) s_slot[it & 1] = slot_of_item(slots, nslots, item);
     const int bsel = it & 1;
     if (!mbar_wait(&bar[bsel], (phase >> bsel) & 1u, ctl->bar_cycles)) s_fail = 1u;
     phase ^= 1u << bsel;
     // this item's box has landed, and every thread is done with the previous
-    // item (whose buffer is refilled below); a copy that never completed ends
-    // the CTA (no other copy is in flight) and the batch reports ST_TIMEOUT
+    // item (whose buffer and s_item entry are reused below); a copy that never
+    // completed ends the CTA (no other copy is in flight) and the batch
+    // reports ST_TIMEOUT
     __syncthreads();
     if (s_fail) {
       if (tid == 0) atomicOr(&ctl->status, ST_TIMEOUT);
       return;
     }
-    const int s = s_slot[it & 1];
-    const BatchSlot<T> &sl = slots[s];
+    const int4 inf = s_item[bsel];
+    const int s = inf.x;
     if (s != cur) {
       if (cur >= 0 && !s_skip) publish<T, NT, STAGE>(sp, slots[cur].sc, s_lead != 0u, red, red.dt, acc);
       acc = Acc<T>();
       __syncthreads();
       if (tid == 0) {
+        const BatchSlot<T> &sl = slots[s];
         sp = sl.p;
         s_io = io_of(sl.fd, STAGE);
         const bool ld = sl.first_item / W == (int)blockIdx.x;
@@ -167,15 +197,13 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
       __syncthreads();
       cur = s;
     }
-    T *box = (it & 1) ? box1 : box0;
+    T *box = bsel ? box1 : box0;
     if (tid == 0 && item + 1 < item_end) {
       fence_proxy_async();  // order the ghost patching's generic writes into that buffer before the copies
-      issue(item + 1, (it & 1) ? box0 : box1, &bar[bsel ^ 1]);
+      issue(bsel ^ 1, &bar[bsel ^ 1]);
     }
     if (!s_skip) {
-      const int t = item - sl.first_item;
-      const int tiles_x = sl.tiles_x;
-      const int i0 = (t % tiles_x) * TX, j0 = (t / tiles_x) * TY;
+      const int i0 = inf.y, j0 = inf.z;
       if (i0 == 0 || j0 == 0 || i0 + TX + 3 > s_io.nx || j0 + TY + 3 > s_io.ny) {
         patch_box<T, TX, TY, NT>(s_io, sp, i0, j0, box, consts<T>(sp).zref, red_v<T>(red, SV_ETA),
                                  red_v<T>(red, SV_UIN));
