@@ -61,6 +61,26 @@ def test_batch_result_is_the_same_alone_and_in_the_mix(tile):
         assert d_alone["t"] == d_mix["t"] and d_mix["steps"] == 35
 
 
+def test_work_chunks_that_cross_many_scenarios():
+    # sixty one-tile grids among four larger ones, more tiles than CTAs: each
+    # CTA's chunk of the work list crosses several scenarios (the per-CTA
+    # cursor moves from slot to slot inside a launch); every result is still
+    # bit for bit that of the scenario run alone
+    rng = np.random.default_rng(31)
+    scs = []
+    for k in range(64):
+        n = 300 + 64 * (k // 16) if k % 16 == 0 else int(rng.integers(3, 30))
+        scs.append(W.gaussian_hump(n=n, sigma_cells=max(1.0, n / 8.0)).copy(t_end=1e6))
+    tiles = sum(-(-sc.nx // 96) * -(-sc.ny // 32) for sc in scs)
+    assert tiles > 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    mix = batch_run(scs, 12, tile=7, runs=(12,))
+    for sc, (st_mix, d_mix) in zip(scs, mix):
+        (st_alone, d_alone), = batch_run([sc], 12, tile=7, runs=(12,))
+        for a, m in zip(st_alone, st_mix):
+            assert np.array_equal(a, m)
+        assert d_alone["t"] == d_mix["t"] and d_mix["steps"] == 12
+
+
 def test_batch_matches_single_scenario_solver():
     # same arithmetic in a separately compiled kernel: FP32 rounding level
     ens = small_ensemble()
