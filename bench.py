@@ -213,7 +213,8 @@ def fp64_bench(swe, W, torch, sc, steps: int = 10):
             "autotune_ms": [round(x, 3) for x in ms_shapes]}
 
 
-def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: float = 20.0):
+def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: float = 20.0,
+                  policies=("srpt", "all")):
     """C5 (bounded sample): Poisson requests, N log-uniform in [256, 2048],
     coast and hills as the ensemble, 150 GB budget, continuous batching."""
     from paper_2301_12010_gb300.serve import Server
@@ -222,7 +223,7 @@ def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: fl
     mix = W.serving_requests(rate=rates[0], count=count, horizon=horizon)
     tile, _ = swe.autotune([(r.scenario.nx, r.scenario.ny) for r in mix[:8]], precision=swe.F32, batch=True, steps=3)
     out = {}
-    for policy in ("srpt", "all"):
+    for policy in policies:
         res = {}
         for rate in rates:
             reqs = W.serving_requests(rate=rate, count=count, horizon=horizon)
@@ -234,7 +235,7 @@ def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: fl
     return {"sample": "%d requests per rate, %g s simulated horizon (config horizon 600 s)" % (count, horizon),
             "policies": {"srpt": "shortest remaining work first, enough requests per launch to fill the GPU",
                          "all": "every live request advances each launch"},
-            "batch_tile": tile, "rates": out["srpt"], "rates_all": out["all"]}
+            "batch_tile": tile, "rates": out.get("srpt"), "rates_all": out.get("all")}
 
 
 def run_reference(args):
@@ -298,9 +299,27 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--serving-sweep", default=None, metavar="RATES",
+                    help="only the serving measurement, at these comma-separated request rates (req/s); "
+                         "prints one JSON object, not a bench line")
+    ap.add_argument("--serving-count", type=int, default=200, help="requests per rate of --serving-sweep")
+    ap.add_argument("--serving-horizon", type=float, default=20.0, help="simulated seconds per request")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving_sweep:
+        import torch
+
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2301_12010_gb300 as swe
+        import workloads as W
+        torch.cuda.set_device(0)
+        rates = tuple(float(r) for r in args.serving_sweep.split(","))
+        res = serving_bench(swe, W, torch, rates=rates, count=args.serving_count, horizon=args.serving_horizon,
+                            policies=("srpt",))
+        print(json.dumps({"serving_sweep": res}))
+        return 0
 
     import numpy as np
     import torch
