@@ -61,6 +61,7 @@ struct swe_batch {
   double timeout_s = 1.0;
   unsigned extra = 0;
   double cfl = 0.4;  // CFL number in the slots' device scalars
+  bool strided = false;  // work order of the current table (the launch must match it)
   int sticky = SWE_OK;
 };
 
@@ -130,6 +131,12 @@ int upload_table(swe_batch *b) {
   c.status = 0;
   c.bar_extra = b->extra;
   c.bar_cycles = (long long)(b->timeout_s * 2.2e9);  // SM clock at most ~2.1 GHz
+  // strided work order when every scenario spans at least two tiles per CTA:
+  // neighbouring tiles in flight together, few scenario switches per CTA
+  bool big = !tab.empty();
+  for (const auto &e : tab) big = big && e.ntiles >= 2 * b->grid;
+  c.strided = big ? 1 : 0;
+  b->strided = big;
   cudaError_t e = cudaSuccess;
   if (!tab.empty())
     e = cudaMemcpyAsync(b->d_table, tab.data(), sizeof(BatchSlot<float>) * tab.size(), cudaMemcpyHostToDevice,
@@ -281,21 +288,22 @@ int swe_batch_run(swe_batch *b, int32_t k_steps, double cfl) {
     if (e != cudaSuccess) return bfail(b, e);
     b->cfl = cfl;
   }
-  auto it = b->graphs.find(k_steps);
+  const int key = 2 * k_steps + (b->strided ? 1 : 0);  // one graph per step count and work order
+  auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ex = nullptr;
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       cudaError_t le = cudaMemsetAsync(&b->d_ctl->bar_count, 0, sizeof(unsigned), b->cap);
-      if (le == cudaSuccess) le = batch_launch(b->tile, b->d_table, b->d_ctl, k_steps, b->grid, b->cap);
+      if (le == cudaSuccess) le = batch_launch(b->tile, b->d_table, b->d_ctl, k_steps, b->grid, b->strided, b->cap);
       e = cudaStreamEndCapture(b->cap, &g);
       if (le != cudaSuccess) e = le;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) return bfail(b, e);
-    it = b->graphs.emplace(k_steps, ex).first;
+    it = b->graphs.emplace(key, ex).first;
   }
   e = cudaGraphLaunch(it->second, b->stream);
   return bfail(b, e);

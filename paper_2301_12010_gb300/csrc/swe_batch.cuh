@@ -27,6 +27,8 @@ struct BatchCtl {
   unsigned status;          // ST_TIMEOUT when a barrier wait ran out
   unsigned bar_extra;       // test hook: arrivals expected beyond the grid (0)
   long long bar_cycles;     // bounded wait: SM clock cycles before giving up
+  int strided;              // work order of the table (set by the host; the launch matches it)
+  int pad_;
 };
 
 // Grid-wide barrier of a cooperative launch with a bounded wait.  Returns
@@ -94,16 +96,20 @@ __host__ __device__ __forceinline__ StageIO<T> io_of(const Field<T> &fd, int sta
 }
 
 // One RK stage over the work list of a batch (scenario after scenario, tiles
-// in order): CTA b handles the contiguous chunk of items [b W, (b+1) W),
-// W = ceil(total / gridDim.x), so that it meets one or two scenarios rather
-// than a new one at every item.  Per-scenario scalars are taken when the CTA
-// enters a scenario and its accumulators are published when it leaves it;
-// the lead CTA of a scenario is the one whose chunk holds its tile 0.
-// Thread 0 walks the chunk with a cursor (slot, tile column, tile row) that
-// advances without searching the slot table, and hands each item's slot and
-// tile origin to the CTA through shared memory when it issues the item's
-// halo-box copies: no thread reads the slot table on the way to a tile.
-template <typename T, int TX, int TY, int NT, int S, int STAGE>
+// in row order).  Contiguous order: CTA b handles the chunk of items
+// [b W, (b+1) W), W = ceil(total / G), so that it meets one or two scenarios
+// rather than a new one at every item.  Strided order (STRIDED; the host's
+// choice when every scenario has at least 2 G tiles): CTA b takes items
+// b, b + G, ..., so that the G CTAs work on neighbouring tiles at any time
+// (halo rows shared through L2) while each still stays in one scenario for
+// runs of items.  Per-scenario scalars are taken when the CTA enters a
+// scenario and its accumulators are published when it leaves it; the lead
+// CTA of a scenario is the one that owns its tile 0.  Thread 0 walks the
+// CTA's items with a cursor that advances without searching the slot table,
+// and hands each item's slot and tile origin to the CTA through shared
+// memory when it issues the item's halo-box copies: no thread reads the slot
+// table on the way to a tile.
+template <typename T, int TX, int TY, int NT, int S, int STAGE, bool STRIDED>
 __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T *smem, RedSmem &red, Phys &sp,
                             BatchCtl *ctl) {
   using G = TileGeom<T, TX, TY>;
@@ -116,34 +122,44 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
   T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
   const int tid = threadIdx.x;
   const int W = (total + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int item_end = min((int)(blockIdx.x + 1) * W, total);
+  const int item_end = STRIDED ? total : min((int)(blockIdx.x + 1) * W, total);
+  const int step = STRIDED ? (int)gridDim.x : 1;
   // the current scenario's per-stage values stay in shared memory (red, s_skip,
   // s_lead) rather than in registers across the item loop
   int cur = -1;
   Acc<T> acc;
-  int item = (int)blockIdx.x * W;
+  int item = STRIDED ? (int)blockIdx.x : (int)blockIdx.x * W;
   // thread 0's cursor, kept in shared memory (not in every thread's
-  // registers): slot of the next item to issue, its tile column and row,
-  // that slot's tile columns, and the tiles left in that slot
+  // registers): slot of the next item to issue and that slot's tile columns
+  // tx; contiguous order: the item's tile column i and row j and the tiles
+  // n left in the slot; strided order: the item's tile index i in the slot
+  // and the slot's tiles n
   struct Cursor {
-    int slot, i, j, tx, left;
+    int slot, i, j, tx, n;
   };
   __shared__ Cursor q;
   // halo box of the cursor's item by tensor copies into buffer bb, with the
   // tensor maps of its scenario; then the cursor moves to the next item
   auto issue = [&](int bb, unsigned long long *b) {
     Cursor c = q;
-    const int i0 = c.i * TX, j0 = c.j * TY;
+    const int i0 = (STRIDED ? c.i % c.tx : c.i) * TX, j0 = (STRIDED ? c.i / c.tx : c.j) * TY;
     s_item[bb] = make_int4(c.slot, i0, j0, 0);
     mbar_expect_tx(b, kBoxBytes);
     const CUtensorMap *m = slots[c.slot].maps[STAGE - 1].m;
     T *dst = bb ? box1 : box0;
 #pragma unroll
     for (int f = 0; f < 4; ++f) tma_load_2d(dst + f * G::FIELD, &m[f], i0 - G::OX, j0 - G::OY, b);
-    if (--c.left == 0) {  // next scenario
+    if constexpr (STRIDED) {
+      c.i += step;
+      while (c.i >= c.n && ++c.slot < nslots) {  // into the next scenario(s)
+        c.i -= c.n;
+        c.n = slots[c.slot].ntiles;
+        c.tx = slots[c.slot].tiles_x;
+      }
+    } else if (--c.n == 0) {  // next scenario
       if (++c.slot < nslots) {
         c.tx = slots[c.slot].tiles_x;
-        c.left = slots[c.slot].ntiles;
+        c.n = slots[c.slot].ntiles;
       }
       c.i = c.j = 0;
     } else if (++c.i == c.tx) {
@@ -160,13 +176,13 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
     if (item < item_end) {
       const int s0 = slot_of_item(slots, nslots, item);
       const int t = item - slots[s0].first_item, tx = slots[s0].tiles_x;
-      q = Cursor{s0, t % tx, t / tx, tx, slots[s0].ntiles - t};
+      q = STRIDED ? Cursor{s0, t, 0, tx, slots[s0].ntiles} : Cursor{s0, t % tx, t / tx, tx, slots[s0].ntiles - t};
       issue(0, &bar[0]);
     }
   }
   __syncthreads();
   unsigned phase = 0u;  // bit b: parity of the next wait on bar[b]
-  for (int it = 0; item < item_end; ++it, ++item) {
+  for (int it = 0; item < item_end; ++it, item += step) {
     const int bsel = it & 1;
     if (!mbar_wait(&bar[bsel], (phase >> bsel) & 1u, ctl->bar_cycles)) s_fail = 1u;
     phase ^= 1u << bsel;
@@ -189,7 +205,7 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
         const BatchSlot<T> &sl = slots[s];
         sp = sl.p;
         s_io = io_of(sl.fd, STAGE);
-        const bool ld = sl.first_item / W == (int)blockIdx.x;
+        const bool ld = (STRIDED ? sl.first_item % (int)gridDim.x : sl.first_item / W) == (int)blockIdx.x;
         stage_scalars<T, STAGE>(sp, sl.sc, ld, red);
         s_skip = red.skip;
         s_lead = ld ? 1u : 0u;
@@ -198,7 +214,7 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
       cur = s;
     }
     T *box = bsel ? box1 : box0;
-    if (tid == 0 && item + 1 < item_end) {
+    if (tid == 0 && item + step < item_end) {
       fence_proxy_async();  // order the ghost patching's generic writes into that buffer before the copies
       issue(bsel ^ 1, &bar[bsel ^ 1]);
     }

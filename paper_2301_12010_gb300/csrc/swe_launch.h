@@ -49,7 +49,8 @@ SWE_SHAPES(SWE_PICK)
   template <typename T>                                                                          \
   cudaError_t make_maps_##K(const Field<T> &fd, BoxMaps out[3]);                                 \
   cudaError_t batch_resident_##K(int *per_sm);                                                   \
-  cudaError_t batch_launch_##K(const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, cudaStream_t st);
+  cudaError_t batch_launch_##K(const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, bool strided, \
+                               cudaStream_t st);
 SWE_SHAPES(SWE_DECL)
 #undef SWE_DECL
 
@@ -99,6 +100,7 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_
 EncodeTiledFn tensor_map_encoder();
 // CTAs per SM of the batch kernel for a shape, and one cooperative launch.
 cudaError_t batch_resident(int shape, int *per_sm);
-cudaError_t batch_launch(int shape, const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, cudaStream_t st);
+cudaError_t batch_launch(int shape, const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, bool strided,
+                         cudaStream_t st);
 
 }  // namespace swe

@@ -81,6 +81,24 @@ def test_work_chunks_that_cross_many_scenarios():
         assert d_alone["t"] == d_mix["t"] and d_mix["steps"] == 12
 
 
+def test_work_order_does_not_change_results():
+    # two grids of more than 2 x 152 tiles each run in strided order (CTA b
+    # takes items b, b + G, ...); with a small grid in the table the order is
+    # contiguous chunks.  Each scenario's result is bit for bit the same.
+    big = [W.gaussian_hump(n=n, sigma_cells=n / 12.0).copy(t_end=1e6) for n in (1024, 1056)]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert all(-(-sc.nx // 96) * -(-sc.ny // 32) >= 2 * sms for sc in big)
+    strided = batch_run(big, 6, tile=7, runs=(6,))
+    mixed = batch_run(big + small_ensemble(2, seed=3), 6, tile=7, runs=(6,))
+    for (st_s, d_s), (st_m, d_m) in zip(strided, mixed[:2]):
+        for a, m in zip(st_s, st_m):
+            assert np.array_equal(a, m)
+        assert d_s["t"] == d_m["t"]
+    (h, hu, hv), d = strided[0]
+    (rh, rhu, rhv), dr = alone(big[0], 6)
+    assert np.sqrt(((h - rh) ** 2).sum() / (rh ** 2).sum()) <= 1e-6
+
+
 def test_batch_matches_single_scenario_solver():
     # same arithmetic in a separately compiled kernel: FP32 rounding level
     ens = small_ensemble()
