@@ -246,6 +246,35 @@ def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: fl
             "batch_tile": tile, "rates": out.get("srpt"), "rates_all": out.get("all")}
 
 
+def profile_batch_case() -> int:
+    """One step of each batch work order and of the single-scenario path
+    (96x32 tiles), for ncu; no timing."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2301_12010_gb300 as swe
+    import workloads as W
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream().cuda_stream
+    ens = W.mitigation_ensemble()
+    with swe.Batch(len(ens), 150 << 30, ens[0], stream=st, tile=7) as b:
+        for sc in ens:
+            b.admit(sc.copy(t_end=1e9))
+        b.run(1)
+        torch.cuda.synchronize()
+    dem = W.coastal_dem(n=2048).copy(bc=(W.WALL,) * 4, inflow_amp=0.0)
+    with swe.Batch(2, 64 << 30, dem, stream=st, tile=7) as b:
+        b.admit(dem.copy(t_end=1e9))
+        b.run(1)
+        torch.cuda.synchronize()
+    with swe.Solver(dem, precision=swe.F32, stream=st, tile=7) as s:
+        s.step(1)
+        s.sync()
+    print("profile-batch: ok")
+    return 0
+
+
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle on the host cores, each step one
     RK3 step of a 512 x 512 window (the inflow edge) of the coastal DEM."""
@@ -312,9 +341,15 @@ def main():
                          "prints one JSON object, not a bench line")
     ap.add_argument("--serving-count", type=int, default=200, help="requests per rate of --serving-sweep")
     ap.add_argument("--serving-horizon", type=float, default=20.0, help="simulated seconds per request")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="only one RK3 step of the batch kernel on the 64-scenario ensemble (contiguous order) "
+                         "and on one walled 2048x2048 DEM (strided order), then the same DEM by the "
+                         "single-scenario kernels: a short case for a profiler")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_batch:
+        return profile_batch_case()
     if args.serving_sweep:
         import torch
 
