@@ -197,12 +197,20 @@ def test_fp32_lake_at_rest_with_islands():
     assert np.abs(hu).max() <= 1e-4 and np.abs(hv).max() <= 1e-4
 
 
-def test_fp32_coastal_dem_full_size_two_steps():
+def test_coastal_dem_full_size_against_the_oracle():
+    # the bench's workload at its full size (4096^2: N-wave inflow, rough
+    # shelf, land and shoreline, Manning friction), 10 steps, in the tile
+    # shape the bench times (96x32) for FP32 and the autotuner's FP64 shape
     sc = W.coastal_dem()
-    ref = run_oracle(sc, 2)
-    h, hu, hv, d, _ = run_gpu(sc, 2, swe.F32)
+    steps = 10
+    ref = run_oracle(sc, steps)
+    h64, hu64, _, d64, _ = run_gpu(sc, steps, swe.F64, tile=2)
+    assert np.abs(h64 - ref.h).max() <= 1e-10  # eta = h + b, b shared
+    assert d64["t"] == pytest.approx(ref.t, rel=1e-12)
+    h, hu, hv, d, _ = run_gpu(sc, steps, swe.F32, tile=7)
     e = rel_l2(eta_tilde(h, sc.b), eta_tilde(ref.h, sc.b))
     assert e <= 1e-4, e
+    assert rel_l2(hu, ref.hu) <= 1e-4
 
 
 # ------------------------------------------------------------- edge cases
