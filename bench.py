@@ -275,6 +275,82 @@ def profile_batch_case() -> int:
     return 0
 
 
+def config_table() -> int:
+    """Per configuration: GPU FP32 and FP64 cell-updates/s beside the FP64
+    oracle's at one thread and at all host cores (bounded samples where a
+    full run would take minutes, marked as such).  Prints one JSON object."""
+    import platform
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_2301_12010_gb300 as swe
+    import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    all_threads = oracle.num_threads()
+
+    def gpu_rate(sc, steps, precision, tile=0):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with swe.Solver(sc, precision=precision, stream=stream.cuda_stream, tile=tile) as s:
+            s.step(3)
+            s.sync()
+            e0.record(stream)
+            s.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s.sync()
+        return sc.cells * steps / (e0.elapsed_time(e1) / 1e3)
+
+    def oracle_rate(scs, steps, threads):
+        oracle.set_threads(threads)
+        sims = [oracle.Simulation(sc) for sc in scs]
+        t0 = time.perf_counter()
+        for sim in sims:
+            sim.step(steps)
+        dt = time.perf_counter() - t0
+        oracle.set_threads(all_threads)
+        return sum(sc.cells for sc in scs) * steps / dt
+
+    rows = {}
+    sc = W.gaussian_hump()
+    rows["C1 hump 128x128, 200 steps"] = {
+        "gpu_f32": gpu_rate(sc, 200, swe.F32), "gpu_f64": gpu_rate(sc, 200, swe.F64),
+        "oracle_1_thread": oracle_rate([sc], 200, 1), "oracle_all_threads": oracle_rate([sc], 200, all_threads),
+        "oracle_sample": "full run"}
+    sc = W.planar_beach()
+    rows["C2 planar beach 2048x64, 5000 steps"] = {
+        "gpu_f32": gpu_rate(sc, 5000, swe.F32), "gpu_f64": gpu_rate(sc, 5000, swe.F64),
+        "oracle_1_thread": oracle_rate([sc], 200, 1), "oracle_all_threads": oracle_rate([sc], 1000, all_threads),
+        "oracle_sample": "200 steps at 1 thread, 1000 at all threads (rate extrapolated to the 5000-step run)"}
+    sc = W.coastal_dem()
+    rows["C3 coastal DEM 4096x4096"] = {
+        "gpu_f32": gpu_rate(sc, 100, swe.F32, tile=7), "gpu_f64": gpu_rate(sc, 10, swe.F64, tile=2),
+        "oracle_1_thread": oracle_rate([sc], 1, 1), "oracle_all_threads": oracle_rate([sc], 2, all_threads),
+        "oracle_sample": "1 step at 1 thread, 2 at all threads of the 1.6e5-step hour (rate extrapolated)"}
+    ens = W.mitigation_ensemble()
+    e = ensemble_bench(swe, W, torch)
+    rows["C4 ensemble of 64 coasts (29.7 M cells)"] = {
+        "gpu_f32": e["batched_cell_updates_per_s"], "gpu_f64": None,
+        "gpu_note": "one batched persistent launch (the batch path is FP32)",
+        "oracle_1_thread": oracle_rate(ens[:4], 1, 1), "oracle_all_threads": oracle_rate(ens[:4], 2, all_threads),
+        "oracle_sample": "4 of the 64 scenarios, 1 step at 1 thread and 2 at all threads (rate extrapolated)"}
+    cpu = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    cpu = "%s (%s)" % (platform.machine(), line.split(":", 1)[1].strip())
+                    break
+    except OSError:
+        pass
+    print(json.dumps({"config_table": rows, "unit": "cell-updates/s", "host": cpu, "nproc": os.cpu_count(),
+                      "oracle_threads": all_threads, "gpu": torch.cuda.get_device_name(0)}))
+    return 0
+
+
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle on the host cores, each step one
     RK3 step of a 512 x 512 window (the inflow edge) of the coastal DEM."""
@@ -345,11 +421,16 @@ def main():
                     help="only one RK3 step of the batch kernel on the 64-scenario ensemble (contiguous order) "
                          "and on one walled 2048x2048 DEM (strided order), then the same DEM by the "
                          "single-scenario kernels: a short case for a profiler")
+    ap.add_argument("--config-table", action="store_true",
+                    help="only the per-configuration table: GPU FP32/FP64 beside the oracle at 1 thread and all "
+                         "cores; prints one JSON object")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_batch:
         return profile_batch_case()
+    if args.config_table:
+        return config_table()
     if args.serving_sweep:
         import torch
 

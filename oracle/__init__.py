@@ -88,6 +88,8 @@ def _load():
         lib.or_inflow_eta.argtypes = [ctypes.POINTER(Params), ctypes.c_double]
         lib.or_inflow_eta.restype = ctypes.c_double
         lib.or_num_threads.restype = ctypes.c_int
+        lib.or_set_threads.argtypes = [ctypes.c_int]
+        lib.or_set_threads.restype = None
         _lib = lib
     return _lib
 
@@ -195,6 +197,12 @@ def inflow_eta(sc, t: float) -> float:
 
 def num_threads() -> int:
     return int(_load().or_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the grid-line loops (timing at 1 thread and at all cores);
+    does not change the arithmetic."""
+    _load().or_set_threads(int(n))
 
 
 def run(sc, steps: Optional[int] = None) -> Simulation:

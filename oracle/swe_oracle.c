@@ -762,6 +762,14 @@ double or_weno5(const double *v, double eps, double *w) {
   return r;
 }
 
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
