@@ -151,6 +151,15 @@ int swe_get_state_async(swe_handle *s, double *h, double *hu, double *hv);
  * paper. */
 int swe_set_wait(swe_handle *s, double timeout_s, int32_t extra_copy_bytes);
 
+/* Test hook for the error paths: the n-th device allocation the library
+ * makes from now on (handle and batch creation, a batch admission, the first
+ * asynchronous read-back's buffers) fails as if the device were out of
+ * memory, and the call that made it returns SWE_ENOMEM with nothing leaked
+ * and its handle or batch still usable; later allocations succeed again.
+ * n = 0 disarms; n < 0 gives SWE_EINVAL.  Process-wide, thread-safe.  No
+ * counterpart in the paper. */
+int swe_debug_fail_alloc(int32_t n);
+
 /* Wait for the read-back started by swe_get_state_async (no-op if none);
  * returns the handle's first error, if any. */
 int swe_wait_state(swe_handle *s);
@@ -236,7 +245,9 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
 /* Admit a scenario: host FP64 bathymetry and state [ny][nx] (copied), run until
  * simulated time t_end (> 0).  Allocates the slot's device memory stream-ordered
  * (cudaMallocAsync).  Returns the slot index in *slot; SWE_EBUDGET if the
- * budget would be exceeded, SWE_EFULL if no slot is free.  Call between runs. */
+ * budget would be exceeded, SWE_EFULL if no slot is free, SWE_ENOMEM if the
+ * device has no room now (the batch is unchanged and usable in all three
+ * cases).  Call between runs. */
 int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, const double *bathymetry,
                     const double *h, const double *hu, const double *hv, double t_end, int32_t *slot);
 

@@ -105,6 +105,7 @@ def _load() -> ctypes.CDLL:
         "swe_autotune": (ip, [ctypes.POINTER(Grid), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                               ctypes.POINTER(ctypes.c_int32), dp]),
         "swe_autotune_lookup": (ip, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
+        "swe_debug_fail_alloc": (ip, [ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -127,6 +128,12 @@ def _check(rc: int, what: str = "") -> None:
 
 def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def debug_fail_alloc(n: int) -> None:
+    """Test hook (swe_debug_fail_alloc): the n-th device allocation of the
+    library from now on fails with ENOMEM; 0 disarms."""
+    _check(lib.swe_debug_fail_alloc(int(n)), "swe_debug_fail_alloc")
 
 
 def tile_shapes() -> Sequence[Tuple[int, int, int]]:
@@ -358,10 +365,12 @@ class Batch:
         return t
 
     def try_admit(self, sc, t_end: Optional[float] = None) -> Optional[int]:
+        """admit, or None when the scenario does not fit now (budget, slots or
+        device memory: the batch is unchanged and a later try may succeed)."""
         try:
             return self.admit(sc, t_end)
         except SweError as e:
-            if e.code in (EBUDGET, EFULL):
+            if e.code in (EBUDGET, EFULL, ENOMEM):
                 return None
             raise
 

@@ -5,15 +5,28 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "../../include/swe.h"
 #include "swe_launch.h"
+#include "swe_trace.h"
+#include "swe_alloc.h"
 
 using namespace swe;
 
 
 namespace swe {
+namespace {
+std::atomic<int> g_alloc_countdown{0};  // > 0: allocations left before the one that fails
+}
+bool alloc_should_fail() {
+  int n = g_alloc_countdown.load();
+  while (n > 0 && !g_alloc_countdown.compare_exchange_weak(n, n - 1)) {
+  }
+  return n == 1;
+}
+
 float thr32(double thr) {
   // smallest float f with (double)f >= thr: comparing h < f in FP32 is the
   // same predicate as (double)h < thr
@@ -236,6 +249,12 @@ const char *swe_strerror(int code) {
   return "unknown status";
 }
 
+int swe_debug_fail_alloc(int32_t n) {
+  if (n < 0) return SWE_EINVAL;
+  g_alloc_countdown.store(n);
+  return SWE_OK;
+}
+
 int swe_tile_count(void) { return num_shapes(); }
 
 int swe_tile_shape(int k, int32_t *tx, int32_t *ty, int32_t *threads) {
@@ -249,6 +268,7 @@ int swe_tile_shape(int k, int32_t *tx, int32_t *ty, int32_t *threads) {
 
 int swe_create(const swe_grid *grid, double dx, double dy, const double *bathymetry, const swe_params *params,
                swe_handle **out) {
+  const TraceRange trace("swe_create");
   if (out) *out = nullptr;
   if (!grid || !out || !bathymetry || !valid_params(params)) return SWE_EINVAL;
   if (grid->nx < 3 || grid->ny < 3 || !(dx > 0.0) || !(dy > 0.0)) return SWE_EINVAL;
@@ -302,7 +322,7 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   const size_t scal = (sizeof(DevScalars) + 255) & ~(size_t)255;
   const size_t part = sizeof(double) * (kMassBlocks + 1);
   const size_t total = plane_al * 10 + stag + scal + part;
-  cudaError_t e = cudaMalloc(&s->mem, total);
+  cudaError_t e = dev_malloc(&s->mem, total);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     delete s;
@@ -355,6 +375,7 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
 }
 
 int swe_set_state(swe_handle *s, const double *h, const double *hu, const double *hv) {
+  const TraceRange trace("swe_set_state");
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
   int rc = upload_field(s, h, s->h[0], true);
   if (rc == SWE_OK) rc = upload_field(s, hu, s->hu[0], false);
@@ -363,6 +384,7 @@ int swe_set_state(swe_handle *s, const double *h, const double *hu, const double
   return rc;
 }
 int swe_set_state_device(swe_handle *s, const void *h, const void *hu, const void *hv) {
+  const TraceRange trace("swe_set_state_device");
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
   int rc = import_device(s, h, s->h[0], true);
   if (rc == SWE_OK) rc = import_device(s, hu, s->hu[0], false);
@@ -372,6 +394,7 @@ int swe_set_state_device(swe_handle *s, const void *h, const void *hu, const voi
 }
 
 int swe_step(swe_handle *s, int32_t n, double cfl) {
+  const TraceRange trace("swe_step");
   if (!s || n < 0) return SWE_EINVAL;
   if (s->prm.fixed_dt <= 0.0 && !(cfl > 0.0 && std::isfinite(cfl))) return SWE_EINVAL;
   if (n == 0) return SWE_OK;
@@ -402,6 +425,7 @@ int swe_step(swe_handle *s, int32_t n, double cfl) {
 }
 
 int swe_sync(swe_handle *s) {
+  const TraceRange trace("swe_sync");
   if (!s) return SWE_EINVAL;
   if (s->sticky != SWE_OK) return s->sticky;
   return device_status(s);
@@ -417,6 +441,7 @@ int swe_status(swe_handle *s) {
 }
 
 int swe_get_state(swe_handle *s, double *h, double *hu, double *hv) {
+  const TraceRange trace("swe_get_state");
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
   int rc = download_field(s, s->h[0], h, true);
   if (rc == SWE_OK) rc = download_field(s, s->hu[0], hu, false);
@@ -427,6 +452,7 @@ int swe_get_state(swe_handle *s, double *h, double *hu, double *hv) {
 }
 
 int swe_get_state_async(swe_handle *s, double *h, double *hu, double *hv) {
+  const TraceRange trace("swe_get_state_async");
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
   if (s->sticky != SWE_OK) return s->sticky;
   const size_t bytes = sizeof(double) * (size_t)s->nx * s->ny;
@@ -436,13 +462,33 @@ int swe_get_state_async(swe_handle *s, double *h, double *hu, double *hv) {
   const size_t plane = s->elem * (size_t)s->pitch * s->ny;
   cudaError_t e = cudaSuccess;
   const size_t nb = sizeof(double) * (size_t)s->nx * s->ny;
-  if (!s->snap) {
-    e = cudaMalloc(&s->snap, 3 * plane);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&s->xstage, 3 * nb);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->xfer, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_snap, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_check(s, e);
+  if (!s->snap) {  // first asynchronous read-back: its buffers, stream and events
+    void *snap = nullptr;
+    double *xs = nullptr;
+    cudaStream_t xf = nullptr;
+    cudaEvent_t ev1 = nullptr, ev2 = nullptr;
+    e = dev_malloc(&snap, 3 * plane);
+    if (e == cudaSuccess) e = dev_malloc((void **)&xs, 3 * nb);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&xf, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev2, cudaEventDisableTiming);
+    if (e != cudaSuccess) {  // nothing half-made stays behind
+      if (ev2) cudaEventDestroy(ev2);
+      if (ev1) cudaEventDestroy(ev1);
+      if (xf) cudaStreamDestroy(xf);
+      if (xs) cudaFree(xs);
+      if (snap) cudaFree(snap);
+      if (e == cudaErrorMemoryAllocation) {  // no room now: the handle is unchanged and usable
+        (void)cudaGetLastError();
+        return SWE_ENOMEM;
+      }
+      return cuda_check(s, e);
+    }
+    s->snap = snap;
+    s->xstage = xs;
+    s->xfer = xf;
+    s->ev_snap = ev1;
+    s->ev_done = ev2;
   }
   // the previous read-back must be done with the snapshot
   if (s->pending) e = cudaStreamWaitEvent(s->stream, s->ev_done, 0);
@@ -475,6 +521,7 @@ int swe_get_state_async(swe_handle *s, double *h, double *hu, double *hv) {
 }
 
 int swe_wait_state(swe_handle *s) {
+  const TraceRange trace("swe_wait_state");
   if (!s) return SWE_EINVAL;
   if (s->pending) {
     const cudaError_t e = cudaEventSynchronize(s->ev_done);
@@ -485,6 +532,7 @@ int swe_wait_state(swe_handle *s) {
 }
 
 int swe_get_state_device(swe_handle *s, void *h, void *hu, void *hv) {
+  const TraceRange trace("swe_get_state_device");
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
   int rc = export_device(s, s->h[0], h, true);
   if (rc == SWE_OK) rc = export_device(s, s->hu[0], hu, false);
@@ -495,6 +543,7 @@ int swe_get_state_device(swe_handle *s, void *h, void *hu, void *hv) {
 }
 
 int swe_mass(swe_handle *s, double *mass, double *clamp_mass) {
+  const TraceRange trace("swe_mass");
   if (!s) return SWE_EINVAL;
   cudaError_t e =
       s->prec == SWE_F64
@@ -511,6 +560,7 @@ int swe_mass(swe_handle *s, double *mass, double *clamp_mass) {
 }
 
 int swe_diagnostics(swe_handle *s, swe_diag *d) {
+  const TraceRange trace("swe_diagnostics");
   if (!s || !d) return SWE_EINVAL;
   DevScalars h;
   cudaError_t e = cudaMemcpyAsync(&h, s->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream);
@@ -598,6 +648,7 @@ int swe_destroy(swe_handle *s) {
 }
 
 int swe_time_stages(swe_handle *s, int32_t n, double cfl, double *ms_total, double *ms_stage) {
+  const TraceRange trace("swe_time_stages");
   if (!s || n <= 0) return SWE_EINVAL;
   int rc = swe_step(s, 1, cfl);  // make sure cfl is on the device and the graph exists
   if (rc != SWE_OK) return rc;

@@ -17,6 +17,7 @@
 
 #include "../../include/swe.h"
 #include "swe_launch.h"
+#include "swe_trace.h"
 
 namespace {
 
@@ -122,6 +123,7 @@ extern "C" {
 
 int swe_autotune(const swe_grid *grids, int32_t ngrids, int32_t precision, int32_t mode, int32_t steps,
                  int32_t *best_tile, double *ms) {
+  const swe::TraceRange trace("swe_autotune");
   if (!grids || ngrids < 1 || (mode != 0 && mode != 1) || steps < 1 || !best_tile) return SWE_EINVAL;
   if (mode == 1 && precision != SWE_F32) return SWE_EINVAL;
   for (int g = 0; g < ngrids; ++g)

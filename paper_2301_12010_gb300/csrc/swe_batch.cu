@@ -13,6 +13,8 @@
 
 #include "../../include/swe.h"
 #include "swe_batch.h"
+#include "swe_trace.h"
+#include "swe_alloc.h"
 
 using namespace swe;
 
@@ -158,6 +160,7 @@ size_t swe_batch_slot_bytes(const swe_grid *grid) {
 }
 
 int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *params, swe_batch **out) {
+  const TraceRange trace("swe_batch_create");
   if (out) *out = nullptr;
   if (!out || !params || nslots < 1 || nslots > 4096 || hbm_budget_bytes == 0) return SWE_EINVAL;
   if (params->precision != SWE_F32) return SWE_EINVAL;  // the batch path is FP32
@@ -179,10 +182,10 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
   b->stream = (cudaStream_t)params->stream;
   b->slots.resize(nslots);
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_sc, sizeof(DevScalars) * nslots);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_table, sizeof(BatchSlot<float>) * nslots);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_part, sizeof(double) * (kMassBlocks + 1));
+  if (e == cudaSuccess) e = dev_malloc((void **)&b->d_sc, sizeof(DevScalars) * nslots);
+  if (e == cudaSuccess) e = dev_malloc((void **)&b->d_table, sizeof(BatchSlot<float>) * nslots);
+  if (e == cudaSuccess) e = dev_malloc((void **)&b->d_ctl, sizeof(BatchCtl));
+  if (e == cudaSuccess) e = dev_malloc((void **)&b->d_part, sizeof(double) * (kMassBlocks + 1));
   int per_sm = 0, dev = 0, sms = 0;
   if (e == cudaSuccess) e = batch_resident(b->tile, &per_sm);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -205,6 +208,7 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
 
 int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, const double *bathymetry,
                     const double *h, const double *hu, const double *hv, double t_end, int32_t *slot) {
+  const TraceRange trace("swe_batch_admit");
   if (slot) *slot = -1;
   if (!b || !grid || !bathymetry || !h || !hu || !hv || !slot) return SWE_EINVAL;
   if (grid->nx < 3 || grid->ny < 3 || !(dx > 0.0) || !(dy > 0.0) || !(t_end > 0.0)) return SWE_EINVAL;
@@ -223,7 +227,12 @@ int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, co
   sl.dy = dy;
   sl.t_end = t_end;
   const size_t plane = plane_bytes(sl.nx, sl.ny, &sl.pitch);
-  cudaError_t e = cudaMallocAsync(&sl.mem, need, b->stream);
+  cudaError_t e = dev_malloc_async(&sl.mem, need, b->stream);
+  if (e == cudaErrorMemoryAllocation) {  // no room now: the batch is unchanged and usable
+    (void)cudaGetLastError();
+    sl = Slot();
+    return SWE_ENOMEM;
+  }
   if (e != cudaSuccess) return bfail(b, e);
   char *q = (char *)sl.mem;
   sl.fd.b = (const float *)q;
@@ -278,6 +287,7 @@ int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, co
 }
 
 int swe_batch_run(swe_batch *b, int32_t k_steps, double cfl) {
+  const TraceRange trace("swe_batch_run");
   if (!b || k_steps < 0 || !(cfl > 0.0)) return SWE_EINVAL;
   if (b->sticky != SWE_OK) return b->sticky;
   if (k_steps == 0) return SWE_OK;
@@ -320,6 +330,7 @@ int swe_batch_status(swe_batch *b) {
 }
 
 int swe_batch_poll(swe_batch *b, int32_t *done_slots, int32_t *ndone) {
+  const TraceRange trace("swe_batch_poll");
   if (!b || !ndone) return SWE_EINVAL;
   *ndone = 0;
   std::vector<DevScalars> h(b->nslots);
@@ -386,6 +397,7 @@ int swe_batch_diagnostics(swe_batch *b, int32_t slot, swe_diag *d) {
 }
 
 int swe_batch_get_state(swe_batch *b, int32_t slot, double *h, double *hu, double *hv) {
+  const TraceRange trace("swe_batch_get_state");
   if (!valid_slot(b, slot) || !h || !hu || !hv) return SWE_EINVAL;
   Slot &sl = b->slots[slot];
   const size_t nb = sizeof(double) * (size_t)sl.nx * sl.ny;
@@ -403,6 +415,7 @@ int swe_batch_get_state(swe_batch *b, int32_t slot, double *h, double *hu, doubl
 }
 
 int swe_batch_retire(swe_batch *b, int32_t slot, double *h, double *hu, double *hv, double *mass, double *runup_max) {
+  const TraceRange trace("swe_batch_retire");
   if (!valid_slot(b, slot)) return SWE_EINVAL;
   Slot &sl = b->slots[slot];
   int rc = SWE_OK;

@@ -9,6 +9,14 @@ horizon (swe_batch_retire: result copied to the host).  Work of requests that
 arrive while others run overlaps on the device.  Latency is arrival ->
 result on the host.
 
+A request may carry `deadline` (seconds after its arrival by which the
+result is wanted) and `cancel_at` (seconds after its arrival at which the
+client withdraws it).  Between launches the loop drops such requests, waiting
+or live (a live one is retired without its state and its slot and memory are
+freed), and reports them as "expired" or "cancelled".  A request that cannot
+be admitted even into an empty batch (larger than the budget or the device
+memory) is reported as "rejected".
+
 Scheduling policy between macro-launches:
   * "all": every live request advances K steps per launch (processor
     sharing by steps: a small request takes as many launches as its steps,
@@ -43,6 +51,7 @@ class Result:
     mass: float
     runup_max: float
     state: Optional[tuple] = None
+    status: str = "done"  # "done", "expired", "cancelled" or "rejected"
 
     @property
     def latency(self) -> float:
@@ -58,13 +67,21 @@ class Report:
     cell_updates: float
 
     def latency_ms(self, q: float) -> float:
-        lat = np.array([r.latency for r in self.results]) * 1e3
+        """Latency percentile (ms) of the completed requests."""
+        lat = np.array([r.latency for r in self.results if r.status == "done"]) * 1e3
         return float(np.percentile(lat, q)) if len(lat) else float("nan")
 
+    def count(self, status: str) -> int:
+        return sum(1 for r in self.results if r.status == status)
+
     def summary(self) -> Dict[str, float]:
-        return {"requests": len(self.results), "p50_ms": self.latency_ms(50), "p99_ms": self.latency_ms(99),
-                "throughput_cell_updates_per_s": self.cell_updates / self.wall if self.wall > 0 else 0.0,
-                "wall_s": self.wall, "macro_launches": self.macro_launches, "max_live_slots": self.max_live}
+        out = {"requests": len(self.results), "p50_ms": self.latency_ms(50), "p99_ms": self.latency_ms(99),
+               "throughput_cell_updates_per_s": self.cell_updates / self.wall if self.wall > 0 else 0.0,
+               "wall_s": self.wall, "macro_launches": self.macro_launches, "max_live_slots": self.max_live}
+        for st in ("expired", "cancelled", "rejected"):
+            if self.count(st):
+                out[st] = self.count(st)
+        return out
 
 
 class Server:
@@ -99,6 +116,18 @@ class Server:
                 break
         return sorted(chosen)
 
+    @staticmethod
+    def _overdue(req, now: float, time_scale: float) -> Optional[str]:
+        """"cancelled" or "expired" once the request's cancel or deadline
+        time (seconds after its arrival) has passed on the loop's clock."""
+        arrival = req.arrival / time_scale
+        cancel, deadline = getattr(req, "cancel_at", None), getattr(req, "deadline", None)
+        if cancel is not None and now >= arrival + cancel / time_scale:
+            return "cancelled"
+        if deadline is not None and now >= arrival + deadline / time_scale:
+            return "expired"
+        return None
+
     def close(self):
         self.batch.close()
 
@@ -128,6 +157,24 @@ class Server:
                 break
             while incoming and requests[incoming[0]].arrival / time_scale <= now:
                 waiting.append(incoming.popleft())
+            # withdrawn and expired requests leave, waiting or live
+            for k in [k for k in waiting if self._overdue(requests[k], now, time_scale)]:
+                waiting.remove(k)
+                sc = requests[k].scenario
+                results.append(Result(k, requests[k].arrival / time_scale, float("nan"), now, sc.cells, 0, 0.0,
+                                      float("nan"), float("nan"), None, self._overdue(requests[k], now, time_scale)))
+            for slot, (k, adm) in list(live.items()):
+                why = self._overdue(requests[k], now, time_scale)
+                if why is None:
+                    continue
+                live.pop(slot)
+                selected = None
+                d = self.batch.diagnostics(slot, check=False)
+                self.batch.retire(slot, want_state=False)
+                sc = requests[k].scenario
+                results.append(Result(k, requests[k].arrival / time_scale, adm, time.perf_counter() - t0, sc.cells,
+                                      d["steps"], d["t"], float("nan"), float("nan"), None, why))
+                cell_updates += float(sc.cells) * d["steps"]
             # admit in arrival order while slots and budget allow
             while waiting:
                 k = waiting[0]
@@ -139,6 +186,13 @@ class Server:
                 live[slot] = (k, time.perf_counter() - t0)
                 steps_seen[slot] = 0
             max_live = max(max_live, len(live))
+            if not live and waiting:
+                # not even an empty batch takes the head request: it never will
+                k = waiting.popleft()
+                sc = requests[k].scenario
+                results.append(Result(k, requests[k].arrival / time_scale, float("nan"), time.perf_counter() - t0,
+                                      sc.cells, 0, 0.0, float("nan"), float("nan"), None, "rejected"))
+                continue
             if not live:
                 if incoming:
                     wait = requests[incoming[0]].arrival / time_scale - (time.perf_counter() - t0)

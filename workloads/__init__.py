@@ -250,6 +250,8 @@ def mitigation_ensemble(count: int = 64, seed: int = 4, dx: float = 2.0, t_end: 
 class Request:
     arrival: float
     scenario: Scenario
+    deadline: Optional[float] = None   # s after arrival by which the result is wanted (None: none)
+    cancel_at: Optional[float] = None  # s after arrival at which the client withdraws (None: never)
 
 
 def serving_requests(rate: float, count: int, seed: int = 5, dx: float = 2.0,
