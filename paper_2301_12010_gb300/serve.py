@@ -89,10 +89,12 @@ class Server:
 
     def __init__(self, template, nslots: int = 64, budget_bytes: int = 150 << 30, k_steps: int = 50,
                  cfl: float = 0.4, stream: Optional[int] = None, tile: int = 0, keep_state: bool = False,
-                 policy: str = "all", fill_cells: int = 152 * 4 * 3072):
+                 policy: str = "all", fill_cells: int = 152 * 4 * 3072, batch=None):
+        """batch: an object with the Batch interface to serve through instead
+        of a new Batch (the host logic can then run against a stand-in)."""
         if policy not in ("all", "srpt"):
             raise ValueError("policy must be 'all' or 'srpt'")
-        self.batch = Batch(nslots, budget_bytes, template, stream=stream, tile=tile)
+        self.batch = batch if batch is not None else Batch(nslots, budget_bytes, template, stream=stream, tile=tile)
         self.k = int(k_steps)
         self.cfl = float(cfl)
         self.keep_state = keep_state
