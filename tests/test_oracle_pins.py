@@ -304,3 +304,22 @@ def test_standing_wave_shoreline_error_stays_bounded():
     ex, _, _ = A.standing_wave_on_slope(r, 0.5 * T, amp, L, slope)
     wet = r > 0.0
     assert np.sqrt(np.mean((eta[wet] - ex[wet]) ** 2)) <= 0.15 * amp
+
+
+def test_oracle_is_bitwise_independent_of_its_thread_count():
+    # OpenMP runs only over independent grid lines; reductions are in fixed
+    # order, so 1 and several threads give the same bits
+    sc = W.coastal_dem(n=48, dx=150.0, t0=500.0)
+    n0 = oracle.num_threads()
+    out = []
+    try:
+        for th in (1, 4):
+            oracle.set_threads(th)
+            sim = oracle.Simulation(sc)
+            sim.step(15)
+            out.append((sim.h.copy(), sim.hu.copy(), sim.hv.copy(), sim.diag()["mass"]))
+    finally:
+        oracle.set_threads(n0)
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
+    assert out[0][3] == out[1][3]
