@@ -323,3 +323,28 @@ def test_oracle_is_bitwise_independent_of_its_thread_count():
     for a, b in zip(out[0][:3], out[1][:3]):
         assert np.array_equal(a, b)
     assert out[0][3] == out[1][3]
+
+
+def test_inflow_enters_as_the_right_going_long_wave():
+    # A small N-wave (2 cm on 10 m, period 60 s) through the inflow edge of a
+    # flat channel must be the right-going long wave eta(x, t) = eta_in(t -
+    # x/c0) with hu = c0 eta.  The elevation pins the time mapping and the
+    # amplitude of Eq. (20); the amplitude inside also pins the ghost
+    # velocity u = eta_in sqrt(g/d0): the split flux at the edge face is about
+    # (hu_ghost + hu_inside)/2 plus the elevation jump, so a ghost at rest
+    # would let in about half the mass flux, twice the velocity 1.5 times.
+    d0, period, amp, dx, nx = 10.0, 60.0, 0.02, 5.0, 400
+    b = np.full((4, nx), -d0)
+    z = np.zeros_like(b)
+    sc = W.Scenario("channel", dx, dx, b, -b, z.copy(), z.copy(), bc=(W.INFLOW, W.WALL, W.WALL, W.WALL),
+                    inflow_amp=amp, inflow_period=period, inflow_depth=d0)
+    c0 = np.sqrt(W.G * d0)
+    sim = oracle.Simulation(sc)
+    while sim.t < 100.0:  # crest ~ 500 m in, front short of the far wall
+        sim.step(50)
+    x = (np.arange(nx) + 0.5) * dx
+    want = np.array([oracle.inflow_eta(sc, sim.t - xi / c0) for xi in x])
+    eta, hu = sim.h[1] - d0, sim.hu[1]
+    assert abs(np.abs(eta).max() / amp - 1.0) <= 0.01
+    assert np.sqrt(((eta - want) ** 2).sum() / (want ** 2).sum()) <= 0.02
+    assert np.sqrt(((hu - c0 * want) ** 2).sum() / ((c0 * want) ** 2).sum()) <= 0.02
