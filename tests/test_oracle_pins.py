@@ -348,3 +348,32 @@ def test_inflow_enters_as_the_right_going_long_wave():
     assert abs(np.abs(eta).max() / amp - 1.0) <= 0.01
     assert np.sqrt(((eta - want) ** 2).sum() / (want ** 2).sum()) <= 0.02
     assert np.sqrt(((hu - c0 * want) ** 2).sum() / ((c0 * want) ** 2).sum()) <= 0.02
+
+
+def _cfl_dt(h, hu, hv, dx, dy, cfl, g=W.G, h_dry=1e-5):
+    # dt = CFL / (alpha_x/dx + alpha_y/dy), alpha = max |velocity| + sqrt(g h)
+    # over the cells of the step's starting state; no velocity below h_dry
+    wet = h >= h_dry
+    u = np.where(wet, hu / np.where(wet, h, 1.0), 0.0)
+    v = np.where(wet, hv / np.where(wet, h, 1.0), 0.0)
+    c = np.sqrt(g * np.maximum(h, 0.0))
+    return cfl / ((np.abs(u) + c).max() / dx + (np.abs(v) + c).max() / dy)
+
+
+def test_time_step_is_the_cfl_step_of_the_state_at_its_start():
+    rng = np.random.default_rng(17)
+    ny, nx, dx, dy = 24, 40, 2.0, 3.0
+    b = -1.0 + 0.2 * rng.standard_normal((ny, nx))
+    b[5:9, 10:14] = 0.5  # a dry island
+    h = np.maximum(0.1 - b + 0.02 * rng.standard_normal((ny, nx)), 0.0)
+    hu = np.where(h > 0, 0.3 * rng.standard_normal((ny, nx)) * h, 0.0)
+    hv = np.where(h > 0, 0.2 * rng.standard_normal((ny, nx)) * h, 0.0)
+    sc = W.Scenario("cfl", dx, dy, b, h, hu, hv, cfl=0.4)
+    sim = oracle.Simulation(sc)
+    want1 = _cfl_dt(h, hu, hv, dx, dy, 0.4)
+    sim.step(1)
+    assert sim.diag()["last_dt"] == pytest.approx(want1, rel=1e-13)
+    want2 = _cfl_dt(sim.h, sim.hu, sim.hv, dx, dy, 0.4)
+    assert want2 != pytest.approx(want1, rel=1e-6)  # the state moved
+    sim.step(1)
+    assert sim.diag()["last_dt"] == pytest.approx(want2, rel=1e-13)
