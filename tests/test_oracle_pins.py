@@ -377,3 +377,28 @@ def test_time_step_is_the_cfl_step_of_the_state_at_its_start():
     assert want2 != pytest.approx(want1, rel=1e-6)  # the state moved
     sim.step(1)
     assert sim.diag()["last_dt"] == pytest.approx(want2, rel=1e-13)
+
+
+def test_runup_is_the_highest_wet_land_surface_of_the_state():
+    # R8: runup_now = max of h + b over cells with h >= h_wet and b > 0 of the
+    # state after the step; runup_max its running maximum.  A pond on a
+    # rough hillside, partly thinner than h_wet, moving under gravity.
+    rng = np.random.default_rng(23)
+    ny, nx = 20, 30
+    x = np.arange(nx)[None, :] * np.ones((ny, 1))
+    b = 0.05 * x + 0.05 * rng.standard_normal((ny, nx))  # land rising in x, partly below 0
+    h = np.maximum(0.6 - b, 0.0) * (rng.random((ny, nx)) > 0.1)
+    h[h < 0.01] *= 0.05  # some films thinner than h_wet
+    z = np.zeros_like(b)
+    sc = W.Scenario("pond", 1.0, 1.0, b, h, z, z.copy())
+    sim = oracle.Simulation(sc)
+    best = -np.inf
+    for _ in range(5):
+        sim.step(1)
+        sel = (sim.h >= sc.h_wet) & (b > 0)
+        assert sel.any() and (~sel & (sim.h > 0)).any()
+        now = (sim.h + b)[sel].max()
+        best = max(best, now)
+        d = sim.diag()
+        assert d["runup_now"] == now
+        assert d["runup_max"] == best
