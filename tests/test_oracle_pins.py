@@ -402,3 +402,22 @@ def test_runup_is_the_highest_wet_land_surface_of_the_state():
         d = sim.diag()
         assert d["runup_now"] == now
         assert d["runup_max"] == best
+
+
+def test_post_stage_rule_leaves_no_negative_depth_and_no_dry_momentum():
+    # R5 after every stage: h < 0 is clamped to 0 (its deficit counted) and
+    # cells below h_dry carry no momentum; the drying bowl exercises both
+    sc = W.lake_at_rest(32, 32, eta0=0.5, depth=10.0, rms=2.0, islands=True)
+    rng = np.random.default_rng(29)
+    sc.hu[:] = np.where(sc.h > 0, 2.0 * rng.standard_normal(sc.h.shape) * sc.h, 0.0)
+    sim = oracle.Simulation(sc)
+    for _ in range(20):
+        sim.step(1)
+        assert (sim.h >= 0).all()
+        dry = sim.h < sc.h_dry
+        assert dry.any()
+        assert (sim.hu[dry] == 0).all() and (sim.hv[dry] == 0).all()
+    d = sim.diag()
+    assert d["clamp_mass"] > 0  # the violent start drove some cells below zero
+    m0 = sc.h.sum() * sc.dx * sc.dy
+    assert d["mass"] - d["clamp_mass"] == pytest.approx(m0, rel=1e-13)
