@@ -70,3 +70,21 @@ def test_tile_shapes(swe):
     for tx, ty, nt in shapes:
         # one strip of S = 8 or 16 cells per thread in both sweep directions
         assert any((tx // S) * ty == nt and (ty // S) * tx == nt for S in (8, 16))
+
+
+def test_batch_arguments_rejected_without_gpu(swe):
+    p = swe.Params()
+    swe.lib.swe_params_default(ctypes.byref(p))
+    b = ctypes.c_void_p()
+    assert swe.lib.swe_batch_destroy(None) == swe.OK
+    assert swe.lib.swe_batch_create(0, 1 << 30, ctypes.byref(p), ctypes.byref(b)) == swe.EINVAL
+    assert swe.lib.swe_batch_create(4, 0, ctypes.byref(p), ctypes.byref(b)) == swe.EINVAL
+    q = swe.Params.from_buffer_copy(p)
+    q.precision = swe.F64  # the batch path is FP32
+    assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
+    q = swe.Params.from_buffer_copy(p)
+    q.bc[0] = swe.INFLOW  # ensembles and requests are walled coasts
+    assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
+    assert not b.value
+    assert swe.lib.swe_batch_run(None, 1, 0.4) == swe.EINVAL
+    assert swe.lib.swe_batch_poll(None, None, None) == swe.EINVAL
