@@ -83,6 +83,8 @@ def _load():
                                     ctypes.POINTER(Params), dp, dp, dp, dp, ctypes.c_double,
                                     ctypes.c_double, dp, dp, dp, dp, dp]
         lib.or_operator.restype = ctypes.c_int
+        lib.or_post_stage.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), dp, dp, dp, dp]
+        lib.or_post_stage.restype = ctypes.c_int
         lib.or_weno5.argtypes = [dp, ctypes.c_double, dp]
         lib.or_weno5.restype = ctypes.c_double
         lib.or_inflow_eta.argtypes = [ctypes.POINTER(Params), ctypes.c_double]
@@ -179,6 +181,20 @@ def operator(sc, t: float = 0.0, dt: float = 0.0, h=None, hu=None, hv=None) -> T
     if rc:
         raise OracleError(rc)
     return Lh, Lhu, Lhv, (float(a2[0]), float(a2[1])), float(ef[0])
+
+
+def post_stage(sc, h, hu, hv) -> Tuple[np.ndarray, np.ndarray, np.ndarray, float]:
+    """The post-stage rule of every RK stage applied once to a state (R5 and
+    the film desingularisation): returns the new (h, hu, hv) and the depth
+    added by the h < 0 clamp, summed over cells."""
+    p = params_of(sc)
+    h, hu, hv = (np.array(x, dtype=np.float64, order="C") for x in (h, hu, hv))
+    ny, nx = h.shape
+    added = np.zeros(1)
+    rc = _load().or_post_stage(nx, ny, ctypes.byref(p), _dp(h), _dp(hu), _dp(hv), _dp(added))
+    if rc:
+        raise OracleError(rc)
+    return h, hu, hv, float(added[0])
 
 
 def weno5(v, eps: float = 1e-6) -> Tuple[float, np.ndarray]:

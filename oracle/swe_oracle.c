@@ -750,6 +750,34 @@ int or_operator(int nx, int ny, double dx, double dy, const or_params *p, const 
   return rc;
 }
 
+/* The post-stage rule alone (for pins): applies to the state h, hu, hv
+ * [ny][nx] (in/out) exactly what every RK stage applies after its update --
+ * h < 0 -> 0, no momentum below h_dry, the film velocity desingularisation
+ * below h_film -- and returns the depth it added in *added (m, summed over
+ * cells; not multiplied by the cell area). */
+int or_post_stage(int nx, int ny, const or_params *p, double *h, double *hu, double *hv,
+                  double *added) {
+  int rc = validate(nx, ny, 1.0, 1.0, p);
+  if (rc) return rc;
+  double *zero = (double *)calloc((size_t)nx * ny, sizeof(double));
+  if (!zero) return OR_ENOMEM;
+  work_t w;
+  rc = work_alloc(&w, nx, ny, 1.0, 1.0, p, zero, h, hu, hv);
+  free(zero);
+  if (rc) return rc;
+  double a = post_rule(&w.g, w.U0.h, w.U0.hu, w.U0.hv);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t c = ix(&w.g, i, j), o = (size_t)j * nx + i;
+      h[o] = w.U0.h[c];
+      hu[o] = w.U0.hu[c];
+      hv[o] = w.U0.hv[c];
+    }
+  if (added) *added = a;
+  free(w.mem);
+  return OR_OK;
+}
+
 /* WENO5-JS value at the right face of v[2] and its weights (for pins). */
 double or_weno5(const double *v, double eps, double *w) {
   double ww[3];

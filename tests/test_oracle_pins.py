@@ -421,3 +421,76 @@ def test_post_stage_rule_leaves_no_negative_depth_and_no_dry_momentum():
     assert d["clamp_mass"] > 0  # the violent start drove some cells below zero
     m0 = sc.h.sum() * sc.dx * sc.dy
     assert d["mass"] - d["clamp_mass"] == pytest.approx(m0, rel=1e-13)
+
+
+def _kurganov_petrova_velocity(h, q, eps4):
+    # Kurganov & Petrova (2007), Eq. (2.17): u = sqrt(2) h q / sqrt(h^4 + max(h^4, eps)),
+    # with the a-priori small number eps taken as h_film^4; the momentum is then h u
+    h4 = h ** 4
+    return math.sqrt(2.0) * h * q / np.sqrt(h4 + np.maximum(h4, eps4))
+
+
+def test_post_stage_film_rule_is_the_kurganov_petrova_desingularisation():
+    # R5: after each stage, films h_dry <= h < h_film carry hu := h u with u
+    # the desingularised velocity of Kurganov-Petrova (max form, computed here
+    # independently of the oracle's piecewise form); at and above h_film the
+    # state is untouched, below h_dry the momentum is zero and h < 0 clamps to
+    # zero.  Depths span all four regimes, log-spaced through the film band.
+    sc = W.lake_at_rest(8, 8, eta0=0.0, depth=1.0, rms=0.0)
+    rng = np.random.default_rng(41)
+    hf, hd = sc.h_film, sc.h_dry
+    h = np.concatenate([-np.geomspace(1e-7, 1e-2, 6), np.geomspace(1e-9, 0.99 * hd, 6),
+                        np.geomspace(hd, hf, 40, endpoint=False), [hf, np.nextafter(hf, 0.0)],
+                        np.geomspace(hf, 10.0, 10)])
+    h = np.resize(h, 64).reshape(8, 8)
+    hu = rng.normal(size=h.shape) * np.maximum(np.abs(h), 1e-6) * 3.0
+    hv = rng.normal(size=h.shape) * np.maximum(np.abs(h), 1e-6) * 3.0
+    h2, hu2, hv2, added = oracle.post_stage(sc, h, hu, hv)
+    hc = np.maximum(h, 0.0)
+    assert np.array_equal(h2, hc)
+    assert added == pytest.approx(-h[h < 0].sum(), rel=1e-15)
+    dry = hc < hd
+    film = (hc >= hd) & (hc < hf)
+    thick = hc >= hf
+    assert film.sum() >= 40 and thick.sum() >= 10 and dry.sum() >= 12
+    assert (hu2[dry] == 0).all() and (hv2[dry] == 0).all()
+    assert np.array_equal(hu2[thick], hu[thick]) and np.array_equal(hv2[thick], hv[thick])
+    for q, q2 in ((hu, hu2), (hv, hv2)):
+        want = hc[film] * _kurganov_petrova_velocity(hc[film], q[film], hf ** 4)
+        assert np.allclose(q2[film], want, rtol=1e-14, atol=0.0)
+    # the factor is continuous at h_film (-> 1) and the velocity of a film is
+    # bounded by sqrt(2) (h/h_film)^2 times the undesingularised one
+    f = hu2[film] / hu[film]
+    hh = hc[film]
+    assert np.all(f <= math.sqrt(2.0) * (hh / hf) ** 2 * (1 + 1e-15))
+    assert np.all(f > 0) and np.all(np.diff(f[np.argsort(hh)]) > 0)
+    top = hh == hh.max()
+    assert f[top][0] == pytest.approx(1.0, abs=2e-2)  # the last film depth is 2.7 % below h_film
+
+
+def test_fixed_time_step_is_used_for_every_stage_and_accumulates_time():
+    # R10: with fixed_dt > 0 (the paper's 5e-3 s runs, Tables 1-3) every step
+    # takes exactly that dt and t advances by it step after step.  The fixed
+    # branch must apply the same dt to all three stages and to the friction
+    # cap: one step with fixed_dt equal to the CFL step of the state is the
+    # CFL step, bit for bit.
+    sc = W.gaussian_hump(n=48, sigma_cells=4.0)
+    sc.manning_n = 0.03
+    cfl = oracle.Simulation(sc)
+    cfl.step(1)
+    dt_cfl = cfl.diag()["last_dt"]
+    fixed = oracle.Simulation(sc.copy(fixed_dt=dt_cfl))
+    fixed.step(1)
+    assert fixed.diag()["last_dt"] == dt_cfl
+    assert np.array_equal(fixed.h, cfl.h) and np.array_equal(fixed.hu, cfl.hu) and np.array_equal(fixed.hv, cfl.hv)
+    sim = oracle.Simulation(sc.copy(fixed_dt=5e-3))
+    t = 0.0
+    for n in range(1, 9):
+        sim.step(1)
+        t += 5e-3
+        d = sim.diag()
+        assert d["last_dt"] == 5e-3 and d["steps"] == n and d["t"] == t
+    # a different fixed step gives a different state (the branch is live)
+    other = oracle.Simulation(sc.copy(fixed_dt=4e-3))
+    other.step(8)
+    assert not np.array_equal(other.h, sim.h)
