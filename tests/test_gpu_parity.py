@@ -139,6 +139,62 @@ def test_fp64_standing_wave_on_slope():
     assert np.abs(hu - ref.hu).max() <= 1e-10
 
 
+@pytest.mark.parametrize("precision", [swe.F64, swe.F32])
+def test_fixed_time_step_hump_and_planar_beach(precision):
+    # the paper's timed runs use a fixed dt of 5e-3 s (Tables 1-3): every step
+    # takes exactly that dt and t accumulates it as the oracle's does; the hump
+    # of config 1 for 200 steps and the planar beach of config 2 (wet/dry,
+    # Manning friction; ny = 4, y-uniform) for 1000 steps
+    cases = ((W.gaussian_hump(), 200), (W.planar_beach(ny=4), 1000))
+    for base, steps in cases:
+        sc = base.copy(fixed_dt=5e-3)
+        ref = run_oracle(sc, steps)
+        rd = ref.diag()
+        h, hu, hv, d, _ = run_gpu(sc, steps, precision)
+        assert d["steps"] == steps and d["last_dt"] == 5e-3 and d["t"] == rd["t"], sc.name
+        if precision == swe.F64:
+            assert np.abs(h - ref.h).max() <= 1e-10, sc.name
+            assert np.abs(hu - ref.hu).max() <= 1e-10 and np.abs(hv - ref.hv).max() <= 1e-10, sc.name
+        else:
+            assert rel_l2(eta_tilde(h, sc.b), eta_tilde(ref.h, sc.b)) <= 1e-4, sc.name
+            assert rel_l2(hu, ref.hu) <= 1e-4, sc.name
+        if rd["runup_max"] > -np.inf:
+            assert abs(d["runup_max"] - rd["runup_max"]) <= (1e-10 if precision == swe.F64 else 0.01)
+
+
+def _film_beach(nx=96, ny=24, seed=43):
+    # a rough 1:40 beach with still water at 0 and, on land, a patchwork of
+    # films of depth h_dry .. 3 h_film with random velocities: the post-stage
+    # film rule (Kurganov-Petrova desingularisation below h_film) acts on
+    # hundreds of cells in every stage
+    rng = np.random.default_rng(seed)
+    x = (np.arange(nx) + 0.5)[None, :] * np.ones((ny, 1))
+    b = (x - nx / 2) / 40.0 + 0.02 * rng.standard_normal((ny, nx))
+    h = np.maximum(-b, 0.0)
+    land = h == 0.0
+    film = land & (rng.random((ny, nx)) < 0.6)
+    h[film] = np.exp(rng.uniform(np.log(1e-5), np.log(3e-3), size=film.sum()))
+    u = rng.normal(size=(ny, nx)) * 0.3
+    v = rng.normal(size=(ny, nx)) * 0.3
+    sc = W.Scenario("film_beach", 1.0, 1.0, b, h, h * u, h * v, manning_n=0.02)
+    return sc
+
+
+@pytest.mark.parametrize("precision", [swe.F64, swe.F32])
+def test_thin_films_on_land(precision):
+    sc = _film_beach()
+    assert ((sc.h >= sc.h_dry) & (sc.h < sc.h_film)).sum() >= 400
+    ref = run_oracle(sc, 30)
+    h, hu, hv, d, (m, cm) = run_gpu(sc, 30, precision)
+    if precision == swe.F64:
+        assert np.abs(h - ref.h).max() <= 1e-10
+        assert np.abs(hu - ref.hu).max() <= 1e-10 and np.abs(hv - ref.hv).max() <= 1e-10
+        assert cm == pytest.approx(ref.diag()["clamp_mass"], rel=1e-9, abs=1e-12)
+    else:
+        assert rel_l2(eta_tilde(h, sc.b), eta_tilde(ref.h, sc.b)) <= 1e-4
+        assert rel_l2(hu, ref.hu) <= 1e-4 and rel_l2(hv, ref.hv) <= 1e-4
+
+
 # ------------------------------------------------------------------ FP32
 def test_fp32_standing_wave_on_slope():
     sc = W.standing_wave_slope(nx_sea=100, nx_land=20, dx=10.0, amp=0.002)
