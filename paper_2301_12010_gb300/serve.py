@@ -15,7 +15,11 @@ client withdraws it).  Between launches the loop drops such requests, waiting
 or live (a live one is retired without its state and its slot and memory are
 freed), and reports them as "expired" or "cancelled".  A request that cannot
 be admitted even into an empty batch (larger than the budget or the device
-memory) is reported as "rejected".
+memory) is reported as "rejected".  A scenario that stops before its horizon
+because its solve failed (a non-finite state, or a domain that ran dry: the
+batch then reports the slot as finished with a nonzero status) is reported as
+"failed", without its state; like the other unfinished requests it is left
+out of the latency percentiles and of the cell-update count.
 
 Scheduling policy between macro-launches:
   * "all": every live request advances K steps per launch (processor
@@ -36,7 +40,7 @@ from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
-from . import Batch, slot_bytes
+from . import OK, Batch, slot_bytes
 
 
 @dataclasses.dataclass
@@ -51,7 +55,7 @@ class Result:
     mass: float
     runup_max: float
     state: Optional[tuple] = None
-    status: str = "done"  # "done", "expired", "cancelled" or "rejected"
+    status: str = "done"  # "done", "expired", "cancelled", "rejected" or "failed"
 
     @property
     def latency(self) -> float:
@@ -78,7 +82,7 @@ class Report:
         out = {"requests": len(self.results), "p50_ms": self.latency_ms(50), "p99_ms": self.latency_ms(99),
                "throughput_cell_updates_per_s": self.cell_updates / self.wall if self.wall > 0 else 0.0,
                "wall_s": self.wall, "macro_launches": self.macro_launches, "max_live_slots": self.max_live}
-        for st in ("expired", "cancelled", "rejected"):
+        for st in ("expired", "cancelled", "rejected", "failed"):
             if self.count(st):
                 out[st] = self.count(st)
         return out
@@ -212,9 +216,16 @@ class Server:
                 selected = None  # the work list changes with the retirement
                 k, adm = live.pop(slot)
                 d = self.batch.diagnostics(slot, check=False)
-                st, m, r = self.batch.retire(slot, want_state=self.keep_state)
                 sc = requests[k].scenario
+                # a slot also finishes when its solve failed (nonzero device
+                # status: non-finite state, dry domain) before its horizon
+                failed = int(d.get("status", OK)) != OK or not d["t"] >= float(sc.t_end)
+                st, m, r = self.batch.retire(slot, want_state=self.keep_state and not failed)
                 fin = time.perf_counter() - t0
+                if failed:
+                    results.append(Result(k, requests[k].arrival / time_scale, adm, fin, sc.cells, d["steps"],
+                                          d["t"], float("nan"), float("nan"), None, "failed"))
+                    continue
                 results.append(Result(k, requests[k].arrival / time_scale, adm, fin, sc.cells, d["steps"], d["t"],
                                       m, r, st))
                 cell_updates += float(sc.cells) * d["steps"]

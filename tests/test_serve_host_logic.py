@@ -139,3 +139,44 @@ def test_expired_cancelled_and_rejected_requests_leave_cleanly():
     done = [r.latency for r in rep.results if r.status == "done"]
     assert rep.latency_ms(50) == pytest.approx(np.percentile(np.array(done) * 1e3, 50))
     assert fake.memory()[0] == 0
+
+
+class FailingBatch(FakeBatch):
+    """A stand-in whose listed requests (by cell count) fail after a few
+    steps the way the device reports it: the slot stops, carries a nonzero
+    status (SWE_ENONFINITE) and is listed by poll() as finished."""
+
+    def __init__(self, *a, fail_cells=(), fail_after=3, **kw):
+        super().__init__(*a, **kw)
+        self.fail_cells, self.fail_after = set(fail_cells), fail_after
+
+    def run(self, k, cfl=0.4):
+        super().run(k, cfl)
+        for v in self.slots.values():
+            if v["cells"] in self.fail_cells and v["steps"] >= self.fail_after:
+                v["status"] = 4
+                v["steps"] = self.fail_after
+
+    def poll(self):
+        return sorted(s for s, v in self.slots.items() if v["t"] >= v["t_end"] or v.get("status", 0))
+
+    def diagnostics(self, slot, check=True):
+        d = super().diagnostics(slot, check)
+        d["status"] = self.slots[slot].get("status", 0)
+        return d
+
+
+def test_failed_solves_are_reported_failed_and_left_out_of_the_figures():
+    fake = FailingBatch(4, 10 ** 6, fail_cells=(77,), fail_after=2)
+    reqs = [request(0.0, 100, 1.0), request(0.0, 77, 1.0), request(0.0, 50, 0.5)]
+    rep = server(fake).serve(reqs)
+    st = {r.index: r.status for r in rep.results}
+    assert st == {0: "done", 1: "failed", 2: "done"}
+    bad = next(r for r in rep.results if r.index == 1)
+    assert bad.state is None and np.isnan(bad.mass) and bad.t < 1.0
+    # cell updates and latency percentiles count the completed requests only
+    assert rep.cell_updates == pytest.approx(100 * 8 + 50 * 4)
+    done = [r.latency for r in rep.results if r.status == "done"]
+    assert rep.latency_ms(99) == pytest.approx(np.percentile(np.array(done) * 1e3, 99))
+    assert rep.summary()["failed"] == 1
+    assert fake.memory()[0] == 0
