@@ -314,7 +314,9 @@ int swe_batch_destroy(swe_batch *b);
  * unknown precision, or ny > SWE_NOALLOC_MAX_ROWS (checked before any device
  * work); SWE_ECUDA if the launch fails.  Asynchronous; allocates nothing.
  * The first call on a device looks up the scratch array's address and caches
- * it: make that first call before any stream capture on the device.  All
+ * it with the device's current context: make that first call before any
+ * stream capture on the device.  After cudaDeviceReset the next call looks
+ * the address up again in the new context.  All
  * calls on a device share the scratch array, so calls whose work overlaps on
  * the GPU (several streams or host threads) race; calls ordered on one
  * stream are safe and need no clearing in between. */

@@ -12,7 +12,7 @@
 #include <vector>
 
 #include "../../include/swe.h"
-#include "swe_batch.h"
+#include "swe_launch.h"
 #include "swe_trace.h"
 #include "swe_alloc.h"
 

@@ -32,8 +32,9 @@ struct BatchCtl {
 };
 
 // Grid-wide barrier of a cooperative launch with a bounded wait.  Returns
-// false (and sets ST_TIMEOUT) if the other CTAs did not arrive in time; the
-// caller then leaves the kernel.
+// false if the other CTAs did not arrive in time (ST_TIMEOUT is set) or if
+// another CTA already flagged a batch-wide status (that status is kept as
+// it is); the caller then leaves the kernel.
 __device__ __forceinline__ bool grid_barrier(BatchCtl *ctl, unsigned nblocks) {
   __shared__ unsigned ok;
   __syncthreads();
@@ -50,7 +51,11 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl *ctl, unsigned nblocks) {
     } else {
       const long long t0 = clock64();
       while (*gen == g) {
-        if (clock64() - t0 > ctl->bar_cycles || *(volatile unsigned *)&ctl->status) {
+        if (*(volatile unsigned *)&ctl->status) {  // another CTA gave up: leave with its status
+          ok = 0u;
+          break;
+        }
+        if (clock64() - t0 > ctl->bar_cycles) {
           atomicOr(&ctl->status, ST_TIMEOUT);
           ok = 0u;
           break;

@@ -17,14 +17,18 @@
 //   - At most SWE_NOALLOC_MAX_ROWS rows; larger grids are rejected with
 //     SWE_EINVAL before any device work.
 //   - The first call on a device looks up the scratch array's device address
-//     (cudaGetSymbolAddress, with that device current) and caches it; make
-//     that first call before any stream capture on the device.
+//     (cudaGetSymbolAddress, with that device current) and caches it with the
+//     device's current context; make that first call before any stream
+//     capture on the device.  A later call in another context of the device
+//     (after cudaDeviceReset, which loads the library's device image anew)
+//     looks the address up again instead of using the old one.
 //   - Every call on a device shares the one scratch array: calls whose work
 //     overlaps on the GPU (different streams, or several host threads) race
 //     and may return wrong sums.  Calls ordered on one stream are safe; each
 //     call rewrites every partial it reads, so nothing needs clearing between
 //     calls.
 //   - No cudaMalloc, cudaFree or allocating library routine is called.
+#include <cuda.h>  // CUcontext (the type only; the entry point is resolved through the runtime)
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -71,19 +75,49 @@ __global__ void k_rows_total(const double *__restrict__ part, int ny, double are
 
 std::mutex g_lock;
 double *g_scratch[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};  // context in which g_scratch[dev] was looked up
 
-// Device address of the scratch array for the current device, looked up once.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+
+// cuCtxGetCurrent from the driver, resolved once through the runtime (no
+// link-time dependence on the driver library); nullptr if unavailable.
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(f);
+    else
+      (void)cudaGetLastError();
+  }
+  return fn;
+}
+
+// Device address of the scratch array for the current device: looked up once
+// per device and context (a new context, e.g. after cudaDeviceReset, holds a
+// new copy of the array at another address).
 cudaError_t scratch_for_current_device(double **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  // the context current on this thread; none before the runtime's first
+  // call on the device, in which case the lookup below makes it current
+  const CtxGetCurrentFn get = ctx_get_current();
+  CUcontext ctx = nullptr;
+  if (get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
   std::lock_guard<std::mutex> guard(g_lock);
-  if (!g_scratch[dev]) {
+  if (!g_scratch[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_row_partials);
     if (e != cudaSuccess) return e;
+    if (get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
     g_scratch[dev] = static_cast<double *>(p);
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch[dev];
   return cudaSuccess;

@@ -7,6 +7,9 @@ the synchronisation of cudaMalloc/cudaFree, a C host without a handle).
 This file is collected last so that a failure here stops a run only after
 every other test has run; it passes alone in a fresh process as well."""
 import ctypes
+import math
+import os
+import re
 
 import numpy as np
 import pytest
@@ -21,7 +24,14 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 import paper_2301_12010_gb300 as swe  # noqa: E402
 
-MAX_ROWS = 16384
+
+def _max_rows() -> int:
+    # the limit as the C header states it (one source for library and test)
+    with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "swe.h")) as f:
+        return int(re.search(r"#define\s+SWE_NOALLOC_MAX_ROWS\s+(\d+)", f.read()).group(1))
+
+
+MAX_ROWS = _max_rows()
 
 
 def _fn():
@@ -67,3 +77,27 @@ def test_noalloc_rejects_sizes_beyond_the_maximum():
     assert f(h.data_ptr(), swe.F32, 4, MAX_ROWS + 1, 1.0, 1.0, out.data_ptr(), None) == swe.EINVAL
     assert f(h.data_ptr(), 9, 4, 4, 1.0, 1.0, out.data_ptr(), None) == swe.EINVAL
     assert f(None, swe.F32, 4, 4, 1.0, 1.0, out.data_ptr(), None) == swe.EINVAL
+
+
+@pytest.mark.parametrize("precision", [swe.F32, swe.F64])
+@pytest.mark.parametrize("shape", [(8, MAX_ROWS), (5, 1025), (70, 1030)])
+def test_noalloc_mass_at_row_counts_up_to_the_maximum(precision, shape):
+    # the largest accepted grid (every block of the row pass full), a row
+    # count just past one 1024-thread block of the final pass (its strided
+    # loop) and partial last blocks; against the correctly rounded sum of the
+    # same values on the host, twice in a row
+    f = _fn()
+    nx, ny = shape
+    rng = np.random.default_rng(nx * 7 + ny)
+    host = rng.uniform(0.0, 3.0, size=(ny, nx)).astype(np.float32 if precision == swe.F32 else np.float64)
+    h = torch.from_numpy(host).to("cuda")
+    dx, dy = 2.0, 0.5
+    want = math.fsum(host.astype(np.float64).ravel()) * dx * dy
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for c in range(2):
+        assert f(h.data_ptr(), precision, nx, ny, dx, dy, out[c:].data_ptr(), stream.cuda_stream) == swe.OK
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert got[0] == pytest.approx(want, rel=1e-12)
+    assert got[1] == got[0]
