@@ -33,21 +33,23 @@ METRIC = "cell-updates/s/GPU FP32 vs FP64 (oracle-matched), %HBM roofline; p50/p
 WORKLOAD = "synthetic coastal DEM 4096x4096, dx=5 m, shelf ramp -200 m to 0 + fractal noise (slope -2, 3 m rms), " \
            "land to +20 m, N-wave inflow 4 m / 600 s, Manning n=0.025, FP32 state, FP64 dt/mass reductions"
 
-# Algorithmic work per cell and RK stage (see the design notes for the
-# derivation): FP32 flops counting an FMA as two, and HBM bytes per stage.
-FLOPS_PER_CELL_STAGE = 1007.0
+# Algorithmic HBM bytes per cell and RK stage (the roofline the metric names):
+# stage 1 reads U^n (12 B) and b (4 B) and writes U1 (12 B); stages 2 and 3
+# also read U^n for the RK combination.  108 B per cell-update over a step.
 BYTES_PER_CELL_STAGE = {1: 28.0, 2: 40.0, 3: 40.0}
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop/FMA x max SM clock
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
-# RK stage from one ncu capture of the stage kernel on the 2048x2048 case of
-# the same workload (96x32 tile), per cell; reported for the 4096x4096 launch
-# scaled by its cells, and only while the stage kernel's sources are those
-# captured: its device code, its translation unit and the tile-shape table.
-NCU_TRAFFIC = {"tile": 7, "cells": 2048 * 2048,
-               "bytes": {1: 67.337728e6 + 15.208448e6, 2: 117.754112e6 + 28.455424e6, 3: 117.664512e6 + 19.184896e6},
+# ncu counters of one launch of each RK stage of the FP32 stage kernel on the
+# bench's own workload (4096 x 4096 coastal DEM, tile shape 7):
+# dram__bytes_read.sum + dram__bytes_write.sum (bytes per launch), executed
+# thread instructions per cell (smsp__thread_inst_executed.sum / cells) and
+# issue-active percent (sm__inst_issued.avg.pct_of_peak_sustained_active).
+# Reported only while the kernel's sources hash to the captured version (its
+# device code, its translation unit and the tile-shape table); None until a
+# capture of the current kernel is recorded.
+NCU_CAPTURE = {"tile": 7, "cells": 4096 * 4096, "profile": None,
+               "dram_bytes": None, "thread_inst_per_cell": None, "issue_active_pct": None,
                "sources": ("swe_core.cuh", "swe_kernels.cu", "swe_launch.h:SWE_SHAPES"),
-               "sha256": "c63ef1b9f770248666f5584979be6fd66dc55600a5d9f976970f4534a1d49d45"}
+               "sha256": None}
 
 
 def kernel_sources_sha256() -> str:
@@ -55,7 +57,7 @@ def kernel_sources_sha256() -> str:
     #define NAME block of that file."""
     import hashlib
     h = hashlib.sha256()
-    for name in NCU_TRAFFIC["sources"]:
+    for name in NCU_CAPTURE["sources"]:
         fname, _, block = name.partition(":")
         with open(os.path.join(ROOT, "paper_2301_12010_gb300", "csrc", fname), "rb") as f:
             data = f.read()
@@ -66,15 +68,24 @@ def kernel_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def ncu_traffic(tile: int, stage: int, cells: int):
-    """Captured DRAM bytes of one stage launch scaled to `cells`, or None if
-    the tile differs or the kernel changed since the capture."""
+def ncu_counters(tile: int, stage: int, cells: int):
+    """The captured counters of one launch of this RK stage, DRAM bytes scaled
+    to `cells` if the capture was of another size, or None if nothing was
+    captured for this tile, or the kernel changed since the capture."""
+    c = NCU_CAPTURE
     try:
-        if tile != NCU_TRAFFIC["tile"] or kernel_sources_sha256() != NCU_TRAFFIC["sha256"]:
+        if c["sha256"] is None or tile != c["tile"] or kernel_sources_sha256() != c["sha256"]:
             return None
     except OSError:
         return None
-    return NCU_TRAFFIC["bytes"][stage] / NCU_TRAFFIC["cells"] * cells
+    out = {"profile": c["profile"]}
+    if c["dram_bytes"]:
+        out["dram_bytes"] = c["dram_bytes"][stage] / c["cells"] * cells
+    if c["thread_inst_per_cell"]:
+        out["thread_inst_per_cell"] = c["thread_inst_per_cell"][stage]
+    if c["issue_active_pct"]:
+        out["issue_active_pct"] = c["issue_active_pct"][stage]
+    return out
 
 
 def peaks():
@@ -498,10 +509,10 @@ def main():
     dom = int(np.argmax(stage_ms)) + 1
     pk, pk_kind = peaks()
     dom_s = stage_ms[dom - 1] / 1e3
-    achieved_tf = FLOPS_PER_CELL_STAGE * cells / dom_s / 1e12
     achieved_gbs = BYTES_PER_CELL_STAGE[dom] * cells / dom_s / 1e9
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
     diag = solver.diagnostics()
+    counters = ncu_counters(diag["tile"], dom, cells)
 
     # end to end through the public API: every step uploads its input state
     # from pinned host FP64 arrays (swe_set_state), advances one step and reads
@@ -543,16 +554,20 @@ def main():
             "config": {"workload": WORKLOAD, "nx": sc.nx, "ny": sc.ny, "cells": cells,
                        "l2": "inputs larger than L2 (10 planes x %.0f MB)" % (cells * 4 / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single", "tile": diag["tile"]},
-            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": ncu_traffic(diag["tile"], dom, cells),
-                         "traffic_unit": "bytes per launch (ncu, 2048x2048 capture scaled by cells)",
+            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak,
+                         "traffic": counters.get("dram_bytes") if counters else None,
+                         "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                          "kernel": "stage_kernel<float> RK stage %d" % dom,
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                         "flops_per_cell_stage": FLOPS_PER_CELL_STAGE},
-            "hbm_roofline": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": achieved_gbs / hbm_peak, "peak_source": pk_kind,
-                             "bytes_per_cell_stage": BYTES_PER_CELL_STAGE[dom],
-                             "step_frac": (108.0 * cells * args.steps * ws / (ms_max / 1e3) / 1e9) / hbm_peak},
+                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % pk_kind,
+                         "bytes_per_cell_stage": BYTES_PER_CELL_STAGE[dom],
+                         "step_frac": (108.0 * cells * args.steps * ws / (ms_max / 1e3) / 1e9) / hbm_peak,
+                         "alu": {"thread_inst_per_cell_stage": counters.get("thread_inst_per_cell")
+                                 if counters else None,
+                                 "issue_active_pct": counters.get("issue_active_pct") if counters else None,
+                                 "source": counters.get("profile") if counters else None,
+                                 "note": "the kernel is bound by FP32 instruction issue, not HBM: executed thread "
+                                         "instructions per cell and RK stage and the issue-active share, from ncu"}},
             "stage_ms": stage_ms,
             "autotune": tune,
             "gpu_launches": 3 * args.steps,

@@ -1,5 +1,6 @@
-"""The bench reports the captured DRAM traffic of the stage kernel only for
-the tile shape and kernel sources it was captured with (host logic, CPU)."""
+"""The bench reports the ncu counters of the stage kernel (DRAM traffic,
+executed instructions, issue share) only for the tile shape and kernel
+sources they were captured with (host logic, CPU)."""
 import os
 import sys
 
@@ -15,7 +16,7 @@ def test_hash_covers_only_the_named_block_of_the_shape_header(tmp_path, monkeypa
     (csrc / "a.cuh").write_text("kernel code\n")
     (csrc / "t.h").write_text("// header\n#define TABLE(X) \\\n  X(1, 2)\n\nint unrelated;\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "sources", ("a.cuh", "t.h:TABLE"))
+    monkeypatch.setitem(bench.NCU_CAPTURE, "sources", ("a.cuh", "t.h:TABLE"))
     h0 = bench.kernel_sources_sha256()
     (csrc / "t.h").write_text("// header, edited\n#define TABLE(X) \\\n  X(1, 2)\n\nint other;\n")
     assert bench.kernel_sources_sha256() == h0  # outside the block: same kernel
@@ -25,11 +26,18 @@ def test_hash_covers_only_the_named_block_of_the_shape_header(tmp_path, monkeypa
     assert bench.kernel_sources_sha256() != h0
 
 
-def test_traffic_is_withheld_for_another_tile_or_changed_sources(monkeypatch):
+def test_counters_are_withheld_for_another_tile_or_changed_sources(monkeypatch):
     cells = 4096 * 4096
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "sha256", bench.kernel_sources_sha256())
-    got = bench.ncu_traffic(bench.NCU_TRAFFIC["tile"], 2, cells)
-    assert got == bench.NCU_TRAFFIC["bytes"][2] / bench.NCU_TRAFFIC["cells"] * cells
-    assert bench.ncu_traffic(bench.NCU_TRAFFIC["tile"] + 1, 2, cells) is None
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "sha256", "0" * 64)
-    assert bench.ncu_traffic(bench.NCU_TRAFFIC["tile"], 2, cells) is None
+    monkeypatch.setitem(bench.NCU_CAPTURE, "sha256", bench.kernel_sources_sha256())
+    monkeypatch.setitem(bench.NCU_CAPTURE, "cells", 2048 * 2048)
+    monkeypatch.setitem(bench.NCU_CAPTURE, "dram_bytes", {1: 1.0e8, 2: 1.5e8, 3: 1.4e8})
+    monkeypatch.setitem(bench.NCU_CAPTURE, "thread_inst_per_cell", {1: 500.0, 2: 510.0, 3: 511.0})
+    monkeypatch.setitem(bench.NCU_CAPTURE, "issue_active_pct", {1: 60.0, 2: 61.0, 3: 62.0})
+    got = bench.ncu_counters(bench.NCU_CAPTURE["tile"], 2, cells)
+    assert got["dram_bytes"] == 1.5e8 * 4  # scaled by cells
+    assert got["thread_inst_per_cell"] == 510.0 and got["issue_active_pct"] == 61.0
+    assert bench.ncu_counters(bench.NCU_CAPTURE["tile"] + 1, 2, cells) is None
+    monkeypatch.setitem(bench.NCU_CAPTURE, "sha256", "0" * 64)
+    assert bench.ncu_counters(bench.NCU_CAPTURE["tile"], 2, cells) is None
+    monkeypatch.setitem(bench.NCU_CAPTURE, "sha256", None)
+    assert bench.ncu_counters(bench.NCU_CAPTURE["tile"], 2, cells) is None
