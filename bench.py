@@ -38,18 +38,22 @@ WORKLOAD = "synthetic coastal DEM 4096x4096, dx=5 m, shelf ramp -200 m to 0 + fr
 # also read U^n for the RK combination.  108 B per cell-update over a step.
 BYTES_PER_CELL_STAGE = {1: 28.0, 2: 40.0, 3: 40.0}
 
-# ncu counters of one launch of each RK stage of the FP32 stage kernel on the
-# bench's own workload (4096 x 4096 coastal DEM, tile shape 7):
-# dram__bytes_read.sum + dram__bytes_write.sum (bytes per launch), executed
-# thread instructions per cell (smsp__thread_inst_executed.sum / cells) and
-# issue-active percent (sm__inst_issued.avg.pct_of_peak_sustained_active).
-# Reported only while the kernel's sources hash to the captured version (its
-# device code, its translation unit and the tile-shape table); None until a
-# capture of the current kernel is recorded.
-NCU_CAPTURE = {"tile": 7, "cells": 4096 * 4096, "profile": None,
-               "dram_bytes": None, "thread_inst_per_cell": None, "issue_active_pct": None,
+# ncu counters of one launch of each RK stage of the FP32 stage kernel (tile
+# shape 7): dram__bytes_read.sum + dram__bytes_write.sum per launch on the
+# bench's own workload (4096 x 4096 coastal DEM, `cells`), and, from the
+# 2048 x 2048 case of the same workload, executed thread instructions per cell
+# (smsp__thread_inst_executed.sum / cells) and the issue-active percent
+# (sm__inst_issued.avg.pct_of_peak_sustained_active).  Reported only while the
+# kernel's sources hash to the captured version (its device code, its
+# translation unit and the tile-shape table).
+NCU_CAPTURE = {"tile": 7, "cells": 4096 * 4096,
+               "profile": "profiles/stage_kernel_f32_coastal_dem_4096_dram.md, "
+                          "profiles/stage_kernel_f32_coastal_dem_2048_pipes.md",
+               "dram_bytes": {1: 269296896 + 166181888, 2: 470734848 + 175684608, 3: 470715648 + 165232128},
+               "thread_inst_per_cell": {1: 564.2, 2: 592.2, 3: 598.9},
+               "issue_active_pct": {1: 61.73, 2: 62.61, 3: 63.12},
                "sources": ("swe_core.cuh", "swe_kernels.cu", "swe_launch.h:SWE_SHAPES"),
-               "sha256": None}
+               "sha256": "c63ef1b9f770248666f5584979be6fd66dc55600a5d9f976970f4534a1d49d45"}
 
 
 def kernel_sources_sha256() -> str:

@@ -62,7 +62,8 @@ def test_ingested_dem_against_the_oracle(tmp_path, precision):
         s.step(steps)
         h, hu, hv = s.get_state()
         d = s.diagnostics()
-    assert d["steps"] == steps and d["t"] == pytest.approx(rd["t"], rel=1e-12)
+    # FP32 wave speeds set an FP32-rounded CFL step
+    assert d["steps"] == steps and d["t"] == pytest.approx(rd["t"], rel=1e-12 if precision == swe.F64 else 1e-5)
     assert rd["boundary_mass"] > 0  # the wave entered
     if precision == swe.F64:
         assert np.abs(h - ref.h).max() <= 1e-10
