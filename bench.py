@@ -237,9 +237,12 @@ def fp64_bench(swe, W, torch, sc, steps: int = 10):
 
 
 def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: float = 20.0,
-                  policies=("srpt", "all")):
-    """C5 (bounded sample): Poisson requests, N log-uniform in [256, 2048],
-    coast and hills as the ensemble, 150 GB budget, continuous batching."""
+                  policies=("srpt", "all"), fill_waves: int = 4):
+    """C5: Poisson requests, N log-uniform in [256, 2048], coast and hills as
+    the ensemble, 150 GB budget, continuous batching.  The default bench line
+    runs a bounded sample (count requests per rate, `horizon` simulated
+    seconds each); --serving-sweep runs the configuration's rates and 600 s
+    horizon."""
     from paper_2301_12010_gb300.serve import Server
     stream = torch.cuda.current_stream().cuda_stream
     # the batch tile shape, tuned on grids of the request mix
@@ -251,12 +254,18 @@ def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: fl
         for rate in rates:
             reqs = W.serving_requests(rate=rate, count=count, horizon=horizon)
             with Server(reqs[0].scenario, nslots=64, budget_bytes=150 << 30, k_steps=50, stream=stream,
-                        policy=policy, tile=tile) as srv:
+                        policy=policy, tile=tile, fill_cells=152 * fill_waves * 3072) as srv:
                 rep = srv.serve(reqs)
             res["%g_req_per_s" % rate] = rep.summary()
         out[policy] = res
-    return {"sample": "%d requests per rate, %g s simulated horizon (config horizon 600 s)" % (count, horizon),
-            "policies": {"srpt": "shortest remaining work first, enough requests per launch to fill the GPU",
+    full = horizon >= 600.0 and count >= 50
+    return {"sample": "%d requests per rate at %s req/s, %g s simulated horizon per request%s"
+                      % (count, ", ".join("%g" % r for r in rates), horizon,
+                         "" if full else " (a bounded sample: configuration 5 asks for 1-50 req/s, at least 200 "
+                                         "requests per rate and a 600 s horizon; python bench.py --serving-sweep "
+                                         "runs 1, 5, 20 and 50 req/s at the 600 s horizon)"),
+            "policies": {"srpt": "shortest remaining work first, enough requests per launch to fill %d waves of "
+                                 "tiles" % fill_waves,
                          "all": "every live request advances each launch"},
             "batch_tile": tile, "rates": out.get("srpt"), "rates_all": out.get("all")}
 
@@ -427,11 +436,15 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--serving-sweep", default=None, metavar="RATES",
-                    help="only the serving measurement, at these comma-separated request rates (req/s); "
-                         "prints one JSON object, not a bench line")
-    ap.add_argument("--serving-count", type=int, default=200, help="requests per rate of --serving-sweep")
-    ap.add_argument("--serving-horizon", type=float, default=20.0, help="simulated seconds per request")
+    ap.add_argument("--serving-sweep", default=None, metavar="RATES", nargs="?", const="1,5,20,50",
+                    help="only the serving measurement, at these comma-separated request rates (req/s; "
+                         "default 1,5,20,50); prints one JSON object, not a bench line")
+    ap.add_argument("--serving-count", type=int, default=50, help="requests per rate of --serving-sweep")
+    ap.add_argument("--serving-horizon", type=float, default=600.0,
+                    help="simulated seconds per request of --serving-sweep (configuration 5: 600)")
+    ap.add_argument("--serving-policies", default="srpt", help="comma-separated: srpt, all")
+    ap.add_argument("--serving-fill-waves", type=int, default=4,
+                    help="srpt: waves of tiles (152 x this x 3072 cells) each launch advances at least")
     ap.add_argument("--profile-batch", action="store_true",
                     help="only one RK3 step of the batch kernel on the 64-scenario ensemble (contiguous order) "
                          "and on one walled 2048x2048 DEM (strided order), then the same DEM by the "
@@ -456,7 +469,7 @@ def main():
         torch.cuda.set_device(0)
         rates = tuple(float(r) for r in args.serving_sweep.split(","))
         res = serving_bench(swe, W, torch, rates=rates, count=args.serving_count, horizon=args.serving_horizon,
-                            policies=("srpt",))
+                            policies=tuple(args.serving_policies.split(",")), fill_waves=args.serving_fill_waves)
         print(json.dumps({"serving_sweep": res}))
         return 0
 

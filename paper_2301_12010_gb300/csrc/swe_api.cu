@@ -52,6 +52,7 @@ struct swe_handle {
   void *h[3] = {}, *hu[3] = {}, *hv[3] = {};
   double *staging = nullptr;      // ny*nx doubles: host-format transfers
   DevScalars *sc = nullptr;
+  DevPartials *cta = nullptr;     // per-CTA partials of the clamp and edge volumes
   double *partials = nullptr;     // kMassBlocks + 1 (last: mass result)
   BoxMaps maps[3] = {};           // tensor maps of the halo-box copies, per RK stage
   cudaGraphExec_t graph = nullptr;
@@ -188,7 +189,7 @@ int after_state_change(swe_handle *s) {
   cudaError_t e = cudaMemcpyAsync(&t, &s->sc->t, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_check(s, e);
-  e = reset_scalars(s->sc, t, s->cfl_dev > 0 ? s->cfl_dev : 0.4, 0.0, s->stream);
+  e = reset_scalars(s->sc, s->cta, t, s->cfl_dev > 0 ? s->cfl_dev : 0.4, 0.0, s->stream);
   if (e == cudaSuccess)
     e = s->prec == SWE_F64 ? state_stats<double>(field_of<double>(s), s->phys, s->sc, s->stream)
                            : state_stats<float>(field_of<float>(s), s->phys, s->sc, s->stream);
@@ -320,8 +321,9 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   const size_t plane_al = (plane + 255) & ~(size_t)255;
   const size_t stag = ((sizeof(double) * (size_t)s->nx * s->ny) + 255) & ~(size_t)255;
   const size_t scal = (sizeof(DevScalars) + 255) & ~(size_t)255;
+  const size_t ctap = (sizeof(DevPartials) + 255) & ~(size_t)255;
   const size_t part = sizeof(double) * (kMassBlocks + 1);
-  const size_t total = plane_al * 10 + stag + scal + part;
+  const size_t total = plane_al * 10 + stag + scal + ctap + part;
   cudaError_t e = dev_malloc(&s->mem, total);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
@@ -337,6 +339,7 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   }
   s->staging = (double *)q; q += stag;
   s->sc = (DevScalars *)q; q += scal;
+  s->cta = (DevPartials *)q; q += ctap;
   s->partials = (double *)q;
 
   int rc = SWE_OK;
@@ -362,7 +365,7 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
     rc = cuda_check(s, e);
   }
   if (rc == SWE_OK) rc = cuda_check(s, cudaMemsetAsync(s->mem, 0, plane_al * 10, s->stream));
-  if (rc == SWE_OK) rc = cuda_check(s, reset_scalars(s->sc, 0.0, 0.4, 0.0, s->stream));
+  if (rc == SWE_OK) rc = cuda_check(s, reset_scalars(s->sc, s->cta, 0.0, 0.4, 0.0, s->stream));
   if (rc == SWE_OK) rc = upload_field(s, bathymetry, s->b, false);
   if (rc == SWE_OK) rc = cuda_check(s, cudaStreamSynchronize(s->stream));
   if (rc != SWE_OK) {
@@ -551,8 +554,7 @@ int swe_mass(swe_handle *s, double *mass, double *clamp_mass) {
           : swe::mass<float>((const float *)s->h[0], (const float *)s->b, s->phys.z_ref, s->nx, s->ny, s->pitch, s->dx * s->dy, s->partials, s->partials + kMassBlocks, s->stream);
   double r[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&r[0], s->partials + kMassBlocks, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&r[1], &s->sc->clamp_mass, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e == cudaSuccess) e = read_volumes(s->cta, &r[1], nullptr, s->stream);
   if (e != cudaSuccess) return cuda_check(s, e);
   if (mass) *mass = r[0];
   if (clamp_mass) *clamp_mass = r[1];
@@ -564,7 +566,7 @@ int swe_diagnostics(swe_handle *s, swe_diag *d) {
   if (!s || !d) return SWE_EINVAL;
   DevScalars h;
   cudaError_t e = cudaMemcpyAsync(&h, s->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e == cudaSuccess) e = read_volumes(s->cta, &d->clamp_mass, &d->boundary_mass, s->stream);
   if (e != cudaSuccess) return cuda_check(s, e);
   auto dbl = [](unsigned long long u) { double x; std::memcpy(&x, &u, 8); return x; };
   d->t = h.t;
@@ -572,8 +574,6 @@ int swe_diagnostics(swe_handle *s, swe_diag *d) {
   d->last_dt = h.dt;
   d->alpha_x = dbl(h.alpha[0][0]);
   d->alpha_y = dbl(h.alpha[0][1]);
-  d->clamp_mass = h.clamp_mass;
-  d->boundary_mass = h.boundary_mass;
   const unsigned long long rn = h.runup_now[(h.steps + 1) & 1];
   d->runup_now = rn ? dbl(rn) : -INFINITY;
   d->runup_max = h.runup_max ? dbl(h.runup_max) : -INFINITY;

@@ -2,6 +2,7 @@
 // batch paths: host-format conversion, per-state statistics (wave speeds,
 // runup), scalar resets and the fixed-order FP64 mass reduction.
 #include <cmath>
+#include <new>
 
 #include "swe_launch.h"
 
@@ -57,8 +58,13 @@ __global__ void k_set_cfl(DevScalars *sc, double cfl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) sc->cfl = cfl;
 }
 
-__global__ void k_reset(DevScalars *sc, double t, double cfl, double t_end) {
+__global__ void k_reset(DevScalars *sc, DevPartials *part, double t, double cfl, double t_end) {
+  for (int b = threadIdx.x; b < kPartSlots; b += blockDim.x) {
+    part->clamp[b] = 0.0;
+    part->edge[b] = 0.0;
+  }
   if (threadIdx.x == 0 && blockIdx.x == 0) {
+    sc->part = part;
     for (int s = 0; s < 3; ++s) sc->alpha[s][0] = sc->alpha[s][1] = 0ull;
     sc->dt = 0.0;
     sc->t = t;
@@ -66,8 +72,6 @@ __global__ void k_reset(DevScalars *sc, double t, double cfl, double t_end) {
     sc->steps = 0;
     sc->runup_now[0] = sc->runup_now[1] = 0ull;
     sc->runup_max = 0ull;
-    sc->clamp_mass = 0.0;
-    sc->boundary_mass = 0.0;
     sc->t_end = t_end;
     sc->cfl = cfl;
     sc->status = 0u;
@@ -230,9 +234,27 @@ const void *pinned_device_ptr(const void *p, size_t bytes) {
   return a0.devicePointer;
 }
 
-cudaError_t reset_scalars(DevScalars *sc, double t, double cfl, double t_end, cudaStream_t st) {
-  k_reset<<<1, 32, 0, st>>>(sc, t, cfl, t_end);
+cudaError_t reset_scalars(DevScalars *sc, DevPartials *part, double t, double cfl, double t_end, cudaStream_t st) {
+  k_reset<<<1, 256, 0, st>>>(sc, part, t, cfl, t_end);
   return cudaGetLastError();
+}
+
+cudaError_t read_volumes(const DevPartials *part, double *clamp, double *edge, cudaStream_t st) {
+  double tot[2] = {0.0, 0.0};
+  DevPartials *h = new (std::nothrow) DevPartials;
+  if (!h) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMemcpyAsync(h, part, sizeof(DevPartials), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    for (int b = 0; b < kPartSlots; ++b) {  // CTA order
+      tot[0] += h->clamp[b];
+      tot[1] += h->edge[b];
+    }
+    if (clamp) *clamp = tot[0];
+    if (edge) *edge = tot[1];
+  }
+  delete h;
+  return e;
 }
 
 cudaError_t set_cfl(DevScalars *sc, double cfl, cudaStream_t st) {

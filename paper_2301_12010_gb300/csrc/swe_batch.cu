@@ -56,6 +56,7 @@ struct swe_batch {
   cudaStream_t stream = nullptr, cap = nullptr;
   std::vector<Slot> slots;
   DevScalars *d_sc = nullptr;          // one per slot
+  DevPartials *d_cta = nullptr;        // one per slot: per-CTA partials of the clamp volume
   BatchSlot<float> *d_table = nullptr; // live slots, work-list order
   BatchCtl *d_ctl = nullptr;
   double *d_part = nullptr;            // mass partials + result
@@ -183,6 +184,7 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
   b->slots.resize(nslots);
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = dev_malloc((void **)&b->d_sc, sizeof(DevScalars) * nslots);
+  if (e == cudaSuccess) e = dev_malloc((void **)&b->d_cta, sizeof(DevPartials) * nslots);
   if (e == cudaSuccess) e = dev_malloc((void **)&b->d_table, sizeof(BatchSlot<float>) * nslots);
   if (e == cudaSuccess) e = dev_malloc((void **)&b->d_ctl, sizeof(BatchCtl));
   if (e == cudaSuccess) e = dev_malloc((void **)&b->d_part, sizeof(double) * (kMassBlocks + 1));
@@ -190,7 +192,7 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
   if (e == cudaSuccess) e = batch_resident(b->tile, &per_sm);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+  if (e == cudaSuccess && (per_sm < 1 || per_sm * sms > kPartSlots)) e = cudaErrorInvalidConfiguration;
   if (e != cudaSuccess) {
     int rc = bfail(b, e);
     swe_batch_destroy(b);
@@ -270,7 +272,7 @@ int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, co
     if (e == cudaSuccess)
       e = import_plane<float>(in, true, dsts[f], f == 1 ? bplane : nullptr, zr, sl.nx, sl.ny, sl.pitch, b->stream);
   }
-  if (e == cudaSuccess) e = reset_scalars(b->d_sc + s, 0.0, b->cfl, t_end, b->stream);
+  if (e == cudaSuccess) e = reset_scalars(b->d_sc + s, b->d_cta + s, 0.0, b->cfl, t_end, b->stream);
   if (e == cudaSuccess) e = state_stats<float>(sl.fd, sl.p, b->d_sc + s, b->stream);
   if (e != cudaSuccess) {
     cudaFreeAsync(sl.mem, b->stream);
@@ -376,7 +378,7 @@ int swe_batch_diagnostics(swe_batch *b, int32_t slot, swe_diag *d) {
   if (!valid_slot(b, slot) || !d) return SWE_EINVAL;
   DevScalars h;
   cudaError_t e = cudaMemcpyAsync(&h, b->d_sc + slot, sizeof(h), cudaMemcpyDeviceToHost, b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = read_volumes(b->d_cta + slot, &d->clamp_mass, &d->boundary_mass, b->stream);
   if (e != cudaSuccess) return bfail(b, e);
   auto dbl = [](unsigned long long u) { double x; std::memcpy(&x, &u, 8); return x; };
   d->t = h.t;
@@ -384,8 +386,6 @@ int swe_batch_diagnostics(swe_batch *b, int32_t slot, swe_diag *d) {
   d->last_dt = h.dt;
   d->alpha_x = dbl(h.alpha[0][0]);
   d->alpha_y = dbl(h.alpha[0][1]);
-  d->clamp_mass = h.clamp_mass;
-  d->boundary_mass = h.boundary_mass;
   const unsigned long long rn = h.runup_now[(h.steps + 1) & 1];
   d->runup_now = rn ? dbl(rn) : -INFINITY;
   d->runup_max = h.runup_max ? dbl(h.runup_max) : -INFINITY;
@@ -463,6 +463,7 @@ int swe_batch_destroy(swe_batch *b) {
     if (sl.mem) cudaFreeAsync(sl.mem, b->stream);
   cudaStreamSynchronize(b->stream);
   if (b->d_sc) cudaFree(b->d_sc);
+  if (b->d_cta) cudaFree(b->d_cta);
   if (b->d_table) cudaFree(b->d_table);
   if (b->d_ctl) cudaFree(b->d_ctl);
   if (b->d_part) cudaFree(b->d_part);

@@ -43,6 +43,20 @@ namespace swe {
 enum : int { BC_WALL = 0, BC_INFLOW = 1, BC_PERIODIC = 2 };
 enum : unsigned { ST_NONFINITE = 1u, ST_DRY = 2u, ST_TIMEOUT = 4u };
 
+// Slots for per-CTA sums of the clamp and edge volumes: at least the CTAs of
+// any persistent launch (resident CTAs x SMs).
+constexpr int kPartSlots = 1024;
+
+// Per-CTA running sums of one scenario (device memory, FP64): CTA b adds its
+// share of every RK stage to slot b, in time order, and only CTA b touches
+// slot b; the host adds the slots in CTA order when it reads the totals.  The
+// totals thus do not depend on the order in which CTAs finish (as atomic adds
+// would), and no kernel waits for another CTA.
+struct DevPartials {
+  double clamp[kPartSlots];  // RK-weighted clamp volume (m^3)
+  double edge[kPartSlots];   // RK-weighted edge inflow volume (m^3)
+};
+
 // Per-scenario device scalars (one struct per handle or batch slot).
 struct DevScalars {
   unsigned long long alpha[3][2];   // wave speeds (x, y) per stage slot, bits of a double
@@ -52,14 +66,15 @@ struct DevScalars {
   long long steps;                  // steps taken
   unsigned long long runup_now[2];  // bits of a double, per step parity; 0 = no wet land cell
   unsigned long long runup_max;     // bits of a double; 0 = none
-  double clamp_mass;                // RK-weighted clamp additions, m^3
-  double boundary_mass;             // RK-weighted edge inflow, m^3
+  double clamp_mass;                // unused: the clamp and edge volumes live in the per-CTA slots
+  double boundary_mass;             // (DevPartials), which the host adds in CTA order
   double t_end;                     // > 0: last step truncated at t_end; no step once t >= t_end
   double cfl;                       // CFL number when fixed_dt <= 0
   unsigned status;                  // ST_* flags
   unsigned running;                 // 1 while the current step runs (set by stage 1)
   unsigned parity;                  // steps & 1 of the running step
   unsigned active;                  // batch: slot is live
+  DevPartials *part;                // this scenario's per-CTA clamp and edge volumes (set by the host)
 };
 
 // Derived constants of the stage arithmetic, precomputed on the host in the
@@ -931,8 +946,8 @@ __device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, boo
 // Block reduction of the per-thread accumulators and device-scope
 // publication for one scenario.
 template <typename T, int NT, int STAGE>
-__device__ __forceinline__ void publish(const Phys &p, DevScalars *sc, bool lead, RedSmem &red, double dt,
-                                        const Acc<T> &acc) {
+__device__ __noinline__ void publish(const Phys &p, DevScalars *sc, bool lead, RedSmem &red, double dt,
+                                     const Acc<T> &acc) {
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   // in the state's precision (FP64 arithmetic is slow on this part); one
   // conversion per published value
@@ -963,8 +978,9 @@ __device__ __forceinline__ void publish(const Phys &p, DevScalars *sc, bool lead
     atomicMax(&sc->alpha[STAGE % 3][1], dbits((double)my));
     constexpr double wgt = (STAGE == 3) ? 1.0 : (STAGE == 2 ? 2.0 / 3.0 : 1.0 / 6.0);
     constexpr double wfl = (STAGE == 3) ? 2.0 / 3.0 : 1.0 / 6.0;
-    if (dsum != T(0)) atomicAdd(&sc->clamp_mass, (wgt * p.area) * (double)dsum);
-    if (fsum != T(0)) atomicAdd(&sc->boundary_mass, wfl * dt * (double)fsum);
+    // this CTA's own FP64 slot (no other CTA writes it: deterministic totals)
+    if (dsum != T(0)) sc->part->clamp[blockIdx.x] += (wgt * p.area) * (double)dsum;
+    if (fsum != T(0)) sc->part->edge[blockIdx.x] += wfl * dt * (double)fsum;
     if (STAGE == 3 && rmax > T(0)) {
       const unsigned long long rb = dbits((double)rmax);
       atomicMax(&sc->runup_now[__ldcg(&sc->parity)], rb);

@@ -61,6 +61,7 @@ cudaError_t SWE_CAT(launch_shape_, SWE_SHAPE)<Real>(const Field<Real> &fd, const
   const int ntiles = ((fd.nx + P::TX - 1) / P::TX) * ((fd.ny + P::TY - 1) / P::TY);
   int grid = g_resident * (g_sms > 0 ? g_sms : 1);
   if (grid > ntiles) grid = ntiles;
+  if (grid > kPartSlots) return cudaErrorInvalidConfiguration;  // one partial slot per CTA
   const StageIO<Real> io = io_of(fd, stage);
   const BoxMaps &m = maps[stage - 1];
   switch (stage) {

@@ -61,7 +61,7 @@ def test_failed_readback_buffers_leave_the_handle_usable():
 
 def test_failed_batch_creation_and_admission_leave_no_trace():
     scs = small_coasts(3)
-    for n in (1, 2, 3, 4):  # each device allocation of swe_batch_create
+    for n in (1, 2, 3, 4, 5):  # each device allocation of swe_batch_create
         swe.debug_fail_alloc(n)
         with pytest.raises(swe.SweError) as ei:
             swe.Batch(4, GB, scs[0], stream=stream())

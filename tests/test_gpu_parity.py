@@ -322,3 +322,19 @@ def test_checkpoint_resume_is_bitwise():
         tc, _ = c.time()
     assert np.array_equal(ha, hc) and np.array_equal(hua, huc) and np.array_equal(hva, hvc)
     assert ta == tc
+
+
+@pytest.mark.parametrize("precision", [swe.F32, swe.F64])
+def test_diagnostic_volumes_are_the_same_run_to_run(precision):
+    # the clamp volume (wet/dry bowl) and the edge inflow volume (inflow DEM)
+    # are sums over all CTAs: per-CTA partials added in CTA order make them
+    # bit-identical from run to run, whatever order the CTAs finish in
+    cases = [(W.parabolic_bowl(nx=400, ny=40), 150, "clamp_mass"),
+             (W.coastal_dem(n=192, dx=100.0, t0=500.0), 40, "boundary_mass")]
+    for sc, steps, key in cases:
+        seen = []
+        for _ in range(3):
+            with swe.Solver(sc, precision=precision, stream=stream()) as s:
+                s.step(steps)
+                seen.append(s.diagnostics()[key])
+        assert seen[0] != 0.0 and seen[0] == seen[1] == seen[2], (key, seen)

@@ -102,3 +102,31 @@ def test_paused_slot_keeps_its_state_and_resumes_bit_for_bit():
         assert ref.diagnostics(s)["steps"] == steps_b == 9
     for x, y in zip(got, want):
         assert np.array_equal(x, y)
+
+
+def test_served_results_match_the_fp64_oracle():
+    # three requests of the serving mix (coast, hills, N-wave; small grids)
+    # served together, each result against the FP64 oracle run to the same
+    # horizon: relative L2 of the surface anomaly and of the momentum <= 1e-4
+    # (FP32), runup within 1 cm
+    import oracle
+    reqs = small_requests(3, rate=1000.0, horizon=4.0, seed=11)
+    with Server(reqs[0].scenario, nslots=3, budget_bytes=1 << 30, k_steps=20, stream=stream(),
+                keep_state=True, policy="srpt", fill_cells=10 ** 9) as srv:
+        rep = srv.serve(reqs)
+    assert sorted(r.index for r in rep.results) == [0, 1, 2] and rep.max_live >= 2
+    for res in rep.results:
+        sc = reqs[res.index].scenario
+        assert res.status == "done" and res.t == sc.t_end
+        ref = oracle.Simulation(sc)
+        ref.run_until(sc.t_end)
+        assert ref.t == sc.t_end
+        h, hu, hv = res.state
+        et = np.where(h >= sc.h_dry, h + sc.b, 0.0)
+        er = np.where(ref.h >= sc.h_dry, ref.h + sc.b, 0.0)
+        rel = lambda a, r: float(np.sqrt(((a - r) ** 2).sum() / (r ** 2).sum()))
+        assert rel(et, er) <= 1e-4, (res.index, rel(et, er))
+        assert rel(hu, ref.hu) <= 1e-4 and rel(hv, ref.hv) <= 1e-4, res.index
+        rd = ref.diag()["runup_max"]
+        if rd > -np.inf:
+            assert abs(res.runup_max - rd) <= 0.01
