@@ -194,6 +194,22 @@ const char *swe_strerror(int code);
 /* Free the handle and its device memory.  NULL-safe; returns SWE_OK. */
 int swe_destroy(swe_handle *s);
 
+/* 1 if this library is the checked build (libswe_checked.so, compiled with
+ * SWE_CHECKED), else 0.  The checked build compares every index into a
+ * tile's shared-memory halo box and flux buffer and into a global plane with
+ * its extent before the access; an index out of range is recorded (the first
+ * one) and the access skipped, with no trap.  It stands in for a memory
+ * checker on devices where none can run.  No counterpart in the paper. */
+int swe_checked_build(void);
+
+/* The handle's check word (checked build): 0 if no index was out of range so
+ * far, else bit 63 set, the access site in bits 40..47 (1 ghost write, 2 wall
+ * mirror read, 3 periodic read, 4 x-pass box chunk, 5 box cell, 6/7 x-pass
+ * epilogue box/flux buffer, 8/9 y-pass epilogue box/flux buffer, 10 output
+ * plane, 11 U^n read) and the index in bits 0..39.  Always 0 in the normal
+ * build.  Reset by swe_set_state.  Synchronises. */
+int swe_check_status(swe_handle *s, uint64_t *word);
+
 /* Number of compiled tile shapes and the shape of entry k (1-based). */
 int swe_tile_count(void);
 int swe_tile_shape(int k, int32_t *tx, int32_t *ty, int32_t *threads);
@@ -280,6 +296,10 @@ int swe_batch_select(swe_batch *b, const int32_t *slots, int32_t n);
  * read-back.  Synchronises. */
 int swe_batch_times(swe_batch *b, double *t);
 
+/* The check word of a live slot (see swe_check_status); 0 in the normal
+ * build.  Synchronises. */
+int swe_batch_check_status(swe_batch *b, int32_t slot, uint64_t *word);
+
 /* Device bytes in use by live slots and the budget. */
 int swe_batch_memory(swe_batch *b, size_t *used, size_t *budget);
 
@@ -295,6 +315,53 @@ int swe_batch_set_barrier(swe_batch *b, double timeout_s, int32_t extra_arrivals
 
 /* Free the batch and all slots.  NULL-safe. */
 int swe_batch_destroy(swe_batch *b);
+
+/* ----------------------------------------------------------------------
+ * Row-partitioned domain: the paper's parallel scheme ("TPU
+ * implementation", Table 1: the domain split among TPU cores, halos
+ * exchanged every RK stage, the wave speed reduced across cores).  The grid
+ * is cut along y into nparts strips of whole rows (boundaries on multiples
+ * of 32 rows when strips hold 64 rows or more; swe_strip_bounds); each strip
+ * keeps three halo rows above and
+ * below.  Every RK stage runs the stage kernel over each strip and then
+ * copies every strip's three boundary rows of the stage output into its
+ * neighbours' halo rows; the wave speeds of a stage are one maximum over all
+ * strips.  The result equals the undivided grid's (swe_create) bit for bit.
+ * The strips run on the calling device, one after another on one stream.
+ * The y sides must be walls (SWE_EINVAL otherwise); x sides as swe_create.
+ * Arrays are full-grid [ny][nx] host FP64, as for swe_create.
+ * ---------------------------------------------------------------------- */
+typedef struct swe_multi swe_multi;
+
+/* Strip k (0-based) of a partition of ny rows into nparts strips: first row
+ * and row count.  SWE_EINVAL if a strip would hold fewer than 3 rows.  Host
+ * only (no device work). */
+int swe_strip_bounds(int32_t ny, int32_t nparts, int32_t k, int32_t *row0, int32_t *rows);
+
+/* Create a row-partitioned solver (as swe_create, nparts strips). */
+int swe_multi_create(const swe_grid *grid, double dx, double dy, const double *bathymetry,
+                     const swe_params *params, int32_t nparts, swe_multi **out);
+
+/* Set the state (host FP64 [ny][nx], copied) and exchange the halos.  Synchronous. */
+int swe_multi_set_state(swe_multi *m, const double *h, const double *hu, const double *hv);
+
+/* Set the simulated time; resets the step count. */
+int swe_multi_set_time(swe_multi *m, double t);
+
+/* Enqueue n RK3 steps (asynchronous, replayed from a captured CUDA graph). */
+int swe_multi_step(swe_multi *m, int32_t n, double cfl);
+
+/* Gather the state into host FP64 arrays [ny][nx].  Synchronises. */
+int swe_multi_get_state(swe_multi *m, double *h, double *hu, double *hv);
+
+/* Water volume sum(h) dx dy (FP64; per strip in fixed order, then strip order). */
+int swe_multi_mass(swe_multi *m, double *mass);
+
+/* Diagnostics of the whole domain (as swe_diagnostics).  Synchronises. */
+int swe_multi_diagnostics(swe_multi *m, swe_diag *d);
+
+/* Free the solver.  NULL-safe. */
+int swe_multi_destroy(swe_multi *m);
 
 /* Allocation-free water volume of a caller-owned device depth field.
  * The paper has no counterpart: this entry point exists for callers that

@@ -17,7 +17,9 @@ from typing import Dict, Optional, Sequence, Tuple
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libswe.so")
+# SWE_LIB_VARIANT=checked loads the index-checked build (libswe_checked.so)
+LIB_PATH = os.path.join(_PKG, "libswe_checked.so" if os.environ.get("SWE_LIB_VARIANT") == "checked"
+                        else "libswe.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EBUDGET, EFULL = range(8)
 F32, F64 = 0, 1
@@ -106,6 +108,20 @@ def _load() -> ctypes.CDLL:
                               ctypes.POINTER(ctypes.c_int32), dp]),
         "swe_autotune_lookup": (ip, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
         "swe_debug_fail_alloc": (ip, [ctypes.c_int32]),
+        "swe_checked_build": (ip, []),
+        "swe_strip_bounds": (ip, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int32)]),
+        "swe_multi_create": (ip, [ctypes.POINTER(Grid), ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(Params),
+                                  ctypes.c_int32, ctypes.POINTER(H)]),
+        "swe_multi_set_state": (ip, [H, dp, dp, dp]),
+        "swe_multi_set_time": (ip, [H, ctypes.c_double]),
+        "swe_multi_step": (ip, [H, ctypes.c_int32, ctypes.c_double]),
+        "swe_multi_get_state": (ip, [H, dp, dp, dp]),
+        "swe_multi_mass": (ip, [H, dp]),
+        "swe_multi_diagnostics": (ip, [H, ctypes.POINTER(Diag)]),
+        "swe_multi_destroy": (ip, [H]),
+        "swe_check_status": (ip, [H, ctypes.POINTER(ctypes.c_uint64)]),
+        "swe_batch_check_status": (ip, [H, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -252,6 +268,12 @@ class Solver:
     def status(self) -> int:
         return int(lib.swe_status(self._h))
 
+    def check_word(self) -> int:
+        """Checked build: the first out-of-range index recorded (0: none)."""
+        w = ctypes.c_uint64()
+        _check(lib.swe_check_status(self._h, ctypes.byref(w)), "swe_check_status")
+        return int(w.value)
+
     def set_time(self, t: float) -> None:
         _check(lib.swe_set_time(self._h, float(t)), "swe_set_time")
 
@@ -304,6 +326,72 @@ def autotune(shapes, precision: int = F32, batch: bool = False, steps: int = 10)
     _check(lib.swe_autotune(grids, len(shapes), int(precision), 1 if batch else 0, int(steps), ctypes.byref(best), ms),
            "swe_autotune")
     return best.value, list(ms)
+
+
+def strip_bounds(ny: int, nparts: int):
+    """[(first row, rows)] of the row partition swe_multi uses (host only)."""
+    out = []
+    for k in range(int(nparts)):
+        r0, n = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.swe_strip_bounds(int(ny), int(nparts), k, ctypes.byref(r0), ctypes.byref(n)), "swe_strip_bounds")
+        out.append((r0.value, n.value))
+    return out
+
+
+class Multi:
+    """One scenario on a row-partitioned domain (the paper's per-core strips
+    with halo exchange every RK stage), through the C ABI."""
+
+    def __init__(self, sc, nparts: int, precision: int = F32, stream: Optional[int] = None, tile: int = 0):
+        self.sc = sc
+        self.nx, self.ny = sc.nx, sc.ny
+        self._m = ctypes.c_void_p()
+        b = np.ascontiguousarray(sc.b, dtype=np.float64)
+        self.params = params_for(sc, precision, stream, tile)
+        _check(lib.swe_multi_create(ctypes.byref(Grid(sc.nx, sc.ny)), float(sc.dx), float(sc.dy), _dp(b),
+                                    ctypes.byref(self.params), int(nparts), ctypes.byref(self._m)), "swe_multi_create")
+        if sc.t0:
+            _check(lib.swe_multi_set_time(self._m, float(sc.t0)), "swe_multi_set_time")
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (sc.h, sc.hu, sc.hv)]
+        _check(lib.swe_multi_set_state(self._m, *[_dp(x) for x in a]), "swe_multi_set_state")
+
+    def close(self) -> None:
+        if self._m:
+            lib.swe_multi_destroy(self._m)
+            self._m = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, n: int, cfl: Optional[float] = None) -> None:
+        c = self.sc.cfl if cfl is None else cfl
+        _check(lib.swe_multi_step(self._m, int(n), float(c)), "swe_multi_step")
+
+    def get_state(self):
+        out = tuple(np.empty((self.ny, self.nx), dtype=np.float64) for _ in range(3))
+        _check(lib.swe_multi_get_state(self._m, *[_dp(x) for x in out]), "swe_multi_get_state")
+        return out
+
+    def mass(self) -> float:
+        m = ctypes.c_double()
+        _check(lib.swe_multi_mass(self._m, ctypes.byref(m)), "swe_multi_mass")
+        return m.value
+
+    def diagnostics(self, check: bool = True) -> Dict[str, float]:
+        d = Diag()
+        rc = lib.swe_multi_diagnostics(self._m, ctypes.byref(d))
+        if check:
+            _check(rc, "swe_multi_diagnostics")
+        return _diag_dict(d)
 
 
 def slot_bytes(nx: int, ny: int) -> int:
@@ -385,6 +473,12 @@ class Batch:
 
     def status(self) -> int:
         return int(lib.swe_batch_status(self._b))
+
+    def check_word(self, slot: int) -> int:
+        """Checked build: the slot's first out-of-range index recorded (0: none)."""
+        w = ctypes.c_uint64()
+        _check(lib.swe_batch_check_status(self._b, int(slot), ctypes.byref(w)), "swe_batch_check_status")
+        return int(w.value)
 
     def get_state(self, slot: int):
         ny, nx = self.shapes[slot]

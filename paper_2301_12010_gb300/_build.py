@@ -1,7 +1,10 @@
 """In-tree build of libswe.so for sm_103a (nvcc, no cmake).
 
 Translation units compile in parallel into ``_build/`` and link into
-``paper_2301_12010_gb300/libswe.so``; both are git-ignored.
+``paper_2301_12010_gb300/libswe.so``; both are git-ignored.  The checked
+build (``build(checked=True)``: every device index compared with its extent
+before the access, SWE_CHECKED) goes to ``_build_checked/`` and
+``libswe_checked.so``.
 """
 from __future__ import annotations
 
@@ -18,6 +21,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libswe.so")
+OUT_DIR_CHECKED = os.path.join(ROOT, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libswe_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 
@@ -41,6 +46,7 @@ UNITS: List[Tuple[str, List[str], str]] = (
     + [("swe_batch_kernels.cu", ["-DSWE_SHAPE=%d" % k], "swe_batch_kernels_s%d.o" % k) for k in SHAPES]
     + [("swe_shapes.cu", [], "swe_shapes.o"), ("swe_api.cu", [], "swe_api.o"), ("swe_aux.cu", [], "swe_aux.o"),
        ("swe_noalloc.cu", [], "swe_noalloc.o"), ("swe_batch.cu", [], "swe_batch.o"),
+       ("swe_multi.cu", [], "swe_multi.o"),
        ("swe_autotune.cu", [], "swe_autotune.o")]
 )
 
@@ -61,23 +67,26 @@ def _sources() -> List[str]:
     return out
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
-def build(force: bool = False, verbose: bool = False, extra: List[str] | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: List[str] | None = None, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    out_dir = OUT_DIR_CHECKED if checked else OUT_DIR
+    if not force and up_to_date(checked):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
-    extra = list(extra or [])
+    extra = list(extra or []) + (["-DSWE_CHECKED"] if checked else [])
 
     def compile_unit(u):
         src, fl, obj = u
-        cmd = [cc] + ARCH + FLAGS + fl + extra + ["-c", os.path.join(CSRC, src), "-o", os.path.join(OUT_DIR, obj)]
+        cmd = [cc] + ARCH + FLAGS + fl + extra + ["-c", os.path.join(CSRC, src), "-o", os.path.join(out_dir, obj)]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -90,14 +99,14 @@ def build(force: bool = False, verbose: bool = False, extra: List[str] | None = 
     if verbose:
         for l in logs:
             sys.stderr.write(l)
-    tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [os.path.join(OUT_DIR, u[2]) for u in UNITS]
+    tmp = lib + ".%d.tmp" % os.getpid()
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [os.path.join(out_dir, u[2]) for u in UNITS]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -93,6 +93,7 @@ Field<T> field_of(const swe_handle *s) {
   f.nx = s->nx;
   f.ny = s->ny;
   f.pitch = s->pitch;
+  f.halo = 0;
   return f;
 }
 
@@ -258,6 +259,24 @@ int swe_debug_fail_alloc(int32_t n) {
 
 int swe_tile_count(void) { return num_shapes(); }
 
+int swe_checked_build(void) {
+#ifdef SWE_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int swe_check_status(swe_handle *s, uint64_t *word) {
+  if (!s || !word) return SWE_EINVAL;
+  unsigned long long w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, &s->sc->check, sizeof(w), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_check(s, e);
+  *word = (uint64_t)w;
+  return SWE_OK;
+}
+
 int swe_tile_shape(int k, int32_t *tx, int32_t *ty, int32_t *threads) {
   const TileShape *t = shape(k);
   if (!t) return SWE_EINVAL;
@@ -341,6 +360,9 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   s->sc = (DevScalars *)q; q += scal;
   s->cta = (DevPartials *)q; q += ctap;
   s->partials = (double *)q;
+#ifdef SWE_CHECKED
+  ph.check = &s->sc->check;  // the checked build records out-of-range indexes here
+#endif
 
   int rc = SWE_OK;
   {

@@ -65,6 +65,7 @@ __global__ void k_reset(DevScalars *sc, DevPartials *part, double t, double cfl,
   }
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     sc->part = part;
+    sc->check = 0ull;
     for (int s = 0; s < 3; ++s) sc->alpha[s][0] = sc->alpha[s][1] = 0ull;
     sc->dt = 0.0;
     sc->t = t;

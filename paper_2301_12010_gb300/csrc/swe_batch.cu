@@ -249,6 +249,7 @@ int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, co
   sl.fd.nx = sl.nx;
   sl.fd.ny = sl.ny;
   sl.fd.pitch = sl.pitch;
+  sl.fd.halo = 0;
   e = make_maps<float>(b->tile, sl.fd, sl.maps);
   if (e != cudaSuccess) {
     cudaFreeAsync(sl.mem, b->stream);
@@ -256,6 +257,9 @@ int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, co
     return bfail(b, e);
   }
   sl.p = phys_of(b->prm, dx, dy);
+#ifdef SWE_CHECKED
+  sl.p.check = &(b->d_sc + s)->check;  // the checked build records out-of-range indexes here
+#endif
   const size_t nb = sizeof(double) * (size_t)sl.nx * sl.ny;
   const double zr = sl.p.z_ref;
   e = cudaMemsetAsync(sl.mem, 0, plane * 10, b->stream);
@@ -438,6 +442,16 @@ int swe_batch_retire(swe_batch *b, int32_t slot, double *h, double *hu, double *
   sl = Slot();
   if (e != cudaSuccess) return bfail(b, e);
   return upload_table(b);
+}
+
+int swe_batch_check_status(swe_batch *b, int32_t slot, uint64_t *word) {
+  if (!valid_slot(b, slot) || !word) return SWE_EINVAL;
+  unsigned long long w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, &(b->d_sc + slot)->check, sizeof(w), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, e);
+  *word = (uint64_t)w;
+  return SWE_OK;
 }
 
 int swe_batch_memory(swe_batch *b, size_t *used, size_t *budget) {

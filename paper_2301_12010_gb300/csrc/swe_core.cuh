@@ -40,7 +40,10 @@
 
 namespace swe {
 
-enum : int { BC_WALL = 0, BC_INFLOW = 1, BC_PERIODIC = 2 };
+// BC_HALO (y sides of a strip of a row-partitioned domain): the ghost rows are
+// the neighbouring strip's rows, copied into the plane's halo rows before the
+// stage (the halo exchange of the paper's per-core partitions).
+enum : int { BC_WALL = 0, BC_INFLOW = 1, BC_PERIODIC = 2, BC_HALO = 3 };
 enum : unsigned { ST_NONFINITE = 1u, ST_DRY = 2u, ST_TIMEOUT = 4u };
 
 // Slots for per-CTA sums of the clamp and edge volumes: at least the CTAs of
@@ -75,6 +78,7 @@ struct DevScalars {
   unsigned parity;                  // steps & 1 of the running step
   unsigned active;                  // batch: slot is live
   DevPartials *part;                // this scenario's per-CTA clamp and edge volumes (set by the host)
+  unsigned long long check;         // checked build: first index found out of range (see SWE_CHK), 0 = none
 };
 
 // Derived constants of the stage arithmetic, precomputed on the host in the
@@ -109,6 +113,16 @@ struct Phys {
   // arrive, so that the timeout path runs
   long long wait_cycles;
   unsigned copy_extra, pad_;
+  // checked build: where an out-of-range index is recorded (the scenario's
+  // DevScalars::check); nullptr in the normal build
+  unsigned long long *check;
+  // strips of a row-partitioned domain: the planes carry halo_rows rows above
+  // and below (the tensor maps start there), and a follower strip leaves the
+  // per-step bookkeeping of the shared device scalars to the lead strip
+  // (a strip's edge fluxes through its y sides are not counted: its host sets
+  // the y edge weights ewy to zero; the true y edges of a partitioned domain
+  // are walls, whose mass flux is zero)
+  int halo_rows, follower;
 };
 
 constexpr long long kDefaultWaitCycles = 1ll << 31;  // ~1 s at the maximum SM clock
@@ -161,11 +175,36 @@ inline void finish_phys(Phys &p) {
   p.in_uf = p.inflow_depth > 0.0 ? std::sqrt(p.g / p.inflow_depth) : 0.0;
 }
 
+// Checked build (compiled with SWE_CHECKED): every index into the shared
+// halo box and L_x and into a global plane is compared with its extent before
+// the access.  An index out of range is recorded in *p.check -- the first one
+// only: bit 63 set, the access site in bits 40..47, the index in bits 0..39 --
+// and the access is skipped (a load reads zero).  No trap, no fault: the host
+// reads the word (swe_check_status).  In the normal build SWE_CHK is `true`
+// and the checks compile out.
+#ifdef SWE_CHECKED
+__device__ __forceinline__ bool swe_chk(unsigned long long *word, long long i, long long n, unsigned site) {
+  if (i >= 0 && i < n) return true;
+  if (word)
+    atomicCAS(word, 0ull, (1ull << 63) | ((unsigned long long)(site & 0xffu) << 40) |
+                              ((unsigned long long)i & 0xffffffffffull));
+  return false;
+}
+#define SWE_CHK(p, i, n, site) swe_chk((p).check, (long long)(i), (long long)(n), (site))
+#else
+#define SWE_CHK(p, i, n, site) true
+#endif
+enum : unsigned {  // access sites of the checked build
+  CK_PATCH_W = 1, CK_PATCH_MIRROR, CK_PATCH_GLOBAL, CK_CHUNK, CK_CELL, CK_XEPI_BOX, CK_XEPI_L, CK_YEPI_BOX,
+  CK_YEPI_L, CK_OUT, CK_U0
+};
+
 template <typename T>
 struct Field {
   const T *b;
   T *h[3], *hu[3], *hv[3];  // planes of U^n, U1, U2; h[] holds ha = h - d
   int nx, ny, pitch;
+  int halo;                 // rows allocated above row 0 and below row ny-1 (a strip's halo rows), else 0
 };
 
 // ------------------------------------------------------------ small helpers
@@ -506,8 +545,10 @@ __device__ __noinline__ void patch_box(const StageIO<T> &io, const Phys &p, int 
     const bool in_i = i >= 0 && i < nx, in_j = j >= 0 && j < ny;
     if (in_i && in_j) continue;  // a real cell, already loaded
     const int o = r * G::P + c;
+    if (!SWE_CHK(p, o, G::FIELD, CK_PATCH_W)) continue;
     const bool xg = !in_i && in_j && i >= -3 && i < nx + 3;  // x ghost
     const bool yg = in_i && !in_j && j >= -3 && j < ny + 3;  // y ghost
+    if (yg && p.bc[j < 0 ? 2 : 3] == BC_HALO) continue;      // the neighbour's rows, loaded with the box
     if (!xg && !yg) {
       bha[o] = bhu[o] = bhv[o] = bb[o] = T(0);
       continue;
@@ -520,6 +561,7 @@ __device__ __noinline__ void patch_box(const StageIO<T> &io, const Phys &p, int 
       if (xg) { si = i < 0 ? i + nx : i - nx; shift = T(i < 0 ? -p.b_jump_x : p.b_jump_x); }
       else { sj = j < 0 ? j + ny : j - ny; shift = T(j < 0 ? -p.b_jump_y : p.b_jump_y); }
       const size_t go = (size_t)sj * io.pitch + si;
+      if (!SWE_CHK(p, go, (long long)io.ny * io.pitch, CK_PATCH_GLOBAL)) continue;
       const T bs = io.b[go], cb = bs + shift;
       bb[o] = cb;
       bha[o] = (io.ha[go] + still_depth(bs, zref)) - still_depth(cb, zref);
@@ -532,6 +574,7 @@ __device__ __noinline__ void patch_box(const StageIO<T> &io, const Phys &p, int 
     if (xg) mc = (i < 0 ? (-1 - i) : (2 * nx - 1 - i)) - (i0 - G::OX);
     else mr = (j < 0 ? (-1 - j) : (2 * ny - 1 - j)) - (j0 - G::OY);
     const int m = mr * G::P + mc;
+    if (!SWE_CHK(p, m, G::FIELD, CK_PATCH_MIRROR)) continue;
     const T cb = bb[m];
     bb[o] = cb;
     if (bc == BC_INFLOW) {
@@ -659,7 +702,7 @@ struct Window {
 // db = 12 (bhat(k+1) - bhat(k)).  Adds ew times the mass flux sum Fs_0
 // through the domain edges that the strip owns (face -1/2 at k = 0 of the
 // first strip, face n-1/2 at k >= 1).
-template <typename T, int S, bool XP, typename E>
+template <typename T, int S, bool XP, int FIELD, typename E>
 __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T *bqt, const T *bb, int o0, int st,
                                             T alpha, const Consts<T> &K, const Phys &p, int ia, int n, bool edge_ok,
                                             T ew, const E &emit, T &edge) {
@@ -679,10 +722,14 @@ __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T 
       const int m = (q + 1) >> 2, e = (q + 1) & 3;
       if (q == 0 || e == 0) {
         const int c0 = o0 - 1 + 4 * m;
-        ch[0][m] = *reinterpret_cast<const float4 *>(bha + c0);
-        ch[1][m] = *reinterpret_cast<const float4 *>(bqn + c0);
-        ch[2][m] = *reinterpret_cast<const float4 *>(bqt + c0);
-        ch[3][m] = *reinterpret_cast<const float4 *>(bb + c0);
+        if (SWE_CHK(p, c0, FIELD - 3, CK_CHUNK)) {
+          ch[0][m] = *reinterpret_cast<const float4 *>(bha + c0);
+          ch[1][m] = *reinterpret_cast<const float4 *>(bqn + c0);
+          ch[2][m] = *reinterpret_cast<const float4 *>(bqt + c0);
+          ch[3][m] = *reinterpret_cast<const float4 *>(bb + c0);
+        } else {
+          ch[0][m] = ch[1][m] = ch[2][m] = ch[3][m] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
       const auto pick = [e](const float4 &v) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); };
       ha = pick(ch[0][m]);
@@ -691,10 +738,11 @@ __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T 
       b = pick(ch[3][m]);
     } else {
       const int o = o0 + q * st;
-      ha = bha[o];
-      qn = bqn[o];
-      qt = bqt[o];
-      b = bb[o];
+      const bool ok = SWE_CHK(p, o, FIELD, CK_CELL);
+      ha = ok ? bha[o] : T(0);
+      qn = ok ? bqn[o] : T(0);
+      qt = ok ? bqt[o] : T(0);
+      b = ok ? bb[o] : T(0);
     }
   };
   T ha, qn, qt, b;
@@ -762,7 +810,9 @@ struct CellEpilogue {
     const T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
     if (X) {
       const int o = xr * G::LP + xc0 + k;
-      const T ha = bha[(xr + G::OY) * G::P + xc0 + k + G::OX];
+      const int hb = (xr + G::OY) * G::P + xc0 + k + G::OX;
+      const T ha = SWE_CHK(p, hb, G::FIELD, CK_XEPI_BOX) ? bha[hb] : T(0);
+      if (!SWE_CHK(p, o, G::NC, CK_XEPI_L)) return;
       sL[o] = -dF0 * K.rfx;
       sL[G::NC + o] = -dF1 * K.rfx - K.g12dx * ha * dbk;
       sL[2 * G::NC + o] = -dF2 * K.rfx;
@@ -772,6 +822,7 @@ struct CellEpilogue {
     if (i >= io.nx || j >= io.ny) return;
     const int o = (yr0 + k) * G::LP + yc;
     const int bo = (yr0 + k + G::OY) * G::P + yc + G::OX;
+    if (!SWE_CHK(p, bo, G::FIELD, CK_YEPI_BOX) || !SWE_CHK(p, o, G::NC, CK_YEPI_L)) return;
     const T ha = bha[bo], hu = bhu[bo], hv = bhv[bo], bc = bb[bo];
     const T d = still_depth(bc, K.zref);
     const T h = ha + d;
@@ -786,6 +837,7 @@ struct CellEpilogue {
     }
     T nha = ha + tdt * Lh, nhu = hu + tdt * Lhu, nhv = hv + tdt * Lhv;
     const size_t go = (size_t)j * io.pitch + i;
+    if (!SWE_CHK(p, go, (long long)io.ny * io.pitch, CK_OUT)) return;
     if (STAGE != 1) {
       nha = u0[0][k] + wrk * (nha - u0[0][k]);
       nhu = u0[1][k] + wrk * (nhu - u0[1][k]);
@@ -864,7 +916,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
 #pragma unroll
       for (int k = 0; k < S; ++k) {
         const int j = j0 + yr0 + k;
-        const bool ok = i < nx && j < ny;
+        const bool ok = i < nx && j < ny && SWE_CHK(p, (size_t)j * io.pitch + i, (long long)ny * io.pitch, CK_U0);
         const size_t go = ok ? (size_t)j * io.pitch + i : 0;
         u0[0][k] = ok ? io.ha0[go] : T(0);
         u0[1][k] = ok ? io.hu0[go] : T(0);
@@ -872,7 +924,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
       }
     }
     const CellEpilogue<T, TX, TY, S, STAGE> emit{io, p, K, box, sL, X, xr, xc0, yc, yr0, i, j0, tdt, rcap, wrk, friction, u0, acc};
-    sweep_strip<T, S, X>(bha, X ? bhu : bhv, X ? bhv : bhu, bb,
+    sweep_strip<T, S, X, G::FIELD>(bha, X ? bhu : bhv, X ? bhv : bhu, bb,
                          X ? (xr + G::OY) * G::P + xc0 + G::OX - 3 : yr0 * G::P + yc + G::OX,
                          X ? 1 : G::P, X ? alx : aly, K, p, X ? i0 + xc0 : j0 + yr0, X ? nx : ny,
                          X ? (j0 + xr < ny) : (i < nx), X ? K.ewx : K.ewy, emit, acc.edge);
@@ -1013,7 +1065,7 @@ __device__ void stage_persistent(const StageIO<T> &io, const BoxMaps &maps, cons
   const int ntiles = tiles_x * tiles_y;
   T *box0 = smem, *box1 = smem + G::BOX, *sL = smem + 2 * G::BOX;
   auto issue = [&](int tile, T *dst, unsigned long long *b) {
-    const int x = (tile % tiles_x) * TX - G::OX, y = (tile / tiles_x) * TY - G::OY;
+    const int x = (tile % tiles_x) * TX - G::OX, y = (tile / tiles_x) * TY - G::OY + p.halo_rows;
     mbar_expect_tx(b, kBoxBytes + p.copy_extra);
 #pragma unroll
     for (int f = 0; f < 4; ++f) tma_load_2d(dst + f * G::FIELD, &maps.m[f], x, y, b);

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(ShapeP<K>::NT, MINB)
   __shared__ RedSmem red;
   using Q = ShapeP<K>;
   stage_persistent<R, Q::TX, Q::TY, Q::NT, Q::S, STAGE>(io, maps, p, sc, reinterpret_cast<R *>(smem_raw), red,
-                                                        blockIdx.x, gridDim.x, blockIdx.x == 0);
+                                                        blockIdx.x, gridDim.x, blockIdx.x == 0 && !p.follower);
 }
 
 namespace {
@@ -80,12 +80,14 @@ cudaError_t SWE_CAT(make_maps_, SWE_SHAPE)<Real>(const Field<Real> &fd, BoxMaps 
   const EncodeTiledFn enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
   const CUtensorMapDataType dtype = sizeof(Real) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-  const cuuint64_t dims[2] = {(cuuint64_t)fd.nx, (cuuint64_t)fd.ny};
+  // a strip's maps also cover its halo rows (the kernels offset y by halo_rows)
+  const cuuint64_t dims[2] = {(cuuint64_t)fd.nx, (cuuint64_t)(fd.ny + 2 * fd.halo)};
+  const size_t hoff = (size_t)fd.halo * fd.pitch;
   const cuuint64_t strides[1] = {(cuuint64_t)fd.pitch * sizeof(Real)};
   const cuuint32_t box[2] = {(cuuint32_t)G::P, (cuuint32_t)G::BH};
   const cuuint32_t estr[2] = {1u, 1u};
   for (int s = 0; s < 3; ++s) {
-    const void *planes[4] = {fd.h[s], fd.hu[s], fd.hv[s], fd.b};
+    const void *planes[4] = {fd.h[s] - hoff, fd.hu[s] - hoff, fd.hv[s] - hoff, fd.b - hoff};
     for (int f = 0; f < 4; ++f) {
       const CUresult r = enc(&out[s].m[f], dtype, 2, const_cast<void *>(planes[f]), dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -88,3 +88,17 @@ def test_batch_arguments_rejected_without_gpu(swe):
     assert not b.value
     assert swe.lib.swe_batch_run(None, 1, 0.4) == swe.EINVAL
     assert swe.lib.swe_batch_poll(None, None, None) == swe.EINVAL
+
+
+def test_checked_build_exports_the_same_calls(swe):
+    # the index-checked library (SWE_CHECKED) is the same ABI; it says which
+    # build it is, and the normal one says it is not checked
+    import ctypes as C
+    b = __import__("__graft_entry__")._build_module()
+    if not b.up_to_date(checked=True):
+        b.build(checked=True)
+    chk = C.CDLL(b.LIB_CHECKED)
+    for n in _declared("swe.h"):
+        assert hasattr(chk, n), n
+    assert chk.swe_checked_build() == 1
+    assert swe.lib.swe_checked_build() == 0
