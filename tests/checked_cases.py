@@ -66,7 +66,7 @@ def ragged(nx, ny):
 def main():
     tiles = list(range(1, swe.lib.swe_tile_count() + 1))
     fp64_tiles = [1, 2, 4, 10, 11]
-    for shape in [(77, 45), (3, 3), (37, 4), (130, 97), (200, 33)]:
+    for shape in [(77, 45), (3, 3), (8, 8), (37, 19), (37, 4), (130, 97), (200, 33)]:
         sc = ragged(*shape)
         for t in tiles:
             compare("ragged %dx%d" % shape, sc, 6, swe.F32, t)
