@@ -49,11 +49,11 @@ BYTES_PER_CELL_STAGE = {1: 28.0, 2: 40.0, 3: 40.0}
 NCU_CAPTURE = {"tile": 7, "cells": 4096 * 4096,
                "profile": "profiles/stage_kernel_f32_coastal_dem_4096_dram.md, "
                           "profiles/stage_kernel_f32_coastal_dem_2048_pipes.md",
-               "dram_bytes": {1: 269296896 + 166181888, 2: 470734848 + 175684608, 3: 470715648 + 165232128},
-               "thread_inst_per_cell": {1: 564.2, 2: 592.2, 3: 598.9},
-               "issue_active_pct": {1: 61.73, 2: 62.61, 3: 63.12},
+               "dram_bytes": {1: 269505280 + 166957824, 2: 470996992 + 176492800, 3: 470738944 + 165443840},
+               "thread_inst_per_cell": {1: 566.3, 2: 593.1, 3: 601.1},
+               "issue_active_pct": {1: 61.10, 2: 62.65, 3: 63.24},
                "sources": ("swe_core.cuh", "swe_kernels.cu", "swe_launch.h:SWE_SHAPES"),
-               "sha256": "c63ef1b9f770248666f5584979be6fd66dc55600a5d9f976970f4534a1d49d45"}
+               "sha256": "11eefae8c7d6ad239067734ddc0f013bbce0e78ff3471040d9ddc0ab32445b42"}
 
 
 def kernel_sources_sha256() -> str:
