@@ -39,7 +39,8 @@ class Params(ctypes.Structure):
         ("cfl", ctypes.c_double), ("t_end", ctypes.c_double), ("b_jump_x", ctypes.c_double),
         ("b_jump_y", ctypes.c_double), ("inflow_amp", ctypes.c_double),
         ("inflow_period", ctypes.c_double), ("inflow_depth", ctypes.c_double),
-        ("z_ref", ctypes.c_double), ("h_film", ctypes.c_double), ("bc", ctypes.c_int32 * 4),
+        ("z_ref", ctypes.c_double), ("h_film", ctypes.c_double), ("alpha_margin", ctypes.c_double),
+        ("bc", ctypes.c_int32 * 4),
     ]
 
 
@@ -83,6 +84,10 @@ def _load():
                                     ctypes.POINTER(Params), dp, dp, dp, dp, ctypes.c_double,
                                     ctypes.c_double, dp, dp, dp, dp, dp]
         lib.or_operator.restype = ctypes.c_int
+        lib.or_operator_split.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.POINTER(Params), dp, dp, dp, dp, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
+        lib.or_operator_split.restype = ctypes.c_int
         lib.or_post_stage.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), dp, dp, dp, dp]
         lib.or_post_stage.restype = ctypes.c_int
         lib.or_weno5.argtypes = [dp, ctypes.c_double, dp]
@@ -108,6 +113,7 @@ def params_of(sc) -> Params:
     p.inflow_amp, p.inflow_period, p.inflow_depth = sc.inflow_amp, sc.inflow_period, sc.inflow_depth
     p.z_ref = sc.z_ref
     p.h_film = sc.h_film
+    p.alpha_margin = sc.alpha_margin
     for k in range(4):
         p.bc[k] = int(sc.bc[k])
     return p
@@ -166,8 +172,10 @@ class Simulation:
                     runup_now=s.runup_now, runup_max=s.runup_max)
 
 
-def operator(sc, t: float = 0.0, dt: float = 0.0, h=None, hu=None, hv=None) -> Tuple[np.ndarray, np.ndarray, np.ndarray, Tuple[float, float], float]:
-    """One evaluation of the spatial operator L (Eq. (7)) of a state."""
+def operator(sc, t: float = 0.0, dt: float = 0.0, h=None, hu=None, hv=None,
+             speeds: Optional[Tuple[float, float]] = None) -> Tuple[np.ndarray, np.ndarray, np.ndarray, Tuple[float, float], float]:
+    """One evaluation of the spatial operator L (Eq. (7)) of a state, split
+    with the state's own wave speeds, or with `speeds` = (alpha_x, alpha_y)."""
     p = params_of(sc)
     b = np.ascontiguousarray(sc.b, dtype=np.float64)
     h = np.ascontiguousarray(sc.h if h is None else h, dtype=np.float64)
@@ -176,8 +184,15 @@ def operator(sc, t: float = 0.0, dt: float = 0.0, h=None, hu=None, hv=None) -> T
     Lh, Lhu, Lhv = (np.zeros_like(b) for _ in range(3))
     a2 = np.zeros(2)
     ef = np.zeros(1)
-    rc = _load().or_operator(sc.nx, sc.ny, sc.dx, sc.dy, ctypes.byref(p), _dp(b), _dp(h), _dp(hu), _dp(hv),
+    lib = _load()
+    if speeds is None:
+        rc = lib.or_operator(sc.nx, sc.ny, sc.dx, sc.dy, ctypes.byref(p), _dp(b), _dp(h), _dp(hu), _dp(hv),
                              float(t), float(dt), _dp(Lh), _dp(Lhu), _dp(Lhv), _dp(a2), _dp(ef))
+    else:
+        a2[:] = speeds
+        rc = lib.or_operator_split(sc.nx, sc.ny, sc.dx, sc.dy, ctypes.byref(p), _dp(b), _dp(h), _dp(hu),
+                                   _dp(hv), float(t), float(dt), float(a2[0]), float(a2[1]), _dp(Lh),
+                                   _dp(Lhu), _dp(Lhv), _dp(ef))
     if rc:
         raise OracleError(rc)
     return Lh, Lhu, Lhv, (float(a2[0]), float(a2[1])), float(ef[0])

@@ -41,6 +41,13 @@
  *    interior cells, recomputed at every RK stage from that stage's input.
  *  - dt = cfl / (alpha_x/dx + alpha_y/dy) from the step's first stage, or a
  *    fixed dt; optionally truncated so that t never passes t_end.
+ *  - Fused-step variant (alpha_margin > 0; not the paper's scheme, which takes
+ *    alpha at every stage): all three stages split with one speed per step,
+ *    alpha_margin x the alpha of U^n, so that a step depends on U^n and the
+ *    bed alone and can be computed in one pass over tiles with a 9-cell halo.
+ *    dt is still the CFL step of U^n's alpha.  alpha_margin >= 1 keeps
+ *    the splitting speed above the speeds of U^n; whether it stays above
+ *    those of the intermediate stages is the margin's job.
  *  - (8) is the Shu-Osher SSP-RK3 form (the printed nesting is the same map).
  *  - Wet/dry (not described in the paper): velocities are zero where
  *    h < h_dry; after every stage h < 0 is set to 0 and hu = hv = 0 where
@@ -86,6 +93,8 @@ typedef struct {
   double inflow_depth;  /* offshore depth d0 */
   double z_ref;         /* still-water level: d = max(z_ref - b, 0) */
   double h_film;        /* film depth of the velocity desingularisation */
+  double alpha_margin;  /* > 0: fused-step variant, splitting speed alpha_margin x alpha(U^n)
+                           in all three stages; 0: alpha of each stage's input (the paper) */
   int32_t bc[4];        /* x-, x+, y-, y+ */
 } or_params;
 
@@ -551,8 +560,12 @@ static int rk3_step(const grid_t *g, const double *b, fields_t U0, fields_t U1, 
   if (p->t_end > 0.0 && t + dt > p->t_end) dt = p->t_end - t;
   if (!(dt > 0.0)) return OR_EINVAL;
 
+  /* the fused-step variant keeps this splitting speed for the whole step */
+  const int fused = p->alpha_margin > 0.0;
+  const double sx = fused ? p->alpha_margin * ax : ax, sy = fused ? p->alpha_margin * ay : ay;
+
   double clamp = 0.0, bmass = 0.0;
-  int rc = operator_L(g, b, U0.h, U0.hu, U0.hv, ax, ay, dt, Lh, Lhu, Lhv, &flux);
+  int rc = operator_L(g, b, U0.h, U0.hu, U0.hv, sx, sy, dt, Lh, Lhu, Lhv, &flux);
   if (rc) return rc;
   bmass += dt * flux / 6.0;
 #pragma omp parallel for
@@ -568,6 +581,7 @@ static int rk3_step(const grid_t *g, const double *b, fields_t U0, fields_t U1, 
   /* stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt L(U1)) */
   fill_state_ghosts(g, b, U1.h, U1.hu, U1.hv, t + dt);
   if (max_speeds(g, U1.h, U1.hu, U1.hv, &ax, &ay)) return OR_ENONFINITE;
+  if (fused) { ax = sx; ay = sy; }
   rc = operator_L(g, b, U1.h, U1.hu, U1.hv, ax, ay, dt, Lh, Lhu, Lhv, &flux);
   if (rc) return rc;
   bmass += dt * flux / 6.0;
@@ -584,6 +598,7 @@ static int rk3_step(const grid_t *g, const double *b, fields_t U0, fields_t U1, 
   /* stage 3: U^{n+1} = 1/3 U0 + 2/3 (U2 + dt L(U2)) */
   fill_state_ghosts(g, b, U2.h, U2.hu, U2.hv, t + 0.5 * dt);
   if (max_speeds(g, U2.h, U2.hu, U2.hv, &ax, &ay)) return OR_ENONFINITE;
+  if (fused) { ax = sx; ay = sy; }
   rc = operator_L(g, b, U2.h, U2.hu, U2.hv, ax, ay, dt, Lh, Lhu, Lhv, &flux);
   if (rc) return rc;
   bmass += dt * flux * (2.0 / 3.0);
@@ -630,6 +645,7 @@ static int validate(int nx, int ny, double dx, double dy, const or_params *p) {
   if (!(p->g > 0.0) || p->manning_n < 0.0 || !(p->h_dry >= 0.0) || !(p->weno_eps > 0.0))
     return OR_EINVAL;
   if (!(p->fixed_dt > 0.0) && !(p->cfl > 0.0)) return OR_EINVAL;
+  if (!(p->alpha_margin == 0.0 || p->alpha_margin >= 1.0)) return OR_EINVAL;
   return OR_OK;
 }
 
@@ -724,30 +740,55 @@ int or_diagnose(int nx, int ny, double dx, double dy, const or_params *p, const 
   return rc;
 }
 
-/* One evaluation of the spatial operator L of (7) at time t with the wave
- * speeds of the given state (dt only enters the friction cap).  Writes the
- * interior L arrays and returns the edge mass flux through *edge_flux. */
-int or_operator(int nx, int ny, double dx, double dy, const or_params *p, const double *b,
-                const double *h, const double *hu, const double *hv, double t, double dt,
-                double *Lh, double *Lhu, double *Lhv, double *alpha2, double *edge_flux) {
+/* One evaluation of the spatial operator L of (7) at time t (dt only enters
+ * the friction cap), split with the speeds (*ax, *ay) if use_given, else with
+ * the wave speeds of the given state, which are returned in *ax, *ay.  Writes
+ * the interior L arrays and returns the edge mass flux through *edge_flux. */
+static int operator_once(int nx, int ny, double dx, double dy, const or_params *p, const double *b,
+                         const double *h, const double *hu, const double *hv, double t, double dt,
+                         double *Lh, double *Lhu, double *Lhv, int use_given, double *ax, double *ay,
+                         double *edge_flux) {
   int rc = validate(nx, ny, dx, dy, p);
   if (rc) return rc;
   work_t w;
   rc = work_alloc(&w, nx, ny, dx, dy, p, b, h, hu, hv);
   if (rc) return rc;
   fill_state_ghosts(&w.g, w.b, w.U0.h, w.U0.hu, w.U0.hv, t);
-  double ax, ay;
-  if (max_speeds(&w.g, w.U0.h, w.U0.hu, w.U0.hv, &ax, &ay)) {
+  double sx, sy;
+  if (max_speeds(&w.g, w.U0.h, w.U0.hu, w.U0.hv, &sx, &sy)) {
     free(w.mem);
     return OR_ENONFINITE;
   }
-  rc = operator_L(&w.g, w.b, w.U0.h, w.U0.hu, w.U0.hv, ax, ay, dt, Lh, Lhu, Lhv, edge_flux);
+  if (use_given) {
+    sx = *ax;
+    sy = *ay;
+  }
+  rc = operator_L(&w.g, w.b, w.U0.h, w.U0.hu, w.U0.hv, sx, sy, dt, Lh, Lhu, Lhv, edge_flux);
+  *ax = sx;
+  *ay = sy;
+  free(w.mem);
+  return rc;
+}
+
+/* L of (7) with the state's own wave speeds (returned in alpha2[0..1]). */
+int or_operator(int nx, int ny, double dx, double dy, const or_params *p, const double *b,
+                const double *h, const double *hu, const double *hv, double t, double dt,
+                double *Lh, double *Lhu, double *Lhv, double *alpha2, double *edge_flux) {
+  double ax = 0.0, ay = 0.0;
+  int rc = operator_once(nx, ny, dx, dy, p, b, h, hu, hv, t, dt, Lh, Lhu, Lhv, 0, &ax, &ay, edge_flux);
   if (alpha2) {
     alpha2[0] = ax;
     alpha2[1] = ay;
   }
-  free(w.mem);
   return rc;
+}
+
+/* L of (7) split with given speeds ax, ay (the fused-step variant's stages). */
+int or_operator_split(int nx, int ny, double dx, double dy, const or_params *p, const double *b,
+                      const double *h, const double *hu, const double *hv, double t, double dt,
+                      double ax, double ay, double *Lh, double *Lhu, double *Lhv, double *edge_flux) {
+  if (!(ax >= 0.0) || !(ay >= 0.0)) return OR_EINVAL;
+  return operator_once(nx, ny, dx, dy, p, b, h, hu, hv, t, dt, Lh, Lhu, Lhv, 1, &ax, &ay, edge_flux);
 }
 
 /* The post-stage rule alone (for pins): applies to the state h, hu, hv
