@@ -76,9 +76,14 @@ typedef struct {
   double inflow_amp;    /* INFLOW: peak surface elevation (m) */
   double inflow_period; /* INFLOW: N-wave period T (s) */
   double inflow_depth;  /* INFLOW: offshore depth d0 (m) */
+  double alpha_margin;  /* fused_step: splitting speed = alpha_margin x alpha(U^n), >= 1; 1.1 */
   int32_t bc[4];        /* sides x-, x+, y-, y+ (swe_bc) */
   int32_t precision;    /* swe_precision of state and arithmetic */
   int32_t tile;         /* 0: autotuned/default tile shape; k > 0: compiled shape k */
+  int32_t fused_step;   /* 0: one kernel per RK stage with the paper's per-stage alpha (Eq. (8) with
+                           Eq. (6) at every stage); 1: the fused-step variant, one kernel per step
+                           splitting all three stages with alpha_margin x alpha(U^n) (walls and the
+                           inflow edge only; not a batch or strip option) */
   void *stream;         /* cudaStream_t to run on (e.g. torch.cuda.Stream().cuda_stream); NULL = legacy default */
 } swe_params;
 
@@ -120,7 +125,11 @@ int swe_set_state_device(swe_handle *s, const void *h, const void *hu, const voi
 /* Enqueue n RK3 steps (Eq. (8)) on the handle's stream.  Each step runs three
  * stage kernels; the time step is dt = cfl / (alpha_x/dx + alpha_y/dy) from
  * the step's first stage (ignored if fixed_dt > 0).  Asynchronous: no host
- * synchronisation; steps are replayed from a captured CUDA graph. */
+ * synchronisation; steps are replayed from a captured CUDA graph.  With
+ * fused_step each step is one kernel (between two one-thread bookkeeping
+ * kernels) that reads U^n and writes U^{n+1} into a second set of planes;
+ * steps are replayed in pairs, and an odd n ends with a device copy of the
+ * state back into the first set. */
 int swe_step(swe_handle *s, int32_t n, double cfl);
 
 /* Wait for the handle's stream and report the device status. */
@@ -217,7 +226,9 @@ int swe_tile_shape(int k, int32_t *tx, int32_t *ty, int32_t *threads);
 /* Timing helper for benchmarks: enqueue n steps as individual stage launches
  * (not the graph) with a CUDA event recorded on the handle's stream around
  * each stage kernel, wait, and return the summed milliseconds of whole steps
- * (*ms_total) and of each stage kernel (ms_stage[3], may be NULL). */
+ * (*ms_total) and of each stage kernel (ms_stage[3], may be NULL).  With
+ * fused_step: ms_stage[0] is the fused kernel's time, ms_stage[1] that of the
+ * two bookkeeping kernels, ms_stage[2] zero. */
 int swe_time_stages(swe_handle *s, int32_t n, double cfl, double *ms_total, double *ms_stage);
 
 /* Tile-shape autotuner (native timing loop).  Times every compiled tile

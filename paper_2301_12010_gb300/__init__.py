@@ -39,8 +39,9 @@ class Params(ctypes.Structure):
         ("h_wet", ctypes.c_double), ("h_film", ctypes.c_double), ("weno_eps", ctypes.c_double),
         ("fixed_dt", ctypes.c_double), ("z_ref", ctypes.c_double), ("b_jump_x", ctypes.c_double), ("b_jump_y", ctypes.c_double),
         ("inflow_amp", ctypes.c_double), ("inflow_period", ctypes.c_double), ("inflow_depth", ctypes.c_double),
+        ("alpha_margin", ctypes.c_double),
         ("bc", ctypes.c_int32 * 4), ("precision", ctypes.c_int32), ("tile", ctypes.c_int32),
-        ("stream", ctypes.c_void_p),
+        ("fused_step", ctypes.c_int32), ("stream", ctypes.c_void_p),
     ]
 
 
@@ -171,6 +172,10 @@ def params_for(sc, precision: int = F32, stream: Optional[int] = None, tile: int
     p.inflow_amp, p.inflow_period, p.inflow_depth = sc.inflow_amp, sc.inflow_period, sc.inflow_depth
     for k in range(4):
         p.bc[k] = int(sc.bc[k])
+    margin = float(getattr(sc, "alpha_margin", 0.0) or 0.0)
+    if margin > 0.0:  # the fused-step variant (one splitting speed per step)
+        p.fused_step = 1
+        p.alpha_margin = margin
     p.precision = int(precision)
     p.tile = int(tile)
     p.stream = stream

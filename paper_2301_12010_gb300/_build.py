@@ -46,7 +46,7 @@ UNITS: List[Tuple[str, List[str], str]] = (
     + [("swe_batch_kernels.cu", ["-DSWE_SHAPE=%d" % k], "swe_batch_kernels_s%d.o" % k) for k in SHAPES]
     + [("swe_shapes.cu", [], "swe_shapes.o"), ("swe_api.cu", [], "swe_api.o"), ("swe_aux.cu", [], "swe_aux.o"),
        ("swe_noalloc.cu", [], "swe_noalloc.o"), ("swe_batch.cu", [], "swe_batch.o"),
-       ("swe_multi.cu", [], "swe_multi.o"),
+       ("swe_multi.cu", [], "swe_multi.o"), ("swe_fused.cu", [], "swe_fused.o"),
        ("swe_autotune.cu", [], "swe_autotune.o")]
 )
 

@@ -55,7 +55,8 @@ struct swe_handle {
   DevPartials *cta = nullptr;     // per-CTA partials of the clamp and edge volumes
   double *partials = nullptr;     // kMassBlocks + 1 (last: mass result)
   BoxMaps maps[3] = {};           // tensor maps of the halo-box copies, per RK stage
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;   // one step (fused_step: two steps, plane sets 0 -> 1 -> 0)
+  cudaGraphExec_t graph1 = nullptr;  // fused_step: one step 0 -> 1 and the copy of set 1 back to set 0
   double cfl_dev = -1.0;          // CFL value last written to the device scalars
   int sticky = SWE_OK;            // first host-visible error
   // asynchronous read-back (swe_get_state_async): U^n is copied to snap on the
@@ -97,8 +98,31 @@ Field<T> field_of(const swe_handle *s) {
   return f;
 }
 
+// The plane set 1 (U1 of the stage kernels) copied back into set 0 (U^n).
+cudaError_t copy_back(swe_handle *s, cudaStream_t st) {
+  const size_t bytes = (size_t)s->pitch * s->ny * s->elem;
+  cudaError_t e = cudaMemcpyAsync(s->h[0], s->h[1], bytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->hu[0], s->hu[1], bytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->hv[0], s->hv[1], bytes, cudaMemcpyDeviceToDevice, st);
+  return e;
+}
+
+// One fused step from plane set `from` to 1 - from.
+cudaError_t enqueue_fused(swe_handle *s, int from, cudaStream_t st, cudaEvent_t *ev = nullptr) {
+  return s->prec == SWE_F64
+             ? launch_fused<double>(field_of<double>(s), from, s->phys, s->sc, s->prm.alpha_margin, st, ev)
+             : launch_fused<float>(field_of<float>(s), from, s->phys, s->sc, s->prm.alpha_margin, st, ev);
+}
+
+// What one replay of s->graph does: one step of three stage kernels, or (fused
+// step) two fused steps that end in plane set 0 again.
 cudaError_t enqueue_step(swe_handle *s, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
+  if (s->prm.fused_step) {
+    e = enqueue_fused(s, 0, st);
+    if (e == cudaSuccess) e = enqueue_fused(s, 1, st);
+    return e;
+  }
   for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
     if (s->prec == SWE_F64) e = launch_stage<double>(s->tile, field_of<double>(s), s->phys, s->sc, stage, st, s->maps);
     else e = launch_stage<float>(s->tile, field_of<float>(s), s->phys, s->sc, stage, st, s->maps);
@@ -213,6 +237,12 @@ bool valid_params(const swe_params *p) {
     return false;
   if (!std::isfinite(p->z_ref) || !std::isfinite(p->fixed_dt)) return false;
   if (p->tile < 0 || p->tile > num_shapes()) return false;
+  if (p->fused_step != 0 && p->fused_step != 1) return false;
+  if (p->fused_step) {
+    for (int k = 0; k < 4; ++k)
+      if (p->bc[k] == SWE_BC_PERIODIC) return false;  // the fused step has wall and inflow ghosts only
+    if (!(p->alpha_margin >= 1.0) || !std::isfinite(p->alpha_margin)) return false;
+  }
   return true;
 }
 
@@ -234,6 +264,8 @@ void swe_params_default(swe_params *p) {
   for (int k = 0; k < 4; ++k) p->bc[k] = SWE_BC_WALL;
   p->precision = SWE_F32;
   p->tile = 0;
+  p->fused_step = 0;
+  p->alpha_margin = 1.1;
   p->stream = nullptr;
 }
 
@@ -374,11 +406,17 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
       rc = SWE_ECUDA;
     } else if (shape_smem(s->tile, (int)s->elem) + sizeof(RedSmem) > (size_t)optin) {
       rc = SWE_EINVAL;
+    } else if (params->fused_step && fused_smem((int)s->elem) + sizeof(RedSmem) + 256 > (size_t)optin) {
+      rc = SWE_EINVAL;
     }
   }
   if (rc == SWE_OK && cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) rc = SWE_ECUDA;
   if (rc == SWE_OK) {
     e = s->prec == SWE_F64 ? prepare_shape<double>(s->tile) : prepare_shape<float>(s->tile);
+    rc = cuda_check(s, e);
+  }
+  if (rc == SWE_OK && params->fused_step) {
+    e = s->prec == SWE_F64 ? prepare_fused<double>() : prepare_fused<float>();
     rc = cuda_check(s, e);
   }
   if (rc == SWE_OK) {
@@ -430,20 +468,29 @@ int swe_step(swe_handle *s, int32_t n, double cfl) {
     if (e != cudaSuccess) return cuda_check(s, e);
     s->cfl_dev = cfl;
   }
-  if (!s->graph) {
+  auto capture = [s](cudaGraphExec_t *out, bool single) {
     cudaGraph_t g = nullptr;
-    e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t le = enqueue_step(s, s->cap);
+      cudaError_t le = single ? enqueue_fused(s, 0, s->cap) : enqueue_step(s, s->cap);
+      if (single && le == cudaSuccess) le = copy_back(s, s->cap);
       e = cudaStreamEndCapture(s->cap, &g);
       if (le != cudaSuccess) e = le;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->graph, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
     if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      s->graph = nullptr;
-      return cuda_check(s, e);
+    if (e != cudaSuccess) *out = nullptr;
+    return e;
+  };
+  if (!s->graph && (e = capture(&s->graph, false)) != cudaSuccess) return cuda_check(s, e);
+  if (s->prm.fused_step) {
+    // the graph advances two steps; an odd count ends with one more and the copy back
+    for (int32_t k = 0; k < n / 2 && e == cudaSuccess; ++k) e = cudaGraphLaunch(s->graph, s->stream);
+    if (e == cudaSuccess && (n & 1)) {
+      if (!s->graph1) e = capture(&s->graph1, true);
+      if (e == cudaSuccess) e = cudaGraphLaunch(s->graph1, s->stream);
     }
+    return cuda_check(s, e);
   }
   for (int32_t k = 0; k < n && e == cudaSuccess; ++k) e = cudaGraphLaunch(s->graph, s->stream);
   return cuda_check(s, e);
@@ -647,6 +694,10 @@ int swe_set_wait(swe_handle *s, double timeout_s, int32_t extra_copy_bytes) {
     cudaGraphExecDestroy(s->graph);
     s->graph = nullptr;
   }
+  if (s->graph1) {
+    cudaGraphExecDestroy(s->graph1);
+    s->graph1 = nullptr;
+  }
   if (s->sticky == SWE_ETIMEOUT) s->sticky = SWE_OK;
   return SWE_OK;
 }
@@ -663,6 +714,7 @@ int swe_destroy(swe_handle *s) {
   if (s->snap) cudaFree(s->snap);
   if (s->xstage) cudaFree(s->xstage);
   if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->graph1) cudaGraphExecDestroy(s->graph1);
   if (s->cap) cudaStreamDestroy(s->cap);
   if (s->mem) cudaFree(s->mem);
   delete s;
@@ -679,7 +731,21 @@ int swe_time_stages(swe_handle *s, int32_t n, double cfl, double *ms_total, doub
     if (cudaEventCreate(&ev[k]) != cudaSuccess) return fail(s, SWE_ECUDA);
   double acc[3] = {0, 0, 0}, tot = 0.0;
   cudaError_t e = cudaSuccess;
-  for (int32_t it = 0; it < n && e == cudaSuccess; ++it) {
+  if (s->prm.fused_step) {
+    // steps alternate between the plane sets; an odd count ends with the copy back
+    for (int32_t it = 0; it < n && e == cudaSuccess; ++it) {
+      e = enqueue_fused(s, it & 1, s->stream, ev);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+      float m[3];
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&m[k], ev[k], ev[k + 1]);
+      if (e != cudaSuccess) break;
+      acc[0] += m[1];
+      acc[1] += m[0] + m[2];
+      tot += m[0] + m[1] + m[2];
+    }
+    if (e == cudaSuccess && (n & 1)) e = copy_back(s, s->stream);
+  }
+  for (int32_t it = 0; it < n && e == cudaSuccess && !s->prm.fused_step; ++it) {
     e = cudaEventRecord(ev[0], s->stream);
     for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
       if (s->prec == SWE_F64)

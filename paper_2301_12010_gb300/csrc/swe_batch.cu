@@ -165,6 +165,7 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
   if (out) *out = nullptr;
   if (!out || !params || nslots < 1 || nslots > 4096 || hbm_budget_bytes == 0) return SWE_EINVAL;
   if (params->precision != SWE_F32) return SWE_EINVAL;  // the batch path is FP32
+  if (params->fused_step) return SWE_EINVAL;             // and runs the paper's per-stage alpha
   for (int k = 0; k < 4; ++k)
     if (params->bc[k] != SWE_BC_WALL) return SWE_EINVAL;  // ensembles and requests are walled coasts
   if (params->tile < 0 || params->tile > num_shapes()) return SWE_EINVAL;

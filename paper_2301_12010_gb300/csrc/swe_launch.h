@@ -88,6 +88,18 @@ cudaError_t mass(const T *ha, const T *bed, double zref, int nx, int ny, int pit
                  double *out, cudaStream_t st);
 float thr32(double thr);
 
+// The fused-step variant (swe_fused.cu): one kernel per RK3 step reading the
+// planes of set `from` (0 or 1) and writing set 1 - from, between a step
+// preparation and a step finishing kernel (one thread each).  With ev != NULL,
+// events ev[0..3] are recorded before the preparation, before and after the
+// step kernel, and after the finishing kernel.
+template <typename T>
+cudaError_t prepare_fused();
+template <typename T>
+cudaError_t launch_fused(const Field<T> &fd, int from, const Phys &p, DevScalars *sc, double margin,
+                         cudaStream_t st, cudaEvent_t *ev = nullptr);
+size_t fused_smem(int elem_bytes);
+
 template <typename T>
 cudaError_t prepare_shape(int k);
 // Tensor maps of the halo-box copies for shape k: out[s] covers the input

@@ -79,6 +79,14 @@ def main():
     compare("periodic Manning 64x8", W.manning_slope(nx=64, ny=8, q=0.8 * qn), 50, swe.F64)
     compare("inflow DEM 96", W.coastal_dem(n=96, dx=150.0, t0=500.0), 20, swe.F64)
     compare("inflow DEM 96", W.coastal_dem(n=96, dx=150.0, t0=500.0), 20, swe.F32)
+    # the fused-step variant (one kernel per step, 9-cell halo frames)
+    for shape in [(3, 3), (8, 8), (37, 19), (77, 45), (130, 97), (65, 33), (200, 33)]:
+        sc = ragged(*shape).copy(alpha_margin=1.1)
+        compare("fused ragged %dx%d" % shape, sc, 6, swe.F32)
+        compare("fused ragged %dx%d" % shape, sc, 6, swe.F64)
+    fdem = W.coastal_dem(n=96, dx=150.0, t0=500.0).copy(alpha_margin=1.1)
+    compare("fused inflow DEM 96", fdem, 20, swe.F32)
+    compare("fused inflow DEM 96", fdem, 20, swe.F64)
     # the batch kernel over a mix of small coasts
     ens = W.mitigation_ensemble(count=5, seed=41, nx_range=(96, 192), ny_range=(32, 128), land_width=90.0)
     with swe.Batch(len(ens), 1 << 30, ens[0], stream=ST) as b:

@@ -38,6 +38,7 @@ def test_defaults_and_strerror(swe):
     p = swe.Params()
     swe.lib.swe_params_default(ctypes.byref(p))
     assert p.g == 9.81 and p.h_dry == 1e-5 and p.weno_eps == 1e-6 and list(p.bc) == [0, 0, 0, 0]
+    assert p.fused_step == 0 and p.alpha_margin == 1.1
     for code in range(8):
         assert swe.lib.swe_strerror(code)
     assert swe.lib.swe_destroy(None) == swe.OK
@@ -59,6 +60,16 @@ def test_invalid_arguments_rejected_without_gpu(swe):
     assert swe.lib.swe_create(ctypes.byref(swe.Grid(4, 4)), 1.0, 1.0, dp, ctypes.byref(q), ctypes.byref(h)) == swe.EINVAL
     q = swe.Params.from_buffer_copy(p)
     q.precision = 7
+    assert swe.lib.swe_create(ctypes.byref(swe.Grid(4, 4)), 1.0, 1.0, dp, ctypes.byref(q), ctypes.byref(h)) == swe.EINVAL
+    # the fused-step variant: a margin below 1, periodic sides, an unknown mode
+    for field, value in (("alpha_margin", 0.9), ("alpha_margin", float("nan")), ("fused_step", 2)):
+        q = swe.Params.from_buffer_copy(p)
+        q.fused_step = 1
+        setattr(q, field, value)
+        assert swe.lib.swe_create(ctypes.byref(swe.Grid(4, 4)), 1.0, 1.0, dp, ctypes.byref(q), ctypes.byref(h)) == swe.EINVAL
+    q = swe.Params.from_buffer_copy(p)
+    q.fused_step = 1
+    q.bc[0] = q.bc[1] = swe.PERIODIC
     assert swe.lib.swe_create(ctypes.byref(swe.Grid(4, 4)), 1.0, 1.0, dp, ctypes.byref(q), ctypes.byref(h)) == swe.EINVAL
     assert not h.value
     assert swe.lib.swe_step(None, 1, 0.4) == swe.EINVAL
@@ -84,6 +95,9 @@ def test_batch_arguments_rejected_without_gpu(swe):
     assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
     q = swe.Params.from_buffer_copy(p)
     q.bc[0] = swe.INFLOW  # ensembles and requests are walled coasts
+    assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
+    q = swe.Params.from_buffer_copy(p)
+    q.fused_step = 1  # the batch runs the per-stage alpha
     assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
     assert not b.value
     assert swe.lib.swe_batch_run(None, 1, 0.4) == swe.EINVAL
