@@ -192,6 +192,12 @@ __device__ __forceinline__ void fused_stage(const FusedIO<T> &io, const Phys &p,
   const T wc = STAGE == 1 ? T(1.0 / 6.0) : (STAGE == 2 ? T(2.0 / 3.0) : T(1));   // clamp weight
   const T wf = STAGE == 3 ? T(2.0 / 3.0) : T(1.0 / 6.0);                          // edge-flux weight
   const T ewx = K.ewx * wf, ewy = K.ewy * wf;
+  // Edge faces count once, in the tile that owns the cell beside them: a tile
+  // that does not own the last column (row) passes an edge index no face can
+  // reach, since a padded strip may run past the domain's edge with cells the
+  // region does not hold.
+  const int ex = i0 + TX >= nx ? nx : 1 << 30, ey = j0 + TY >= ny ? ny : 1 << 30;
+  const bool own_ex = i0 == 0 || i0 + TX >= nx, own_ey = j0 == 0 || j0 + TY >= ny;
 
   // x pass: lane -> row (consecutive rows: distinct banks), strips across
   const int nsx = (RW + S - 1) / S;
@@ -209,8 +215,8 @@ __device__ __forceinline__ void fused_stage(const FusedIO<T> &io, const Phys &p,
       lhu[o] = -dF1 * K.rfx - K.g12dx * ha * dbk;
       lhv[o] = -dF2 * K.rfx;
     };
-    sweep_strip<T, S, false, FIELD>(iha, ihu, ihv, bb, row + c0 - 3, 1, fs.sx, K, p, ri0 + c0, nx,
-                                    j >= j0 && j < j0 + TY, ewx, emit, acc.edge);
+    sweep_strip<T, S, false, FIELD>(iha, ihu, ihv, bb, row + c0 - 3, 1, fs.sx, K, p, ri0 + c0, ex,
+                                    own_ex && j >= j0 && j < j0 + TY, ewx, emit, acc.edge);
   }
   __syncthreads();
 
@@ -293,7 +299,7 @@ __device__ __forceinline__ void fused_stage(const FusedIO<T> &io, const Phys &p,
       }
     };
     sweep_strip<T, S, false, FIELD>(iha, ihv, ihu, bb, (fr0 + r0 - 3) * G::P + fc0 + c, G::P, fs.sy, K, p,
-                                    rj0 + r0, ny, own_col, ewy, emit, acc.edge);
+                                    rj0 + r0, ey, own_ey && own_col, ewy, emit, acc.edge);
   }
   __syncthreads();
 }
