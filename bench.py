@@ -236,6 +236,58 @@ def fp64_bench(swe, W, torch, sc, steps: int = 10):
             "autotune_ms": [round(x, 3) for x in ms_shapes]}
 
 
+FUSED_BYTES_PER_CELL = 28.0  # FP32: U^n (12 B) and the bed (4 B) read, U^{n+1} (12 B) written, once per step
+
+
+def fused_bench(swe, W, torch, sc, steps: int = 20, margin: float = 1.1, warmup: int = 4,
+                per_stage_ms: float = 0.0, hbm_peak: float = 6800.0):
+    """The fused-step variant on the same workload: one kernel per RK3 step
+    (9-cell halo frames in shared memory), all three stages split with
+    margin x alpha(U^n) instead of the paper's per-stage alpha."""
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with swe.Solver(sc.copy(alpha_margin=margin), precision=swe.F32, stream=stream.cuda_stream) as s:
+        s.step(warmup)
+        s.sync()
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.sync()
+        ms = e0.elapsed_time(e1) / steps
+        nk = 10
+        _, kst = s.time_stages(nk)
+    k_ms = kst[0] / nk
+    achieved = FUSED_BYTES_PER_CELL * sc.cells / (k_ms / 1e3) / 1e9
+    out = {"value": sc.cells / (ms / 1e3), "unit": "cell-updates/s", "steps": steps, "ms_per_step": ms,
+           "kernel_ms": k_ms, "bookkeeping_ms": kst[1] / nk, "alpha_margin": margin, "dtype": "f32",
+           "scheme": "fused-step variant: one splitting speed per step (margin x alpha of U^n), not the "
+                     "paper's per-stage alpha",
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": achieved / hbm_peak, "bytes_per_cell_update": FUSED_BYTES_PER_CELL},
+           "gpu_launches": 3 * steps}
+    if per_stage_ms > 0:
+        out["speed_vs_stage_kernels"] = per_stage_ms / ms
+    return out
+
+
+def profile_fused_case(n: int = 2048) -> int:
+    """A few fused steps on the n x n coastal DEM, for ncu; no timing."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2301_12010_gb300 as swe
+    import workloads as W
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream().cuda_stream
+    with swe.Solver(W.coastal_dem(n=n).copy(alpha_margin=1.1), precision=swe.F32, stream=st) as s:
+        s.step(4)
+        s.sync()
+    print("profile-fused: ok")
+    return 0
+
+
 def serving_bench(swe, W, torch, rates=(5.0, 20.0), count: int = 12, horizon: float = 20.0,
                   policies=("srpt", "all"), fill_waves: int = 4):
     """C5: Poisson requests, N log-uniform in [256, 2048], coast and hills as
@@ -449,6 +501,9 @@ def main():
                     help="only one RK3 step of the batch kernel on the 64-scenario ensemble (contiguous order) "
                          "and on one walled 2048x2048 DEM (strided order), then the same DEM by the "
                          "single-scenario kernels: a short case for a profiler")
+    ap.add_argument("--no-fused", action="store_true", help="skip the fused-step variant's measurement")
+    ap.add_argument("--profile-fused", action="store_true",
+                    help="only four fused steps on the --n coastal DEM: a short case for a profiler")
     ap.add_argument("--config-table", action="store_true",
                     help="only the per-configuration table: GPU FP32/FP64 beside the oracle at 1 thread and all "
                          "cores; prints one JSON object")
@@ -457,6 +512,8 @@ def main():
         return run_reference(args)
     if args.profile_batch:
         return profile_batch_case()
+    if args.profile_fused:
+        return profile_fused_case(args.n)
     if args.config_table:
         return config_table()
     if args.serving_sweep:
@@ -597,6 +654,9 @@ def main():
                     "sequential_how": "per step swe_set_state + swe_step(1) + swe_get_state, all synchronous"},
             "sim": {"t": diag["t"], "steps": diag["steps"], "last_dt": diag["last_dt"]},
         }
+        if ws == 1 and not args.no_fused:
+            line["fused_step"] = fused_bench(swe, W, torch, sc, per_stage_ms=ms_max / args.steps,
+                                             hbm_peak=hbm_peak)
         if ws == 1 and not args.no_fp64:
             line["fp64"] = fp64_bench(swe, W, torch, sc)
         if ws == 1 and not args.no_ensemble:

@@ -249,7 +249,7 @@ int swe_autotune(const swe_grid *grids, int32_t ngrids, int32_t precision, int32
 int swe_autotune_lookup(int32_t precision, int32_t mode, double cells);
 
 /* ----------------------------------------------------------------------
- * Batched ensemble and continuous-batching serving (FP32, walls).
+ * Batched ensemble and continuous-batching serving (FP32).
  * A batch holds up to nslots independent scenarios ("slots") of any grid
  * size, admitted while device memory stays within hbm_budget_bytes.
  * swe_batch_run advances every live slot by up to k RK3 steps (each slot
@@ -264,9 +264,10 @@ typedef struct swe_batch swe_batch;
 /* Device bytes one admission of this grid takes (counted against the budget). */
 size_t swe_batch_slot_bytes(const swe_grid *grid);
 
-/* Create an empty batch.  params: precision must be SWE_F32 and all four
- * sides SWE_BC_WALL; tile 0 picks the default shape; stream as for swe_create.
- * SWE_EINVAL otherwise. */
+/* Create an empty batch.  params: precision must be SWE_F32 and fused_step 0;
+ * the sides (walls, the inflow edge, periodic pairs) and the physical
+ * parameters are those of every slot, under the rules of swe_create; tile 0
+ * picks the default shape; stream as for swe_create.  SWE_EINVAL otherwise. */
 int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *params, swe_batch **out);
 
 /* Admit a scenario: host FP64 bathymetry and state [ny][nx] (copied), run until
@@ -277,6 +278,10 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
  * cases).  Call between runs. */
 int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, const double *bathymetry,
                     const double *h, const double *hu, const double *hv, double t_end, int32_t *slot);
+
+/* Set a live slot's simulated time (its inflow N-wave is read at that time;
+ * t_end stays absolute).  Call between runs, before the slot's first run. */
+int swe_batch_set_time(swe_batch *b, int32_t slot, double t);
 
 /* Enqueue one persistent launch of k RK3 steps over all live slots with the
  * given CFL number (asynchronous; slots past t_end are skipped). */

@@ -98,6 +98,7 @@ def _load() -> ctypes.CDLL:
         "swe_batch_poll": (ip, [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "swe_batch_select": (ip, [H, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
         "swe_batch_times": (ip, [H, dp]),
+        "swe_batch_set_time": (ip, [H, ctypes.c_int32, ctypes.c_double]),
         "swe_batch_get_state": (ip, [H, ctypes.c_int32, dp, dp, dp]),
         "swe_batch_diagnostics": (ip, [H, ctypes.c_int32, ctypes.POINTER(Diag)]),
         "swe_batch_retire": (ip, [H, ctypes.c_int32, dp, dp, dp, dp, dp]),
@@ -441,6 +442,8 @@ class Batch:
         _check(lib.swe_batch_admit(self._b, ctypes.byref(Grid(sc.nx, sc.ny)), float(sc.dx), float(sc.dy),
                                    *[_dp(a) for a in arrs], float(te), ctypes.byref(slot)), "swe_batch_admit")
         self.shapes[slot.value] = (sc.ny, sc.nx)
+        if getattr(sc, "t0", 0.0):
+            _check(lib.swe_batch_set_time(self._b, slot.value, float(sc.t0)), "swe_batch_set_time")
         return slot.value
 
     def select(self, slots=None) -> None:

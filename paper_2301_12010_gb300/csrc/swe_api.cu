@@ -223,6 +223,10 @@ int after_state_change(swe_handle *s) {
   return cuda_check(s, e);
 }
 
+}  // namespace
+
+namespace swe {
+// Parameters a solver (or a batch, under its own extra rules) accepts.
 bool valid_params(const swe_params *p) {
   if (!p) return false;
   if (p->precision != SWE_F32 && p->precision != SWE_F64) return false;
@@ -245,8 +249,7 @@ bool valid_params(const swe_params *p) {
   }
   return true;
 }
-
-}  // namespace
+}  // namespace swe
 
 extern "C" {
 

@@ -16,6 +16,10 @@
 #include "swe_trace.h"
 #include "swe_alloc.h"
 
+namespace swe {
+bool valid_params(const swe_params *p);  // swe_api.cu
+}
+
 using namespace swe;
 
 namespace {
@@ -166,11 +170,7 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
   if (!out || !params || nslots < 1 || nslots > 4096 || hbm_budget_bytes == 0) return SWE_EINVAL;
   if (params->precision != SWE_F32) return SWE_EINVAL;  // the batch path is FP32
   if (params->fused_step) return SWE_EINVAL;             // and runs the paper's per-stage alpha
-  for (int k = 0; k < 4; ++k)
-    if (params->bc[k] != SWE_BC_WALL) return SWE_EINVAL;  // ensembles and requests are walled coasts
-  if (params->tile < 0 || params->tile > num_shapes()) return SWE_EINVAL;
-  if (!(params->g > 0.0) || !(params->weno_eps > 0.0) || !(params->h_dry >= 0.0) || !(params->manning_n >= 0.0))
-    return SWE_EINVAL;
+  if (!valid_params(params)) return SWE_EINVAL;          // sides and physics as for one scenario
   swe_batch *b = new (std::nothrow) swe_batch();
   if (!b) return SWE_ENOMEM;
   b->nslots = nslots;
@@ -367,6 +367,15 @@ int swe_batch_select(swe_batch *b, const int32_t *slots, int32_t n) {
     for (auto &sl : b->slots) sl.selected = true;
   }
   return upload_table(b);
+}
+
+int swe_batch_set_time(swe_batch *b, int32_t slot, double t) {
+  if (!valid_slot(b, slot) || !std::isfinite(t) || !(t < b->slots[slot].t_end)) return SWE_EINVAL;
+  DevScalars *sc = b->d_sc + slot;
+  cudaError_t e = cudaMemcpyAsync(&sc->t, &t, sizeof(double), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&sc->t_step, &t, sizeof(double), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? SWE_OK : bfail(b, e);
 }
 
 int swe_batch_times(swe_batch *b, double *t) {

@@ -94,7 +94,13 @@ def test_batch_arguments_rejected_without_gpu(swe):
     q.precision = swe.F64  # the batch path is FP32
     assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
     q = swe.Params.from_buffer_copy(p)
-    q.bc[0] = swe.INFLOW  # ensembles and requests are walled coasts
+    q.bc[0] = swe.INFLOW  # an inflow edge needs the N-wave's depth and period
+    assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
+    q = swe.Params.from_buffer_copy(p)
+    q.bc[1] = swe.INFLOW  # the inflow edge is the x- side only
+    assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
+    q = swe.Params.from_buffer_copy(p)
+    q.bc[2] = swe.PERIODIC  # periodic sides come in pairs
     assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
     q = swe.Params.from_buffer_copy(p)
     q.fused_step = 1  # the batch runs the per-stage alpha

@@ -124,6 +124,72 @@ def test_batch_matches_fp64_oracle():
     assert np.sqrt(((et - er) ** 2).sum() / (er ** 2).sum()) <= 1e-4
 
 
+def test_ensemble_at_full_size_matches_fp64_oracle():
+    # the ensemble of the batched-ensemble workload itself (64 coasts of
+    # 512-1024 x 256-1024 cells, hills and a shoreline): the largest and the
+    # smallest coast, each run in one batch together with two others, against
+    # the oracle after 30 steps
+    ens = W.mitigation_ensemble()
+    sizes = [sc.cells for sc in ens]
+    pick = [int(np.argmax(sizes)), int(np.argmin(sizes))]
+    others = [k for k in range(len(ens)) if k not in pick][:2]
+    with swe.Batch(4, 8 * GB, ens[0], stream=stream()) as b:
+        slots = {k: b.admit(ens[k]) for k in pick + others}
+        b.run(30)
+        got = {k: (b.get_state(slots[k]), b.diagnostics(slots[k])) for k in pick}
+    for k in pick:
+        sc = ens[k]
+        ref = oracle.Simulation(sc)
+        ref.step(30)
+        (h, hu, hv), d = got[k]
+        et = np.where(h >= 1e-5, h + sc.b, 0.0)
+        er = np.where(ref.h >= 1e-5, ref.h + sc.b, 0.0)
+        assert np.sqrt(((et - er) ** 2).sum() / (er ** 2).sum()) <= 1e-4, sc.name
+        assert np.sqrt(((hu - ref.hu) ** 2).sum() / (ref.hu ** 2).sum()) <= 1e-4, sc.name
+        assert d["t"] == pytest.approx(ref.t, rel=1e-5), sc.name
+        rd = ref.diag()
+        if rd["runup_max"] > -np.inf:
+            assert abs(d["runup_max"] - rd["runup_max"]) <= 0.01, sc.name
+
+
+def test_batch_with_the_inflow_edge_matches_fp64_oracle():
+    # coastal DEMs with the N-wave inflow edge, Manning friction and a dry
+    # shore, each starting at its own time, advanced together in one batch
+    cases = [W.coastal_dem(n=n, dx=dx, t0=t0) for n, dx, t0 in ((96, 150.0, 500.0), (128, 120.0, 450.0),
+                                                                 (160, 100.0, 520.0))]
+    with swe.Batch(4, 4 * GB, cases[0], stream=stream()) as b:
+        slots = [b.admit(sc, t_end=1e6) for sc in cases]
+        b.run(20)
+        got = [(b.get_state(s), b.diagnostics(s)) for s in slots]
+    for sc, ((h, hu, hv), d) in zip(cases, got):
+        ref = oracle.Simulation(sc)
+        ref.step(20)
+        rd = ref.diag()
+        et = np.where(h >= 1e-5, h + sc.b, 0.0)
+        er = np.where(ref.h >= 1e-5, ref.h + sc.b, 0.0)
+        assert np.sqrt(((et - er) ** 2).sum() / (er ** 2).sum()) <= 1e-4, sc.name
+        assert np.sqrt(((hu - ref.hu) ** 2).sum() / (ref.hu ** 2).sum()) <= 1e-4, sc.name
+        assert d["t"] == pytest.approx(rd["t"], rel=1e-6), sc.name
+        assert d["boundary_mass"] == pytest.approx(rd["boundary_mass"], rel=1e-4), sc.name
+
+
+def test_batch_with_periodic_sides_matches_fp64_oracle():
+    # flow down a periodic 1:20 slope with Manning friction (bed offset of one
+    # period): two discharges in one batch
+    from tests.analytic import manning_normal_discharge
+    qn = manning_normal_discharge(0.5, 1 / 20, 0.033)
+    cases = [W.manning_slope(nx=64, ny=8, q=f * qn) for f in (0.8, 1.2)]
+    with swe.Batch(2, GB, cases[0], stream=stream()) as b:
+        slots = [b.admit(sc, t_end=1e6) for sc in cases]
+        b.run(60)
+        got = [b.get_state(s) for s in slots]
+    for sc, (h, hu, hv) in zip(cases, got):
+        ref = oracle.Simulation(sc)
+        ref.step(60)
+        assert np.sqrt(((h - ref.h) ** 2).sum() / (ref.h ** 2).sum()) <= 1e-5
+        assert np.sqrt(((hu - ref.hu) ** 2).sum() / (ref.hu ** 2).sum()) <= 1e-4
+
+
 def test_batch_stops_at_t_end_and_reports_done():
     ens = small_ensemble(3, seed=8)
     with swe.Batch(4, GB, ens[0], stream=stream()) as b:
