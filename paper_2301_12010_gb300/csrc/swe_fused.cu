@@ -56,10 +56,11 @@ struct FusedGeom {
   static constexpr int UN = 0, A = 3 * PLANE, B = 6 * PLANE, BED = 9 * PLANE;
 };
 
-// Compiled shapes of the fused kernel: (TX, TY, threads) per precision.
+// Compiled shapes of the fused kernel: (TX, TY, threads, CTAs per SM asked
+// of the register allocator) per precision.
 template <typename T> struct FusedShape;
-template <> struct FusedShape<float> { static constexpr int TX = 64, TY = 32, NT = 384; };
-template <> struct FusedShape<double> { static constexpr int TX = 32, TY = 16, NT = 192; };
+template <> struct FusedShape<float> { static constexpr int TX = 64, TY = 32, NT = 384, MINB = 1; };
+template <> struct FusedShape<double> { static constexpr int TX = 32, TY = 16, NT = 192, MINB = 1; };
 
 template <typename T>
 struct FusedIO {
@@ -173,7 +174,7 @@ __device__ void fused_load(const FusedIO<T> &io, const Phys &p, int i0, int j0, 
 // cells (and edge faces) of the tile itself only, with the stage's RK weight:
 // clamp 1/6, 2/3, 1; edge flux dt/6, dt/6, 2 dt/3 (dt applied at publication).
 template <typename T, int TX, int TY, int NT, int STAGE>
-__device__ __forceinline__ void fused_stage(const FusedIO<T> &io, const Phys &p, const FusedStep<T> &fs, int i0,
+__device__ __noinline__ void fused_stage(const FusedIO<T> &io, const Phys &p, const FusedStep<T> &fs, int i0,
                                             int j0, T *sm, Acc<T> &acc) {
   using G = FusedGeom<T, TX, TY>;
   constexpr int S = G::S;
@@ -346,7 +347,8 @@ __device__ __noinline__ void fused_publish(const Phys &p, DevScalars *sc, RedSme
 }
 
 template <typename T, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT, 1) fused_step_kernel(FusedIO<T> io, Phys p, DevScalars *sc, double margin) {
+__global__ void __launch_bounds__(NT, FusedShape<T>::MINB)
+    fused_step_kernel(FusedIO<T> io, Phys p, DevScalars *sc, double margin) {
   using G = FusedGeom<T, TX, TY>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ RedSmem red;
