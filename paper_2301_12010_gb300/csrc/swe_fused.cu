@@ -174,7 +174,7 @@ __device__ void fused_load(const FusedIO<T> &io, const Phys &p, int i0, int j0, 
 // cells (and edge faces) of the tile itself only, with the stage's RK weight:
 // clamp 1/6, 2/3, 1; edge flux dt/6, dt/6, 2 dt/3 (dt applied at publication).
 template <typename T, int TX, int TY, int NT, int STAGE>
-__device__ __noinline__ void fused_stage(const FusedIO<T> &io, const Phys &p, const FusedStep<T> &fs, int i0,
+__device__ __forceinline__ void fused_stage(const FusedIO<T> &io, const Phys &p, const FusedStep<T> &fs, int i0,
                                             int j0, T *sm, Acc<T> &acc) {
   using G = FusedGeom<T, TX, TY>;
   constexpr int S = G::S;
