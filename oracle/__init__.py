@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
         ("b_jump_y", ctypes.c_double), ("inflow_amp", ctypes.c_double),
         ("inflow_period", ctypes.c_double), ("inflow_depth", ctypes.c_double),
         ("z_ref", ctypes.c_double), ("h_film", ctypes.c_double), ("alpha_margin", ctypes.c_double),
-        ("bc", ctypes.c_int32 * 4),
+        ("bc", ctypes.c_int32 * 4), ("shore", ctypes.c_int32), ("pad_", ctypes.c_int32),
     ]
 
 
@@ -114,6 +114,7 @@ def params_of(sc) -> Params:
     p.z_ref = sc.z_ref
     p.h_film = sc.h_film
     p.alpha_margin = sc.alpha_margin
+    p.shore = int(sc.shore)
     for k in range(4):
         p.bc[k] = int(sc.bc[k])
     return p

@@ -56,6 +56,19 @@
  *    h_dry <= h < h_film get the velocity desingularisation of Kurganov &
  *    Petrova (2007): u = sqrt(2) h hu / sqrt(h^4 + h_film^4), hu := h u (and
  *    the same for v), which keeps thin-film velocities bounded.
+ *  - Shoreline variant (shore = 1; not in the paper, which is silent on wet/dry
+ *    fronts): a face whose six-cell WENO stencil holds a dry cell (h < h_dry)
+ *    or a land cell (d = 0) takes the first-order hydrostatic reconstruction
+ *    of Audusse et al. (2004) instead: face bed b_f = max(b_L, b_R), face
+ *    depths h*_s = max(0, h_s + b_s - b_f), the global-LF flux of the standard
+ *    SWE flux (pressure g h*^2/2) of those face states with the line's alpha,
+ *    and for each side s the normal-momentum flux it sees raised by
+ *    g (h_s^2 - h*_s^2)/2.  Each side's value is then shifted by the
+ *    cell-local -g d_s^2/2 + g (h_s - d_s) b_s, which carries it into this
+ *    file's still-depth form: at rest a WENO face and such a face give the same
+ *    value g (h - d)(eta + z_ref)/2 to a cell between them, so a lake at rest is
+ *    exact at any level beside any dry land, and shore cells update with
+ *    the positivity-preserving first-order scheme.
  *  - Friction is explicit, applied only where h >= h_dry, with the rate
  *    kappa = g n^2 |q| / h^(7/3) capped at 1/dt.
  *  - Walls: ghost k mirrors interior k-1 (h, b, tangential momentum even,
@@ -96,6 +109,9 @@ typedef struct {
   double alpha_margin;  /* > 0: fused-step variant, splitting speed alpha_margin x alpha(U^n)
                            in all three stages; 0: alpha of each stage's input (the paper) */
   int32_t bc[4];        /* x-, x+, y-, y+ */
+  int32_t shore;        /* 1: shoreline variant, hydrostatic-reconstruction faces where a WENO
+                           stencil meets a dry or land cell; 0: WENO at every face (the paper) */
+  int32_t pad_;
 } or_params;
 
 typedef struct {
@@ -344,6 +360,97 @@ static void sweep_line(int n, double eps, int mom, double *const fp[3], double *
   }
 }
 
+/* Shoreline variant along one grid line (see the header): for every face
+ * i+1/2, i = -1 .. n-1 (index i+1), whose stencil cells i-2 .. i+3 hold a
+ * dry or a land cell, the values the left and the right cell see replace
+ * the WENO face values: FL[m], bL for cell i, FR[m], bR for cell i+1 (the
+ * bed values enter through g (h - d) b of the cell update).  Elsewhere
+ * FL = FR = Fhat and bL = bR = bhat.  hl, ql, tl, bl: depth, normal and
+ * tangential momentum and bed along the line (cells -3 .. n+2).  mom: the
+ * component of the normal momentum (1 in x, 2 in y). */
+static void shore_faces(const or_params *p, int n, double alpha, int mom, const double *hl, const double *ql,
+                        const double *tl, const double *bl, double *const Fhat[3], const double *bhat,
+                        double *const FL[3], double *const FR[3], double *bL, double *bR) {
+  const int tan = 3 - mom;
+  for (int i = -1; i < n; ++i) {
+    const int c = i + NG, f = i + 1;
+    int shore = 0;
+    for (int k = c - 2; k <= c + 3; ++k)
+      if (hl[k] < p->h_dry || still_depth(p, bl[k]) == 0.0) shore = 1;
+    if (!shore) {
+      for (int m = 0; m < 3; ++m) FL[m][f] = FR[m][f] = Fhat[m][f];
+      bL[f] = bR[f] = bhat[f];
+      continue;
+    }
+    const int side[2] = {c, c + 1};
+    const double bf = bl[c] > bl[c + 1] ? bl[c] : bl[c + 1];
+    double hs[2], F[2][3], U[2][3];
+    for (int s = 0; s < 2; ++s) {
+      const int k = side[s];
+      double u, v;
+      velocity(p, hl[k], ql[k], tl[k], &u, &v); /* u: normal, v: tangential velocity */
+      hs[s] = hl[k] + bl[k] - bf;
+      if (hs[s] < 0.0) hs[s] = 0.0;
+      U[s][0] = hs[s];
+      U[s][mom] = hs[s] * u;
+      U[s][tan] = hs[s] * v;
+      F[s][0] = hs[s] * u;
+      F[s][mom] = hs[s] * u * u + 0.5 * p->g * hs[s] * hs[s];
+      F[s][tan] = hs[s] * u * v;
+    }
+    double Fhr[3];
+    for (int m = 0; m < 3; ++m) Fhr[m] = 0.5 * (F[0][m] + F[1][m]) - 0.5 * alpha * (U[1][m] - U[0][m]);
+    for (int s = 0; s < 2; ++s) {
+      const int k = side[s];
+      const double d = still_depth(p, bl[k]);
+      double *const *out = s == 0 ? FL : FR;
+      out[0][f] = Fhr[0];
+      out[tan][f] = Fhr[tan];
+      out[mom][f] = Fhr[mom] + 0.5 * p->g * (hl[k] * hl[k] - hs[s] * hs[s]) - 0.5 * p->g * d * d;
+      (s == 0 ? bL : bR)[f] = bl[k];
+    }
+  }
+}
+
+/* Per-line scratch of the face values each side of a face sees. */
+typedef struct {
+  double *mem;
+  double *h, *q, *t;              /* depth, normal and tangential momentum, cells -3 .. n+2 */
+  double *FL[3], *FR[3], *bL, *bR; /* faces -1/2 .. n-1/2 */
+} line_t;
+
+static int line_alloc(line_t *ln, size_t len, int n) {
+  const size_t nf = (size_t)n + 1;
+  ln->mem = (double *)malloc(sizeof(double) * (3 * len + 8 * nf));
+  if (!ln->mem) return 1;
+  ln->h = ln->mem;
+  ln->q = ln->h + len;
+  ln->t = ln->q + len;
+  double *f = ln->t + len;
+  for (int m = 0; m < 3; ++m) {
+    ln->FL[m] = f + m * nf;
+    ln->FR[m] = f + (3 + m) * nf;
+  }
+  ln->bL = f + 6 * nf;
+  ln->bR = f + 7 * nf;
+  return 0;
+}
+
+/* The face values of one line: the WENO values, or with the shoreline
+ * variant the hydrostatic-reconstruction values where a stencil meets a dry
+ * or land cell. */
+static void line_faces(const or_params *p, line_t *ln, int n, double alpha, int mom, const double *bl,
+                       double *const Fhat[3], const double *bhat) {
+  if (p->shore) {
+    shore_faces(p, n, alpha, mom, ln->h, ln->q, ln->t, bl, Fhat, bhat, ln->FL, ln->FR, ln->bL, ln->bR);
+    return;
+  }
+  for (int f = 0; f <= n; ++f) {
+    for (int m = 0; m < 3; ++m) ln->FL[m][f] = ln->FR[m][f] = Fhat[m][f];
+    ln->bL[f] = ln->bR[f] = bhat[f];
+  }
+}
+
 /* L(U) of (7): L = -(Fhat_{i+1/2} - Fhat_{i-1/2})/dx - (Ghat_{j+1/2} - Ghat_{j-1/2})/dy + S.
  * Ghosts of h, hu, hv and b must be filled.  Writes interior-sized L arrays
  * and the net mass flux into the domain through its edges (per unit time). */
@@ -377,8 +484,14 @@ static int operator_L(const grid_t *g, const double *b, const double *h, const d
       double *bl = buf + 6 * len;
       double *Fh[3] = {buf + 7 * len, buf + 7 * len + (n + 1), buf + 7 * len + 2 * (n + 1)};
       double *bh = buf + 7 * len + 3 * (n + 1);
+      line_t ln;
+      if (line_alloc(&ln, len, n)) {
+#pragma omp atomic write
+        fail = 1;
+      }
 #pragma omp for
       for (int j = 0; j < ny; ++j) {
+        if (!ln.mem) continue;
         for (int i = -NG; i < n + NG; ++i) {
           size_t c = ix(g, i, j);
           double a[3], m_[3];
@@ -388,18 +501,23 @@ static int operator_L(const grid_t *g, const double *b, const double *h, const d
             fm[m][i + NG] = m_[m];
           }
           bl[i + NG] = b[c];
+          ln.h[i + NG] = h[c];
+          ln.q[i + NG] = hu[c];
+          ln.t[i + NG] = hv[c];
         }
         sweep_line(n, p->weno_eps, 1, fp, fm, bl, Fh, bh);
+        line_faces(p, &ln, n, ax, 1, bl, Fh, bh);
         for (int i = 0; i < n; ++i) {
           size_t c = ix(g, i, j);
           size_t o = (size_t)j * nx + i;
           double ha = h[c] - still_depth(p, b[c]);
-          Lh[o] = -(Fh[0][i + 1] - Fh[0][i]) / g->dx;
-          Lhu[o] = -(Fh[1][i + 1] - Fh[1][i]) / g->dx - p->g * ha * (bh[i + 1] - bh[i]) / g->dx;
-          Lhv[o] = -(Fh[2][i + 1] - Fh[2][i]) / g->dx;
+          Lh[o] = -(ln.FL[0][i + 1] - ln.FR[0][i]) / g->dx;
+          Lhu[o] = -(ln.FL[1][i + 1] - ln.FR[1][i]) / g->dx - p->g * ha * (ln.bL[i + 1] - ln.bR[i]) / g->dx;
+          Lhv[o] = -(ln.FL[2][i + 1] - ln.FR[2][i]) / g->dx;
         }
-        rowflux[j] = (Fh[0][0] - Fh[0][n]) * g->dy;
+        rowflux[j] = (ln.FR[0][0] - ln.FL[0][n]) * g->dy;
       }
+      free(ln.mem);
       free(buf);
     }
   }
@@ -424,8 +542,14 @@ static int operator_L(const grid_t *g, const double *b, const double *h, const d
       double *bl = buf + 6 * len;
       double *Gh[3] = {buf + 7 * len, buf + 7 * len + (n + 1), buf + 7 * len + 2 * (n + 1)};
       double *bh = buf + 7 * len + 3 * (n + 1);
+      line_t ln;
+      if (line_alloc(&ln, len, n)) {
+#pragma omp atomic write
+        fail = 1;
+      }
 #pragma omp for
       for (int i = 0; i < nx; ++i) {
+        if (!ln.mem) continue;
         for (int j = -NG; j < n + NG; ++j) {
           size_t c = ix(g, i, j);
           double a[3], m_[3];
@@ -435,18 +559,23 @@ static int operator_L(const grid_t *g, const double *b, const double *h, const d
             fm[m][j + NG] = m_[m];
           }
           bl[j + NG] = b[c];
+          ln.h[j + NG] = h[c];
+          ln.q[j + NG] = hv[c];
+          ln.t[j + NG] = hu[c];
         }
         sweep_line(n, p->weno_eps, 2, fp, fm, bl, Gh, bh);
+        line_faces(p, &ln, n, ay, 2, bl, Gh, bh);
         for (int j = 0; j < n; ++j) {
           size_t c = ix(g, i, j);
           size_t o = (size_t)j * nx + i;
           double ha = h[c] - still_depth(p, b[c]);
-          Lh[o] += -(Gh[0][j + 1] - Gh[0][j]) / g->dy;
-          Lhu[o] += -(Gh[1][j + 1] - Gh[1][j]) / g->dy;
-          Lhv[o] += -(Gh[2][j + 1] - Gh[2][j]) / g->dy - p->g * ha * (bh[j + 1] - bh[j]) / g->dy;
+          Lh[o] += -(ln.FL[0][j + 1] - ln.FR[0][j]) / g->dy;
+          Lhu[o] += -(ln.FL[1][j + 1] - ln.FR[1][j]) / g->dy;
+          Lhv[o] += -(ln.FL[2][j + 1] - ln.FR[2][j]) / g->dy - p->g * ha * (ln.bL[j + 1] - ln.bR[j]) / g->dy;
         }
-        colflux[i] = (Gh[0][0] - Gh[0][n]) * g->dx;
+        colflux[i] = (ln.FR[0][0] - ln.FL[0][n]) * g->dx;
       }
+      free(ln.mem);
       free(buf);
     }
   }
@@ -646,6 +775,7 @@ static int validate(int nx, int ny, double dx, double dy, const or_params *p) {
     return OR_EINVAL;
   if (!(p->fixed_dt > 0.0) && !(p->cfl > 0.0)) return OR_EINVAL;
   if (!(p->alpha_margin == 0.0 || p->alpha_margin >= 1.0)) return OR_EINVAL;
+  if (p->shore != 0 && p->shore != 1) return OR_EINVAL;
   return OR_OK;
 }
 

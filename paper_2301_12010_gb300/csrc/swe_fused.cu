@@ -167,20 +167,22 @@ __device__ void fused_load(const FusedIO<T> &io, const Phys &p, int i0, int j0, 
   __syncthreads();
 }
 
-// One RK stage of the fused step on the tile (i0, j0) grown by MG cells and
+// One RK stage of the fused step (STAGE 1, 2 or 3, a runtime value: one copy
+// of the sweeps' code serves all three stages, which keeps the kernel in the
+// instruction cache) on the tile (i0, j0) grown by MG cells and
 // clipped to the domain: x pass (L_x parked in the output planes, or in A for
 // stage 3), then y pass (sources, friction, the RK combination with U^n from
 // the frame, the post-stage rule; stage 3 writes HBM).  Diagnostics count the
 // cells (and edge faces) of the tile itself only, with the stage's RK weight:
 // clamp 1/6, 2/3, 1; edge flux dt/6, dt/6, 2 dt/3 (dt applied at publication).
-template <typename T, int TX, int TY, int NT, int STAGE>
+template <typename T, int TX, int TY, int NT>
 __device__ __forceinline__ void fused_stage(const FusedIO<T> &io, const Phys &p, const FusedStep<T> &fs, int i0,
-                                            int j0, T *sm, Acc<T> &acc) {
+                                            int j0, T *sm, Acc<T> &acc, const int STAGE) {
   using G = FusedGeom<T, TX, TY>;
   constexpr int S = G::S;
-  constexpr int MG = (3 - STAGE) * 3;
-  constexpr int IN = STAGE == 1 ? G::UN : (STAGE == 2 ? G::A : G::B);
-  constexpr int OUT = STAGE == 1 ? G::A : (STAGE == 2 ? G::B : G::A);  // stage 3: L_x only
+  const int MG = (3 - STAGE) * 3;
+  const int IN = STAGE == 1 ? G::UN : (STAGE == 2 ? G::A : G::B);
+  const int OUT = STAGE == 1 ? G::A : (STAGE == 2 ? G::B : G::A);  // stage 3: L_x only
   constexpr int FIELD = G::PLANE + G::TAIL;
   const Consts<T> &K = consts<T>(p);
   const int nx = io.nx, ny = io.ny, tid = threadIdx.x;
@@ -400,13 +402,15 @@ __global__ void __launch_bounds__(NT, FusedShape<T>::MINB)
     const int i0 = (t % tiles_x) * TX, j0 = (t / tiles_x) * TY;
     __syncthreads();  // every thread is done with the previous tile's frame
     fused_load<T, TX, TY, NT>(io, p, i0, j0, sm, zref, fs.eta[0], fs.uin[0]);
-    fused_stage<T, TX, TY, NT, 1>(io, p, fs, i0, j0, sm, acc);
-    fused_ghosts<T, TX, TY, NT>(p, io.nx, io.ny, i0, j0, sm + G::A, sm + G::BED, zref, fs.eta[1], fs.uin[1]);
-    __syncthreads();
-    fused_stage<T, TX, TY, NT, 2>(io, p, fs, i0, j0, sm, acc);
-    fused_ghosts<T, TX, TY, NT>(p, io.nx, io.ny, i0, j0, sm + G::B, sm + G::BED, zref, fs.eta[2], fs.uin[2]);
-    __syncthreads();
-    fused_stage<T, TX, TY, NT, 3>(io, p, fs, i0, j0, sm, acc);
+#pragma unroll 1
+    for (int st = 1; st <= 3; ++st) {
+      fused_stage<T, TX, TY, NT>(io, p, fs, i0, j0, sm, acc, st);
+      if (st < 3) {
+        fused_ghosts<T, TX, TY, NT>(p, io.nx, io.ny, i0, j0, sm + (st == 1 ? G::A : G::B), sm + G::BED, zref,
+                                    fs.eta[st], fs.uin[st]);
+        __syncthreads();
+      }
+    }
   }
   fused_publish<T, NT>(p, sc, red, fs.dt, acc);
 }

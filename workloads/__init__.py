@@ -55,6 +55,7 @@ class Scenario:
     inflow_depth: float = 0.0
     z_ref: float = 0.0  # still-water level; still-water depth d = max(z_ref - b, 0)
     alpha_margin: float = 0.0  # > 0: the fused-step variant (one splitting speed per step); 0: per stage
+    shore: int = 0  # 1: the shoreline variant (hydrostatic-reconstruction faces at dry and land cells)
     t0: float = 0.0
     steps: int = 0  # suggested number of RK3 steps for this workload
 
