@@ -58,7 +58,7 @@
  *    the same for v), which keeps thin-film velocities bounded.
  *  - Shoreline variant (shore = 1; not in the paper, which is silent on wet/dry
  *    fronts): a face whose six-cell WENO stencil holds a dry cell (h < h_dry)
- *    or a land cell (d = 0) takes the first-order hydrostatic reconstruction
+ *    takes the first-order hydrostatic reconstruction
  *    of Audusse et al. (2004) instead: face bed b_f = max(b_L, b_R), face
  *    depths h*_s = max(0, h_s + b_s - b_f), the global-LF flux of the standard
  *    SWE flux (pressure g h*^2/2) of those face states with the line's alpha,
@@ -66,9 +66,9 @@
  *    g (h_s^2 - h*_s^2)/2.  Each side's value is then shifted by the
  *    cell-local -g d_s^2/2 + g (h_s - d_s) b_s, which carries it into this
  *    file's still-depth form: at rest a WENO face and such a face give the same
- *    value g (h - d)(eta + z_ref)/2 to a cell between them, so a lake at rest is
- *    exact at any level beside any dry land, and shore cells update with
- *    the positivity-preserving first-order scheme.
+ *    value g (h - d)(eta + z_ref)/2 to a cell between them, so a lake at rest
+ *    at any level at or below z_ref is exact beside any dry land, and shore
+ *    cells update with the positivity-preserving first-order scheme.
  *  - Friction is explicit, applied only where h >= h_dry, with the rate
  *    kappa = g n^2 |q| / h^(7/3) capped at 1/dt.
  *  - Walls: ghost k mirrors interior k-1 (h, b, tangential momentum even,
@@ -110,7 +110,7 @@ typedef struct {
                            in all three stages; 0: alpha of each stage's input (the paper) */
   int32_t bc[4];        /* x-, x+, y-, y+ */
   int32_t shore;        /* 1: shoreline variant, hydrostatic-reconstruction faces where a WENO
-                           stencil meets a dry or land cell; 0: WENO at every face (the paper) */
+                           stencil meets a dry cell; 0: WENO at every face (the paper) */
   int32_t pad_;
 } or_params;
 
@@ -362,7 +362,7 @@ static void sweep_line(int n, double eps, int mom, double *const fp[3], double *
 
 /* Shoreline variant along one grid line (see the header): for every face
  * i+1/2, i = -1 .. n-1 (index i+1), whose stencil cells i-2 .. i+3 hold a
- * dry or a land cell, the values the left and the right cell see replace
+ * dry cell, the values the left and the right cell see replace
  * the WENO face values: FL[m], bL for cell i, FR[m], bR for cell i+1 (the
  * bed values enter through g (h - d) b of the cell update).  Elsewhere
  * FL = FR = Fhat and bL = bR = bhat.  hl, ql, tl, bl: depth, normal and
@@ -376,7 +376,7 @@ static void shore_faces(const or_params *p, int n, double alpha, int mom, const 
     const int c = i + NG, f = i + 1;
     int shore = 0;
     for (int k = c - 2; k <= c + 3; ++k)
-      if (hl[k] < p->h_dry || still_depth(p, bl[k]) == 0.0) shore = 1;
+      if (hl[k] < p->h_dry) shore = 1;
     if (!shore) {
       for (int m = 0; m < 3; ++m) FL[m][f] = FR[m][f] = Fhat[m][f];
       bL[f] = bR[f] = bhat[f];
@@ -438,7 +438,7 @@ static int line_alloc(line_t *ln, size_t len, int n) {
 
 /* The face values of one line: the WENO values, or with the shoreline
  * variant the hydrostatic-reconstruction values where a stencil meets a dry
- * or land cell. */
+ * cell. */
 static void line_faces(const or_params *p, line_t *ln, int n, double alpha, int mom, const double *bl,
                        double *const Fhat[3], const double *bhat) {
   if (p->shore) {
