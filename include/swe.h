@@ -84,6 +84,11 @@ typedef struct {
                            Eq. (6) at every stage); 1: the fused-step variant, one kernel per step
                            splitting all three stages with alpha_margin x alpha(U^n) (walls and the
                            inflow edge only; not a batch or strip option) */
+  int32_t shore;        /* 0: WENO at every face (the paper); 1: the shoreline variant, first-order
+                           hydrostatic-reconstruction faces (Audusse et al. 2004) wherever a WENO
+                           stencil meets a dry cell, so that lakes at rest at or below z_ref stay at
+                           rest beside dry land (tile 0 or its one compiled shape: 96x32 in FP32,
+                           64x32 in FP64; not a batch, strip or fused_step option) */
   void *stream;         /* cudaStream_t to run on (e.g. torch.cuda.Stream().cuda_stream); NULL = legacy default */
 } swe_params;
 

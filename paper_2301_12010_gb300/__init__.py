@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
         ("inflow_amp", ctypes.c_double), ("inflow_period", ctypes.c_double), ("inflow_depth", ctypes.c_double),
         ("alpha_margin", ctypes.c_double),
         ("bc", ctypes.c_int32 * 4), ("precision", ctypes.c_int32), ("tile", ctypes.c_int32),
-        ("fused_step", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("fused_step", ctypes.c_int32), ("shore", ctypes.c_int32), ("stream", ctypes.c_void_p),
     ]
 
 
@@ -173,6 +173,7 @@ def params_for(sc, precision: int = F32, stream: Optional[int] = None, tile: int
     p.inflow_amp, p.inflow_period, p.inflow_depth = sc.inflow_amp, sc.inflow_period, sc.inflow_depth
     for k in range(4):
         p.bc[k] = int(sc.bc[k])
+    p.shore = int(getattr(sc, "shore", 0) or 0)  # the shoreline variant
     margin = float(getattr(sc, "alpha_margin", 0.0) or 0.0)
     if margin > 0.0:  # the fused-step variant (one splitting speed per step)
         p.fused_step = 1

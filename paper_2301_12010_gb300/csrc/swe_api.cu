@@ -114,6 +114,15 @@ cudaError_t enqueue_fused(swe_handle *s, int from, cudaStream_t st, cudaEvent_t 
              : launch_fused<float>(field_of<float>(s), from, s->phys, s->sc, s->prm.alpha_margin, st, ev);
 }
 
+// One stage kernel: the paper's WENO faces, or the shoreline variant's.
+cudaError_t launch_one_stage(swe_handle *s, int stage, cudaStream_t st) {
+  if (s->prm.shore)
+    return s->prec == SWE_F64 ? launch_shore<double>(field_of<double>(s), s->phys, s->sc, stage, st, s->maps)
+                              : launch_shore<float>(field_of<float>(s), s->phys, s->sc, stage, st, s->maps);
+  return s->prec == SWE_F64 ? launch_stage<double>(s->tile, field_of<double>(s), s->phys, s->sc, stage, st, s->maps)
+                            : launch_stage<float>(s->tile, field_of<float>(s), s->phys, s->sc, stage, st, s->maps);
+}
+
 // What one replay of s->graph does: one step of three stage kernels, or (fused
 // step) two fused steps that end in plane set 0 again.
 cudaError_t enqueue_step(swe_handle *s, cudaStream_t st) {
@@ -123,10 +132,7 @@ cudaError_t enqueue_step(swe_handle *s, cudaStream_t st) {
     if (e == cudaSuccess) e = enqueue_fused(s, 1, st);
     return e;
   }
-  for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
-    if (s->prec == SWE_F64) e = launch_stage<double>(s->tile, field_of<double>(s), s->phys, s->sc, stage, st, s->maps);
-    else e = launch_stage<float>(s->tile, field_of<float>(s), s->phys, s->sc, stage, st, s->maps);
-  }
+  for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) e = launch_one_stage(s, stage, st);
   return e;
 }
 
@@ -242,6 +248,9 @@ bool valid_params(const swe_params *p) {
   if (!std::isfinite(p->z_ref) || !std::isfinite(p->fixed_dt)) return false;
   if (p->tile < 0 || p->tile > num_shapes()) return false;
   if (p->fused_step != 0 && p->fused_step != 1) return false;
+  if (p->shore != 0 && p->shore != 1) return false;
+  if (p->shore && p->fused_step) return false;  // the fused step has WENO faces only
+  if (p->shore && p->tile != 0 && p->tile != shore_shape(p->precision == SWE_F64 ? 8 : 4)) return false;
   if (p->fused_step) {
     for (int k = 0; k < 4; ++k)
       if (p->bc[k] == SWE_BC_PERIODIC) return false;  // the fused step has wall and inflow ghosts only
@@ -337,7 +346,8 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   s->prm = *params;
   s->prec = params->precision;
   s->elem = s->prec == SWE_F64 ? 8 : 4;
-  if (params->tile > 0) s->tile = params->tile;
+  if (params->shore) s->tile = shore_shape((int)s->elem);  // the shoreline kernels' one shape
+  else if (params->tile > 0) s->tile = params->tile;
   else {
     const int cached = swe_autotune_lookup(params->precision, 0, (double)grid->nx * grid->ny);
     s->tile = cached > 0 ? cached : 1;
@@ -416,6 +426,10 @@ int swe_create(const swe_grid *grid, double dx, double dy, const double *bathyme
   if (rc == SWE_OK && cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) rc = SWE_ECUDA;
   if (rc == SWE_OK) {
     e = s->prec == SWE_F64 ? prepare_shape<double>(s->tile) : prepare_shape<float>(s->tile);
+    rc = cuda_check(s, e);
+  }
+  if (rc == SWE_OK && params->shore) {
+    e = s->prec == SWE_F64 ? prepare_shore<double>() : prepare_shore<float>();
     rc = cuda_check(s, e);
   }
   if (rc == SWE_OK && params->fused_step) {
@@ -751,9 +765,7 @@ int swe_time_stages(swe_handle *s, int32_t n, double cfl, double *ms_total, doub
   for (int32_t it = 0; it < n && e == cudaSuccess && !s->prm.fused_step; ++it) {
     e = cudaEventRecord(ev[0], s->stream);
     for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
-      if (s->prec == SWE_F64)
-        e = launch_stage<double>(s->tile, field_of<double>(s), s->phys, s->sc, stage, s->stream, s->maps);
-      else e = launch_stage<float>(s->tile, field_of<float>(s), s->phys, s->sc, stage, s->stream, s->maps);
+      e = launch_one_stage(s, stage, s->stream);
       if (e == cudaSuccess) e = cudaEventRecord(ev[stage], s->stream);
     }
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);

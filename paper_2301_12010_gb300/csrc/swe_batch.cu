@@ -170,6 +170,7 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
   if (!out || !params || nslots < 1 || nslots > 4096 || hbm_budget_bytes == 0) return SWE_EINVAL;
   if (params->precision != SWE_F32) return SWE_EINVAL;  // the batch path is FP32
   if (params->fused_step) return SWE_EINVAL;             // and runs the paper's per-stage alpha
+  if (params->shore) return SWE_EINVAL;                  // and its WENO faces
   if (!valid_params(params)) return SWE_EINVAL;          // sides and physics as for one scenario
   swe_batch *b = new (std::nothrow) swe_batch();
   if (!b) return SWE_ENOMEM;

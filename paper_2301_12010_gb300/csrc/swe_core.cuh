@@ -702,7 +702,17 @@ struct Window {
 // db = 12 (bhat(k+1) - bhat(k)).  Adds ew times the mass flux sum Fs_0
 // through the domain edges that the strip owns (face -1/2 at k = 0 of the
 // first strip, face n-1/2 at k >= 1).
-template <typename T, int S, bool XP, int FIELD, typename E>
+//
+// SHORE (the shoreline variant): a face whose six window cells hold a dry
+// cell takes the first-order hydrostatic reconstruction (Audusse et al.,
+// 2004) instead of the WENO values: face bed b_f = max(b_L, b_R), face depths
+// h*_s = max(0, h_s + b_s - b_f), the global-LF flux of the standard SWE flux
+// of those states with this line's alpha; each side s sees the normal
+// momentum flux raised by g (h_s^2 - h*_s^2 - d_s^2)/2 and the bed value b_s
+// (the cell update then adds g (h_s - d_s) b_s), which puts a lake at rest
+// beside dry land in balance at any level at or below z_ref.  The face values
+// enter the differences as corrections to the WENO values of the face.
+template <typename T, int S, bool XP, int FIELD, typename E, bool SHORE = false>
 __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T *bqt, const T *bb, int o0, int st,
                                             T alpha, const Consts<T> &K, const Phys &p, int ia, int n, bool edge_ok,
                                             T ew, const E &emit, T &edge) {
@@ -745,33 +755,102 @@ __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T 
       b = ok ? bb[o] : T(0);
     }
   };
+  // SHORE: bit s of `dry` flags window slot s as dry; (c0, c1, c2, cb) the
+  // corrections of the previous face as its right-hand cell sees them
+  unsigned dry = 0u;
+  T r0 = T(0), r1 = T(0), r2 = T(0), rb = T(0);
+  auto note = [&](T ha_, T b_) {
+    if constexpr (SHORE)
+      dry = (dry >> 1) | (Num<T>::below(ha_ + still_depth(b_, zref), p.h_dry32, p.h_dry) ? 32u : 0u);
+  };
   T ha, qn, qt, b;
   cell(0, ha, qn, qt, b);
+  note(ha, b);
   win.template put<0>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
   cell(1, ha, qn, qt, b);
+  note(ha, b);
   win.template put<1>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
   cell(2, ha, qn, qt, b);
+  note(ha, b);
   win.template put<2>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
   cell(3, ha, qn, qt, b);
+  note(ha, b);
   win.template put<3>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
   cell(4, ha, qn, qt, b);
+  note(ha, b);
   win.template put<4>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
 #pragma unroll
   for (int k = 0; k <= S; ++k) {
     cell(k + 5, ha, qn, qt, b);
+    note(ha, b);
     win.template put<5>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
     V2 x01;
     T x2, x3;
     win.face(x01, x2, x3);
+    // corrections of this face as its left (l*) and right (r*) cells see them
+    T l0 = T(0), l1 = T(0), l2 = T(0), lb = T(0), n0 = T(0), n1 = T(0), n2 = T(0), nb = T(0);
+    bool hr = false;
+    if constexpr (SHORE) {
+      hr = (dry & 63u) != 0u;
+      if (hr) {
+        T haL, qnL, qtL, bL, haR, qnR, qtR, bR;
+        cell(k + 2, haL, qnL, qtL, bL);  // window slot 2: the face's left cell
+        cell(k + 3, haR, qnR, qtR, bR);  // window slot 3: its right cell
+        const T dL = still_depth(bL, zref), dR = still_depth(bR, zref);
+        const T hL = haL + dL, hR = haR + dR;
+        T uL = T(0), vL = T(0), uR = T(0), vR = T(0);
+        if (!Num<T>::below(hL, p.h_dry32, p.h_dry)) { uL = qnL / hL; vL = qtL / hL; }
+        if (!Num<T>::below(hR, p.h_dry32, p.h_dry)) { uR = qnR / hR; vR = qtR / hR; }
+        const T bf = bL > bR ? bL : bR;
+        T sL = hL + bL - bf, sR = hR + bR - bf;
+        sL = sL > T(0) ? sL : T(0);
+        sR = sR > T(0) ? sR : T(0);
+        const T g2 = T(0.5) * K.g, ah = T(0.5) * alpha;
+        const T qL = sL * uL, qR = sR * uR;
+        const T F0 = T(0.5) * (qL + qR) - ah * (sR - sL);
+        const T F1 = T(0.5) * (qL * uL + g2 * sL * sL + qR * uR + g2 * sR * sR) - ah * (qR - qL);
+        const T F2 = T(0.5) * (qL * vL + qR * vR) - ah * (sR * vR - sL * vL);
+        // the WENO values of this face, carried: Fs_c = 6 (f+_c(2) + f-_c(3)) + X_c
+        const V2 fp2 = vsub(vsub(vsub(win.lp01, win.dp01[5]), win.dp01[4]), win.dp01[3]);
+        const V2 fm3 = vsub(vsub(win.lm01, win.dm01[5]), win.dm01[4]);
+        const V2 w01 = vfma(sp<V2>(6.0), vadd(fp2, fm3), x01);
+        const T w2 = fma(T(6), (win.lp2 - win.dp2[5] - win.dp2[4] - win.dp2[3]) + (win.lm2 - win.dm2[5] - win.dm2[4]),
+                         x2);
+        const T wb = fma(T(6), (win.lb - win.db[5] - win.db[4] - win.db[3]) + (win.lb - win.db[5] - win.db[4]), x3);
+        const T c6 = T(10.392304845413264);  // 6 sqrt 3
+        l0 = n0 = c6 * F0 - w01.x;
+        l2 = n2 = c6 * F2 - w2;
+        l1 = c6 * (F1 + g2 * (hL * hL - sL * sL - dL * dL)) - w01.y;
+        n1 = c6 * (F1 + g2 * (hR * hR - sR * sR - dR * dR)) - w01.y;
+        lb = T(12) * bL - wb;
+        nb = T(12) * bR - wb;
+      }
+    }
     if (edge_ok && ((k == 0 && ia == 0) || (k > 0 && ia + k == n))) {
-      const T fe = win.edge_flux(x01) * ew;
+      T fs = win.edge_flux(x01);
+      if constexpr (SHORE) fs += l0;  // the face's mass flux, either form
+      const T fe = fs * ew;
       edge += (k == 0) ? fe : -fe;
     }
     if (k > 0) {
-      const V2 d01 = vfma(sp<V2>(6.0), vadd(win.dp01[2], win.dm01[3]), vsub(x01, win.xp01));
-      emit(k - 1, d01.x, d01.y, fma(T(6), win.dp2[2] + win.dm2[3], x2 - win.xp2),
-           fma(T(6), win.db[2] + win.db[3], x3 - win.xb));
+      V2 d01 = vfma(sp<V2>(6.0), vadd(win.dp01[2], win.dm01[3]), vsub(x01, win.xp01));
+      T d2 = fma(T(6), win.dp2[2] + win.dm2[3], x2 - win.xp2);
+      T dbk = fma(T(6), win.db[2] + win.db[3], x3 - win.xb);
+      if constexpr (SHORE) {
+        d01.x += l0 - r0;
+        d01.y += l1 - r1;
+        d2 += l2 - r2;
+        dbk += lb - rb;
+      }
+      emit(k - 1, d01.x, d01.y, d2, dbk);
     }
+    if constexpr (SHORE) {
+      r0 = n0;
+      r1 = n1;
+      r2 = n2;
+      rb = nb;
+    }
+    (void)hr;
     win.xp01 = x01;
     win.xp2 = x2;
     win.xb = x3;
@@ -880,7 +959,7 @@ struct CellEpilogue {
 // followed by the post-stage rule, with L of Eq. (7).  Pass 0 sweeps x and
 // stores L_x; pass 1 sweeps y, adds L_y and the sources and updates.  The
 // pass loop is unrolled, so each pass runs code specialised for its frame.
-template <typename T, int TX, int TY, int NT, int S, int STAGE>
+template <typename T, int TX, int TY, int NT, int S, int STAGE, bool SHORE = false>
 __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p, int i0, int j0, const T *box,
                                              T *sL, T tdt, T rcap, T alx, T aly, Acc<T> &acc) {
   using G = TileGeom<T, TX, TY>;
@@ -924,7 +1003,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
       }
     }
     const CellEpilogue<T, TX, TY, S, STAGE> emit{io, p, K, box, sL, X, xr, xc0, yc, yr0, i, j0, tdt, rcap, wrk, friction, u0, acc};
-    sweep_strip<T, S, X, G::FIELD>(bha, X ? bhu : bhv, X ? bhv : bhu, bb,
+    sweep_strip<T, S, X, G::FIELD, CellEpilogue<T, TX, TY, S, STAGE>, SHORE>(bha, X ? bhu : bhv, X ? bhv : bhu, bb,
                          X ? (xr + G::OY) * G::P + xc0 + G::OX - 3 : yr0 * G::P + yc + G::OX,
                          X ? 1 : G::P, X ? alx : aly, K, p, X ? i0 + xc0 : j0 + yr0, X ? nx : ny,
                          X ? (j0 + xr < ny) : (i < nx), X ? K.ewx : K.ewy, emit, acc.edge);
@@ -1053,7 +1132,7 @@ __device__ __noinline__ void publish(const Phys &p, DevScalars *sc, bool lead, R
 // current tile is computed.  Each buffer has an mbarrier; every thread waits
 // on it with a bounded spin (on expiry the CTA flags ST_TIMEOUT and returns,
 // no other copy being in flight at that point).
-template <typename T, int TX, int TY, int NT, int S, int STAGE>
+template <typename T, int TX, int TY, int NT, int S, int STAGE, bool SHORE = false>
 __device__ void stage_persistent(const StageIO<T> &io, const BoxMaps &maps, const Phys &p, DevScalars *sc, T *smem,
                                  RedSmem &red, int first, int stride, bool lead) {
   using G = TileGeom<T, TX, TY>;
@@ -1115,7 +1194,7 @@ __device__ void stage_persistent(const StageIO<T> &io, const BoxMaps &maps, cons
       patch_box<T, TX, TY, NT>(io, p, i0, j0, box, zref, eta_in, u_in);
       __syncthreads();
     }
-    tile_compute<T, TX, TY, NT, S, STAGE>(io, p, i0, j0, box, sL, tdt, rcap, alx, aly, acc);
+    tile_compute<T, TX, TY, NT, S, STAGE, SHORE>(io, p, i0, j0, box, sL, tdt, rcap, alx, aly, acc);
   }
   publish<T, NT, STAGE>(p, sc, lead, red, dt, acc);
 }

@@ -100,6 +100,15 @@ cudaError_t launch_fused(const Field<T> &fd, int from, const Phys &p, DevScalars
                          cudaStream_t st, cudaEvent_t *ev = nullptr);
 size_t fused_smem(int elem_bytes);
 
+// The shoreline variant's stage kernels (swe_shore.cu): one compiled tile
+// shape per precision (shore_shape), the handle's tensor maps built for it.
+int shore_shape(int elem_bytes);
+template <typename T>
+cudaError_t prepare_shore();
+template <typename T>
+cudaError_t launch_shore(const Field<T> &fd, const Phys &p, DevScalars *sc, int stage, cudaStream_t st,
+                         const BoxMaps *maps);
+
 template <typename T>
 cudaError_t prepare_shape(int k);
 // Tensor maps of the halo-box copies for shape k: out[s] covers the input

@@ -274,6 +274,7 @@ int swe_multi_create(const swe_grid *grid, double dx, double dy, const double *b
   if (out) *out = nullptr;
   if (!grid || !out || !bathymetry || !valid_multi_params(params)) return SWE_EINVAL;
   if (params->fused_step) return SWE_EINVAL;  // strips exchange halos between the stages
+  if (params->shore) return SWE_EINVAL;       // strips run the paper's WENO faces
   if (grid->nx < 3 || grid->ny < 3 || !(dx > 0.0) || !(dy > 0.0) || nparts < 1 || nparts > 64) return SWE_EINVAL;
   if ((long long)grid->nx * grid->ny > (1ll << 31)) return SWE_EINVAL;
   int r0 = 0, rn = 0;

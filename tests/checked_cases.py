@@ -87,6 +87,13 @@ def main():
     fdem = W.coastal_dem(n=96, dx=150.0, t0=500.0).copy(alpha_margin=1.1)
     compare("fused inflow DEM 96", fdem, 20, swe.F32)
     compare("fused inflow DEM 96", fdem, 20, swe.F64)
+    # the shoreline variant (hydrostatic-reconstruction faces at dry cells)
+    for shape in [(3, 3), (37, 19), (77, 45), (200, 33)]:
+        sc = ragged(*shape).copy(shore=1)
+        sc.h[::5, ::3] = 0.0
+        compare("shore ragged %dx%d" % shape, sc, 6, swe.F32)
+        compare("shore ragged %dx%d" % shape, sc, 6, swe.F64)
+    compare("shore inflow DEM 96", W.coastal_dem(n=96, dx=150.0, t0=500.0).copy(shore=1), 20, swe.F32)
     # the batch kernel over a mix of small coasts
     ens = W.mitigation_ensemble(count=5, seed=41, nx_range=(96, 192), ny_range=(32, 128), land_width=90.0)
     with swe.Batch(len(ens), 1 << 30, ens[0], stream=ST) as b:

@@ -67,6 +67,12 @@ def test_invalid_arguments_rejected_without_gpu(swe):
         q.fused_step = 1
         setattr(q, field, value)
         assert swe.lib.swe_create(ctypes.byref(swe.Grid(4, 4)), 1.0, 1.0, dp, ctypes.byref(q), ctypes.byref(h)) == swe.EINVAL
+    # the shoreline variant: its own tile shape only, not with the fused step
+    for field, value in (("shore", 2), ("tile", 1), ("fused_step", 1)):
+        q = swe.Params.from_buffer_copy(p)
+        q.shore = 1
+        setattr(q, field, value)
+        assert swe.lib.swe_create(ctypes.byref(swe.Grid(4, 4)), 1.0, 1.0, dp, ctypes.byref(q), ctypes.byref(h)) == swe.EINVAL
     q = swe.Params.from_buffer_copy(p)
     q.fused_step = 1
     q.bc[0] = q.bc[1] = swe.PERIODIC
@@ -101,6 +107,9 @@ def test_batch_arguments_rejected_without_gpu(swe):
     assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
     q = swe.Params.from_buffer_copy(p)
     q.bc[2] = swe.PERIODIC  # periodic sides come in pairs
+    assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
+    q = swe.Params.from_buffer_copy(p)
+    q.shore = 1  # the batch runs the paper's WENO faces
     assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
     q = swe.Params.from_buffer_copy(p)
     q.fused_step = 1  # the batch runs the per-stage alpha
