@@ -389,7 +389,7 @@ static void shore_faces(const or_params *p, int n, double alpha, int mom, const 
       const int k = side[s];
       double u, v;
       velocity(p, hl[k], ql[k], tl[k], &u, &v); /* u: normal, v: tangential velocity */
-      hs[s] = hl[k] + bl[k] - bf;
+      hs[s] = hl[k] + (bl[k] - bf);
       if (hs[s] < 0.0) hs[s] = 0.0;
       U[s][0] = hs[s];
       U[s][mom] = hs[s] * u;

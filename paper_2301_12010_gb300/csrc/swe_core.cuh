@@ -802,7 +802,7 @@ __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T 
         if (!Num<T>::below(hL, p.h_dry32, p.h_dry)) { uL = qnL / hL; vL = qtL / hL; }
         if (!Num<T>::below(hR, p.h_dry32, p.h_dry)) { uR = qnR / hR; vR = qtR / hR; }
         const T bf = bL > bR ? bL : bR;
-        T sL = hL + bL - bf, sR = hR + bR - bf;
+        T sL = hL + (bL - bf), sR = hR + (bR - bf);  // bed difference first: films keep their digits
         sL = sL > T(0) ? sL : T(0);
         sR = sR > T(0) ? sR : T(0);
         const T g2 = T(0.5) * K.g, ah = T(0.5) * alpha;

@@ -27,7 +27,7 @@ from tests.test_oracle_pins import _standing_wave_case  # noqa: E402
 from tests.test_oracle_shore_pins import _two_lakes  # noqa: E402
 
 
-def _check(sc, steps, precision, name):
+def _check(sc, steps, precision, name, still=False):
     ref = run_oracle(sc, steps)
     rd = ref.diag()
     h, hu, hv, d, (m, cm) = run_gpu(sc, steps, precision)
@@ -42,7 +42,8 @@ def _check(sc, steps, precision, name):
             assert abs(d["runup_max"] - rd["runup_max"]) <= 1e-10, name
     else:
         assert rel_l2(eta_tilde(h, sc.b), eta_tilde(ref.h, sc.b)) <= 1e-4, name
-        assert rel_l2(hu, ref.hu) <= 1e-4 and rel_l2(hv, ref.hv) <= 1e-4, name
+        if not still:  # (water at rest: the momenta are round-off on both sides)
+            assert rel_l2(hu, ref.hu) <= 1e-4 and rel_l2(hv, ref.hv) <= 1e-4, name
         assert abs(m - rd["mass"]) <= 1e-6 * m, name
         if rd["runup_max"] > -np.inf:
             assert abs(d["runup_max"] - rd["runup_max"]) <= 0.01, name
@@ -54,7 +55,7 @@ def test_two_lakes_at_rest_beside_dry_land(precision):
     sc, level = _two_lakes()
     sc = dataclasses.replace(sc, shore=1)
     wet = sc.h > 0
-    h, hu, hv, d = _check(sc, 100, precision, "two lakes")
+    h, hu, hv, d = _check(sc, 100, precision, "two lakes", still=True)
     tol = 1e-12 if precision == swe.F64 else 2e-6
     assert np.abs((h + sc.b - level)[wet]).max() <= tol
     assert np.abs(hu).max() <= tol * 10 and np.abs(hv).max() <= tol * 10
@@ -64,10 +65,13 @@ def test_two_lakes_at_rest_beside_dry_land(precision):
 def test_standing_wave_shoreline(precision):
     sc, amp, L, slope, r, T = _standing_wave_case()
     sc = dataclasses.replace(sc, shore=1)
+    probe = oracle.Simulation(sc)
+    probe.run_until(0.5 * T)  # the step count that reaches T/2 (its last step shortened)
+    n = probe.diag()["steps"]
+    ref = oracle.Simulation(sc)
+    ref.step(n)  # n full CFL steps, as the GPU takes them
     with swe.Solver(sc, precision=precision, stream=stream()) as s:
-        ref = oracle.Simulation(sc)
-        ref.run_until(0.5 * T)
-        s.step(ref.diag()["steps"])
+        s.step(n)
         h, hu, hv = s.get_state()
     if precision == swe.F64:
         assert np.abs(h - ref.h).max() <= 1e-10 and np.abs(hu - ref.hu).max() <= 1e-10
