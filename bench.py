@@ -271,6 +271,30 @@ def fused_bench(swe, W, torch, sc, steps: int = 20, margin: float = 1.1, warmup:
     return out
 
 
+def shore_bench(swe, W, torch, sc, steps: int = 20, warmup: int = 4, per_stage_ms: float = 0.0):
+    """The shoreline variant on the same workload (hydrostatic-reconstruction
+    faces wherever a stencil meets a dry cell: the DEM's land and its wet/dry
+    front); its one compiled tile shape (96 x 32 in FP32)."""
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with swe.Solver(sc.copy(shore=1), precision=swe.F32, stream=stream.cuda_stream) as s:
+        s.step(warmup)
+        s.sync()
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.sync()
+        ms = e0.elapsed_time(e1) / steps
+    dry = float((sc.h < sc.h_dry).mean())
+    out = {"value": sc.cells / (ms / 1e3), "unit": "cell-updates/s", "steps": steps, "ms_per_step": ms,
+           "dtype": "f32", "dry_cell_fraction": dry,
+           "scheme": "shoreline variant: hydrostatic-reconstruction faces next to dry cells, WENO elsewhere"}
+    if per_stage_ms > 0:
+        out["speed_vs_stage_kernels"] = per_stage_ms / ms
+    return out
+
+
 def profile_fused_case(n: int = 2048) -> int:
     """A few fused steps on the n x n coastal DEM, for ncu; no timing."""
     import torch
@@ -502,6 +526,7 @@ def main():
                          "and on one walled 2048x2048 DEM (strided order), then the same DEM by the "
                          "single-scenario kernels: a short case for a profiler")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused-step variant's measurement")
+    ap.add_argument("--no-shore", action="store_true", help="skip the shoreline variant's measurement")
     ap.add_argument("--profile-fused", action="store_true",
                     help="only four fused steps on the --n coastal DEM: a short case for a profiler")
     ap.add_argument("--config-table", action="store_true",
@@ -657,6 +682,8 @@ def main():
         if ws == 1 and not args.no_fused:
             line["fused_step"] = fused_bench(swe, W, torch, sc, per_stage_ms=ms_max / args.steps,
                                              hbm_peak=hbm_peak)
+        if ws == 1 and not args.no_shore:
+            line["shore_step"] = shore_bench(swe, W, torch, sc, per_stage_ms=ms_max / args.steps)
         if ws == 1 and not args.no_fp64:
             line["fp64"] = fp64_bench(swe, W, torch, sc)
         if ws == 1 and not args.no_ensemble:
