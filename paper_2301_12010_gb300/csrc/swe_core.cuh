@@ -786,12 +786,19 @@ __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T 
     win.template put<5>(ha, qn, qt, b, sa, pg, zref, eps2, eps1, p);
     V2 x01;
     T x2, x3;
-    win.face(x01, x2, x3);
     // corrections of this face as its left (l*) and right (r*) cells see them
     T l0 = T(0), l1 = T(0), l2 = T(0), lb = T(0), n0 = T(0), n1 = T(0), n2 = T(0), nb = T(0);
     bool hr = false;
+    if constexpr (SHORE) hr = (dry & 63u) != 0u;
+    if (!hr) {
+      win.face(x01, x2, x3);
+    } else {
+      // the WENO corrections X of a face that the hydrostatic values replace
+      // cancel from the cells' differences whatever they are: zero
+      x01 = sp<V2>(0.0);
+      x2 = x3 = T(0);
+    }
     if constexpr (SHORE) {
-      hr = (dry & 63u) != 0u;
       if (hr) {
         T haL, qnL, qtL, bL, haR, qnR, qtR, bR;
         cell(k + 2, haL, qnL, qtL, bL);  // window slot 2: the face's left cell
