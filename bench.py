@@ -49,11 +49,11 @@ BYTES_PER_CELL_STAGE = {1: 28.0, 2: 40.0, 3: 40.0}
 NCU_CAPTURE = {"tile": 7, "cells": 4096 * 4096,
                "profile": "profiles/stage_kernel_f32_coastal_dem_4096_dram.md, "
                           "profiles/stage_kernel_f32_coastal_dem_2048_pipes.md",
-               "dram_bytes": {1: 269505280 + 166957824, 2: 470996992 + 176492800, 3: 470738944 + 165443840},
+               "dram_bytes": {1: 269528064 + 167055872, 2: 470991104 + 176387072, 3: 470633216 + 165647104},
                "thread_inst_per_cell": {1: 566.3, 2: 593.1, 3: 601.1},
-               "issue_active_pct": {1: 61.10, 2: 62.65, 3: 63.24},
+               "issue_active_pct": {1: 61.13, 2: 62.72, 3: 63.54},
                "sources": ("swe_core.cuh", "swe_kernels.cu", "swe_launch.h:SWE_SHAPES"),
-               "sha256": "11eefae8c7d6ad239067734ddc0f013bbce0e78ff3471040d9ddc0ab32445b42"}
+               "sha256": "b752e6bb6b0fd3f0f49b5412dd8a5de491946f9681b52c6d324ef25b0b3c653f"}
 
 
 def kernel_sources_sha256() -> str:
