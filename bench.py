@@ -614,24 +614,25 @@ def main():
     counters = ncu_counters(diag["tile"], dom, cells)
 
     # end to end through the public API: every step uploads its input state
-    # from pinned host FP64 arrays (swe_set_state), advances one step and reads
-    # its result back into pinned host FP64 arrays (bytes counted from the
-    # arrays copied).  Pipelined: swe_get_state_async lets the next step's
-    # upload overlap this step's read-back; the last read-back is waited for
-    # inside the timed region.  The fully synchronous loop is reported beside it.
+    # from pinned host FP64 arrays, advances one step and reads its result back
+    # into pinned host FP64 arrays (bytes counted from the arrays copied).
+    # Pipelined: swe_set_state_async and swe_get_state_async let copy engines
+    # carry the next step's input and this step's result while the step runs;
+    # the last read-back is waited for inside the timed region.  The fully
+    # synchronous loop is reported beside it.
     pin = [torch.empty((sc.ny, sc.nx), dtype=torch.float64, pin_memory=True) for _ in range(6)]
     for a, src in zip(pin[:3], (sc.h, sc.hu, sc.hv)):
         a.numpy()[...] = src
     hin = [a.numpy() for a in pin[:3]]
     hout = tuple(a.numpy() for a in pin[3:])
-    solver.set_state(*hin)
+    solver.set_state_async(*hin)
     solver.step(1)
     solver.get_state_async(hout)
     solver.wait_state()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        solver.set_state(*hin)
+        solver.set_state_async(*hin)
         solver.step(1)
         solver.get_state_async(hout)
     solver.wait_state()
@@ -673,8 +674,9 @@ def main():
             "clocks": clk,
             "e2e": {"value": e2e_v, "unit": "cell-updates/s", "h2d_bytes_per_step": 3 * 8 * cells,
                     "d2h_bytes_per_step": 3 * 8 * cells,
-                    "how": "per step swe_set_state(pinned FP64 host) + swe_step(1) + swe_get_state_async(pinned "
-                           "FP64 host), the read-back overlapping the next upload; swe_wait_state at the end",
+                    "how": "per step swe_set_state_async(pinned FP64 host) + swe_step(1) + swe_get_state_async("
+                           "pinned FP64 host): copy engines carry the next input and the last result while the "
+                           "step runs; swe_wait_state at the end",
                     "sequential_value": e2e_seq,
                     "sequential_how": "per step swe_set_state + swe_step(1) + swe_get_state, all synchronous"},
             "sim": {"t": diag["t"], "steps": diag["steps"], "last_dt": diag["last_dt"]},

@@ -127,6 +127,18 @@ int swe_set_state(swe_handle *s, const double *h, const double *hu, const double
  * owned by the caller, read on the handle's stream). */
 int swe_set_state_device(swe_handle *s, const void *h, const void *hu, const void *hv);
 
+/* Asynchronous form of swe_set_state for page-locked host FP64 arrays
+ * [ny][nx] (cudaHostAlloc, cudaHostRegister, a pinned torch tensor): returns
+ * at once; copy engines carry the arrays to the device on a second stream
+ * (overlapping steps and read-backs already enqueued), and the conversion
+ * into the state, the wave speeds and the runup follow on the handle's
+ * stream, so that the next swe_step uses the new state.  The time is kept.
+ * The arrays must stay unchanged until the next synchronising call
+ * (swe_sync, swe_get_state, swe_wait_state, swe_diagnostics).  Pageable
+ * arrays: swe_set_state (synchronous).  Allocates its staging (3 FP64
+ * planes) at the first call; SWE_ENOMEM leaves the handle usable. */
+int swe_set_state_async(swe_handle *s, const double *h, const double *hu, const double *hv);
+
 /* Enqueue n RK3 steps (Eq. (8)) on the handle's stream.  Each step runs three
  * stage kernels; the time step is dt = cfl / (alpha_x/dx + alpha_y/dy) from
  * the step's first stage (ignored if fixed_dt > 0).  Asynchronous: no host

@@ -71,6 +71,7 @@ def _load() -> ctypes.CDLL:
                             ctypes.POINTER(H)]),
         "swe_set_state": (ip, [H, dp, dp, dp]),
         "swe_set_state_device": (ip, [H, vp, vp, vp]),
+        "swe_set_state_async": (ip, [H, dp, dp, dp]),
         "swe_step": (ip, [H, ctypes.c_int32, ctypes.c_double]),
         "swe_sync": (ip, [H]),
         "swe_get_state": (ip, [H, dp, dp, dp]),
@@ -229,6 +230,16 @@ class Solver:
     def set_state(self, h, hu, hv) -> None:
         a = [np.ascontiguousarray(x, dtype=np.float64) for x in (h, hu, hv)]
         _check(lib.swe_set_state(self._h, *[_dp(x) for x in a]), "swe_set_state")
+
+    def set_state_async(self, h, hu, hv) -> None:
+        """Upload a state from page-locked float64 arrays without waiting
+        (swe_set_state_async); the arrays must stay unchanged until the next
+        synchronising call.  Pageable arrays are uploaded synchronously."""
+        for x in (h, hu, hv):
+            if x.dtype != np.float64 or not x.flags.c_contiguous or x.shape != (self.ny, self.nx):
+                raise ValueError("set_state_async needs contiguous float64 arrays of shape (ny, nx)")
+        self._async_in = (h, hu, hv)  # kept alive until the upload is done
+        _check(lib.swe_set_state_async(self._h, *[_dp(x) for x in (h, hu, hv)]), "swe_set_state_async")
 
     def set_state_device(self, h, hu, hv) -> None:
         """From device tensors (torch) of the solver's precision, contiguous [ny][nx]."""

@@ -67,6 +67,14 @@ struct swe_handle {
   cudaEvent_t ev_snap = nullptr;  // snapshot taken
   cudaEvent_t ev_done = nullptr;  // read-back finished (snapshot free again)
   bool pending = false;
+  // asynchronous upload (swe_set_state_async): copy engines carry the host FP64
+  // state into instage on the upload stream; the conversion into U^n runs on
+  // the caller's stream after it
+  double *instage = nullptr;      // three FP64 [ny][nx] planes
+  cudaStream_t upl = nullptr;     // upload stream (non-blocking)
+  cudaEvent_t ev_up = nullptr;    // upload landed
+  cudaEvent_t ev_used = nullptr;  // instage converted (free for the next upload)
+  bool up_used = false;
 };
 
 namespace {
@@ -473,6 +481,68 @@ int swe_set_state_device(swe_handle *s, const void *h, const void *hu, const voi
   return after_state_change(s);
 }
 
+int swe_set_state_async(swe_handle *s, const double *h, const double *hu, const double *hv) {
+  const TraceRange trace("swe_set_state_async");
+  if (!s || !h || !hu || !hv) return SWE_EINVAL;
+  if (s->sticky != SWE_OK) return s->sticky;
+  const size_t n = (size_t)s->nx * s->ny, nb = sizeof(double) * n;
+  if (!pinned_device_ptr(h, nb) || !pinned_device_ptr(hu, nb) || !pinned_device_ptr(hv, nb))
+    return swe_set_state(s, h, hu, hv);  // pageable: synchronous
+  cudaError_t e = cudaSuccess;
+  if (!s->instage) {  // first asynchronous upload: its buffers, stream and events
+    double *st = nullptr;
+    cudaStream_t us = nullptr;
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    e = dev_malloc((void **)&st, 3 * nb);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&e2, cudaEventDisableTiming);
+    if (e != cudaSuccess) {  // nothing half-made stays behind
+      if (e2) cudaEventDestroy(e2);
+      if (e1) cudaEventDestroy(e1);
+      if (us) cudaStreamDestroy(us);
+      if (st) cudaFree(st);
+      if (e == cudaErrorMemoryAllocation) {  // no room now: the handle is unchanged and usable
+        (void)cudaGetLastError();
+        return SWE_ENOMEM;
+      }
+      return cuda_check(s, e);
+    }
+    s->instage = st;
+    s->upl = us;
+    s->ev_up = e1;
+    s->ev_used = e2;
+  }
+  // the copy engines fill the staging planes once the previous upload's
+  // conversion is done with them; the conversion into U^n follows on the
+  // caller's stream, after the work enqueued so far (steps, a snapshot)
+  if (s->up_used) e = cudaStreamWaitEvent(s->upl, s->ev_used, 0);
+  const double *src[3] = {h, hu, hv};
+  for (int f = 0; f < 3 && e == cudaSuccess; ++f)
+    e = cudaMemcpyAsync(s->instage + f * n, src[f], nb, cudaMemcpyHostToDevice, s->upl);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_up, s->upl);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_up, 0);
+  void *dst[3] = {s->h[0], s->hu[0], s->hv[0]};
+  for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
+    if (s->prec == SWE_F64)
+      e = import_plane<double>(s->instage + f * n, true, (double *)dst[f], f == 0 ? (const double *)s->b : nullptr,
+                               s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
+    else
+      e = import_plane<float>(s->instage + f * n, true, (float *)dst[f], f == 0 ? (const float *)s->b : nullptr,
+                              s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_used, s->stream);
+  if (e == cudaSuccess) s->up_used = true;
+  // the scalars of the new state, on the stream: time kept, the rest cleared,
+  // wave speeds and runup of U^n
+  if (s->cfl_dev <= 0) s->cfl_dev = 0.4;
+  if (e == cudaSuccess) e = reset_scalars(s->sc, s->cta, NAN, s->cfl_dev, 0.0, s->stream);
+  if (e == cudaSuccess)
+    e = s->prec == SWE_F64 ? state_stats<double>(field_of<double>(s), s->phys, s->sc, s->stream)
+                           : state_stats<float>(field_of<float>(s), s->phys, s->sc, s->stream);
+  return cuda_check(s, e);
+}
+
 int swe_step(swe_handle *s, int32_t n, double cfl) {
   const TraceRange trace("swe_step");
   if (!s || n < 0) return SWE_EINVAL;
@@ -726,6 +796,13 @@ int swe_destroy(swe_handle *s) {
     cudaStreamSynchronize(s->xfer);
     cudaStreamDestroy(s->xfer);
   }
+  if (s->upl) {
+    cudaStreamSynchronize(s->upl);
+    cudaStreamDestroy(s->upl);
+  }
+  if (s->ev_up) cudaEventDestroy(s->ev_up);
+  if (s->ev_used) cudaEventDestroy(s->ev_used);
+  if (s->instage) cudaFree(s->instage);
   if (s->ev_snap) cudaEventDestroy(s->ev_snap);
   if (s->ev_done) cudaEventDestroy(s->ev_done);
   if (s->snap) cudaFree(s->snap);

@@ -64,12 +64,13 @@ __global__ void k_reset(DevScalars *sc, DevPartials *part, double t, double cfl,
     part->edge[b] = 0.0;
   }
   if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double tk = t == t ? t : sc->t;  // NaN: keep the current time
     sc->part = part;
     sc->check = 0ull;
     for (int s = 0; s < 3; ++s) sc->alpha[s][0] = sc->alpha[s][1] = 0ull;
     sc->dt = 0.0;
-    sc->t = t;
-    sc->t_step = t;
+    sc->t = tk;
+    sc->t_step = tk;
     sc->steps = 0;
     sc->runup_now[0] = sc->runup_now[1] = 0ull;
     sc->runup_max = 0ull;

@@ -74,8 +74,9 @@ cudaError_t export_plane(const T *src, void *dst, bool dst_f64, const T *bed_for
 // directly across the host link, with no staging copy.  nullptr otherwise
 // (pageable memory takes the staging copy).
 const void *pinned_device_ptr(const void *p, size_t bytes);
-// Reset a scenario's device scalars (time t, CFL number, horizon t_end) and
-// clear its per-CTA partials `part`, which the scalars then point to.
+// Reset a scenario's device scalars (time t, or the current time if t is
+// NaN; CFL number; horizon t_end) and clear its per-CTA partials `part`,
+// which the scalars then point to.
 cudaError_t reset_scalars(DevScalars *sc, DevPartials *part, double t, double cfl, double t_end, cudaStream_t st);
 cudaError_t set_cfl(DevScalars *sc, double cfl, cudaStream_t st);
 // A scenario's clamp and edge volumes: its per-CTA FP64 running sums added

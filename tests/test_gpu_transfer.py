@@ -102,3 +102,43 @@ def test_async_read_back_into_pageable_arrays_is_synchronous():
         for x, y in zip(out, ref):  # already filled
             assert np.array_equal(x, y)
         s.wait_state()
+
+
+@pytest.mark.parametrize("precision", [swe.F32, swe.F64])
+def test_async_upload_gives_the_synchronous_state(precision):
+    # swe_set_state_async from page-locked arrays, pipelined with steps and
+    # asynchronous read-backs as a streaming caller does: every step's result
+    # equals the synchronous upload + step, bit for bit, and the time is kept
+    states = [_wavy(seed=20 + k) for k in range(3)]
+    pin = [[pinned_like(x) for x in (sc.h, sc.hu, sc.hv)] for sc in states]
+    outs = [[torch.empty(states[0].h.shape, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+            for _ in states]
+    with swe.Solver(states[0], precision=precision, stream=stream()) as a:
+        a.set_time(5.0)
+        for k, p in enumerate(pin):
+            a.set_state_async(*(t.numpy() for t in p))
+            a.step(2)
+            a.get_state_async(tuple(t.numpy() for t in outs[k]))
+        a.wait_state()
+        t_a, n_a = a.time()
+    with swe.Solver(states[0], precision=precision, stream=stream()) as b:
+        b.set_time(5.0)
+        for k, sc in enumerate(states):
+            b.set_state(sc.h, sc.hu, sc.hv)
+            b.step(2)
+            ref = b.get_state()
+            for x, y in zip(outs[k], ref):
+                assert np.array_equal(x.numpy(), y)
+        t_b, n_b = b.time()
+    assert t_a == t_b and n_a == n_b == 2
+
+
+def test_async_upload_from_pageable_arrays_is_synchronous():
+    sc, other = _wavy(seed=30), _wavy(seed=31)
+    with swe.Solver(sc, precision=swe.F32, stream=stream()) as s:
+        s.set_state_async(other.h, other.hu, other.hv)  # pageable numpy arrays
+        got = s.get_state()
+    with swe.Solver(other, precision=swe.F32, stream=stream()) as r:
+        ref = r.get_state()
+    for x, y in zip(got, ref):
+        assert np.array_equal(x, y)
