@@ -266,7 +266,7 @@ int swe_autotune(const swe_grid *grids, int32_t ngrids, int32_t precision, int32
 int swe_autotune_lookup(int32_t precision, int32_t mode, double cells);
 
 /* ----------------------------------------------------------------------
- * Batched ensemble and continuous-batching serving (FP32).
+ * Batched ensemble and continuous-batching serving (FP32; FP64 for parity).
  * A batch holds up to nslots independent scenarios ("slots") of any grid
  * size, admitted while device memory stays within hbm_budget_bytes.
  * swe_batch_run advances every live slot by up to k RK3 steps (each slot
@@ -278,13 +278,15 @@ int swe_autotune_lookup(int32_t precision, int32_t mode, double cells);
  * ---------------------------------------------------------------------- */
 typedef struct swe_batch swe_batch;
 
-/* Device bytes one admission of this grid takes (counted against the budget). */
+/* Device bytes one admission of this grid takes in an FP32 batch (counted
+ * against the budget; an FP64 batch counts its ten planes at 8 bytes). */
 size_t swe_batch_slot_bytes(const swe_grid *grid);
 
-/* Create an empty batch.  params: precision must be SWE_F32 and fused_step 0;
- * the sides (walls, the inflow edge, periodic pairs) and the physical
- * parameters are those of every slot, under the rules of swe_create; tile 0
- * picks the default shape; stream as for swe_create.  SWE_EINVAL otherwise. */
+/* Create an empty batch.  params: fused_step and shore 0; the sides (walls,
+ * the inflow edge, periodic pairs) and the physical parameters are those of
+ * every slot, under the rules of swe_create; precision SWE_F32 (tile 0 picks
+ * the default shape) or SWE_F64 (the parity mode: its one compiled shape,
+ * 32x32, taken for tile 0); stream as for swe_create.  SWE_EINVAL otherwise. */
 int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *params, swe_batch **out);
 
 /* Admit a scenario: host FP64 bathymetry and state [ny][nx] (copied), run until

@@ -421,10 +421,11 @@ class Batch:
     """Independent scenarios advanced together by one persistent launch per
     run (the ensemble and serving path, FP32)."""
 
-    def __init__(self, nslots: int, budget_bytes: int, template, stream: Optional[int] = None, tile: int = 0):
+    def __init__(self, nslots: int, budget_bytes: int, template, stream: Optional[int] = None, tile: int = 0,
+                 precision: int = F32):
         self._b = ctypes.c_void_p()
         self.nslots = int(nslots)
-        self.params = params_for(template, F32, stream, tile)
+        self.params = params_for(template, precision, stream, tile)
         _check(lib.swe_batch_create(self.nslots, int(budget_bytes), ctypes.byref(self.params), ctypes.byref(self._b)),
                "swe_batch_create")
         self.shapes: Dict[int, Tuple[int, int]] = {}

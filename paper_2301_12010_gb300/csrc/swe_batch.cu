@@ -32,22 +32,28 @@ struct Slot {
   size_t bytes = 0;
   void *mem = nullptr;
   double *staging = nullptr;
-  Field<float> fd{};
+  Field<float> fd{};     // the planes of an FP32 batch
+  Field<double> fd64{};  // the planes of an FP64 batch
   Phys p{};
   BoxMaps maps[3] = {};  // tensor maps of the halo-box copies (the batch's tile shape)
 };
 
-size_t plane_bytes(int nx, int ny, int *pitch_out) {
+size_t plane_bytes(int nx, int ny, int *pitch_out, size_t elem = sizeof(float)) {
   const int pitch = ((nx + 31) / 32) * 32;
   if (pitch_out) *pitch_out = pitch;
-  return (((size_t)pitch * ny * sizeof(float)) + 255) & ~(size_t)255;
+  return (((size_t)pitch * ny * elem) + 255) & ~(size_t)255;
 }
 
-size_t slot_bytes(int nx, int ny) {
-  const size_t plane = plane_bytes(nx, ny, nullptr);
+size_t slot_bytes(int nx, int ny, size_t elem = sizeof(float)) {
+  const size_t plane = plane_bytes(nx, ny, nullptr, elem);
   const size_t stag = ((sizeof(double) * (size_t)nx * ny) + 255) & ~(size_t)255;
   return plane * 10 + stag;
 }
+
+template <typename T> Field<T> &field_of(Slot &sl);
+template <> Field<float> &field_of<float>(Slot &sl) { return sl.fd; }
+template <> Field<double> &field_of<double>(Slot &sl) { return sl.fd64; }
+static_assert(sizeof(BatchSlot<float>) == sizeof(BatchSlot<double>), "one table size for both precisions");
 
 }  // namespace
 
@@ -55,13 +61,15 @@ struct swe_batch {
   int nslots = 0;
   size_t budget = 0, used = 0;
   swe_params prm{};
+  int prec = SWE_F32;
+  size_t elem = sizeof(float);
   int tile = 1;
   int grid = 0;
   cudaStream_t stream = nullptr, cap = nullptr;
   std::vector<Slot> slots;
   DevScalars *d_sc = nullptr;          // one per slot
   DevPartials *d_cta = nullptr;        // one per slot: per-CTA partials of the clamp volume
-  BatchSlot<float> *d_table = nullptr; // live slots, work-list order
+  void *d_table = nullptr;             // BatchSlot<float or double>: live slots, work-list order
   BatchCtl *d_ctl = nullptr;
   double *d_part = nullptr;            // mass partials + result
   std::map<int, cudaGraphExec_t> graphs;
@@ -112,16 +120,17 @@ Phys phys_of(const swe_params &q, double dx, double dy) {
 
 // Rebuild the work list (live, selected slots in index order) and the
 // control block.
-int upload_table(swe_batch *b) {
-  std::vector<BatchSlot<float>> tab;
+template <typename T>
+int upload_table_t(swe_batch *b) {
+  std::vector<BatchSlot<T>> tab;
   int total = 0;
   const TileShape *ts = shape(b->tile);
   for (int s = 0; s < b->nslots; ++s) {
-    const Slot &sl = b->slots[s];
+    Slot &sl = b->slots[s];
     if (!sl.live || !sl.selected) continue;
-    BatchSlot<float> e{};
+    BatchSlot<T> e{};
     for (int k = 0; k < 3; ++k) e.maps[k] = sl.maps[k];
-    e.fd = sl.fd;
+    e.fd = field_of<T>(sl);
     e.p = sl.p;
     e.sc = b->d_sc + s;
     e.tiles_x = (sl.nx + ts->tx - 1) / ts->tx;
@@ -146,14 +155,86 @@ int upload_table(swe_batch *b) {
   b->strided = big;
   cudaError_t e = cudaSuccess;
   if (!tab.empty())
-    e = cudaMemcpyAsync(b->d_table, tab.data(), sizeof(BatchSlot<float>) * tab.size(), cudaMemcpyHostToDevice,
+    e = cudaMemcpyAsync(b->d_table, tab.data(), sizeof(BatchSlot<T>) * tab.size(), cudaMemcpyHostToDevice,
                         b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   return bfail(b, e);
 }
 
+int upload_table(swe_batch *b) { return b->prec == SWE_F64 ? upload_table_t<double>(b) : upload_table_t<float>(b); }
+
 bool valid_slot(const swe_batch *b, int32_t s) { return b && s >= 0 && s < b->nslots && b->slots[s].live; }
+
+// A new slot's planes in its device memory (bed, U^n, U1, U2, staging), its
+// tensor maps, physics, the host FP64 inputs converted in (page-locked host
+// arrays read by the conversion kernel directly, pageable ones through the
+// staging plane), its scalars and the wave speeds and runup of its state.
+template <typename T>
+cudaError_t fill_slot(swe_batch *b, Slot &sl, int s, size_t plane, const double *const srcs[4]) {
+  Field<T> &fd = field_of<T>(sl);
+  char *q = (char *)sl.mem;
+  T *bplane = (T *)q;
+  fd.b = bplane;
+  q += plane;
+  for (int k = 0; k < 3; ++k) {
+    fd.h[k] = (T *)q; q += plane;
+    fd.hu[k] = (T *)q; q += plane;
+    fd.hv[k] = (T *)q; q += plane;
+  }
+  sl.staging = (double *)q;
+  fd.nx = sl.nx;
+  fd.ny = sl.ny;
+  fd.pitch = sl.pitch;
+  fd.halo = 0;
+  cudaError_t e = make_maps<T>(b->tile, fd, sl.maps);
+  if (e != cudaSuccess) return e;
+  sl.p = phys_of(b->prm, sl.dx, sl.dy);
+#ifdef SWE_CHECKED
+  sl.p.check = &(b->d_sc + s)->check;  // the checked build records out-of-range indexes here
+#endif
+  const size_t nb = sizeof(double) * (size_t)sl.nx * sl.ny;
+  e = cudaMemsetAsync(sl.mem, 0, plane * 10, b->stream);
+  T *dsts[4] = {bplane, fd.h[0], fd.hu[0], fd.hv[0]};
+  for (int f = 0; f < 4 && e == cudaSuccess; ++f) {
+    const void *in = pinned_device_ptr(srcs[f], nb);
+    if (!in) {
+      e = cudaMemcpyAsync(sl.staging, srcs[f], nb, cudaMemcpyHostToDevice, b->stream);
+      in = sl.staging;
+    }
+    if (e == cudaSuccess)
+      e = import_plane<T>(in, true, dsts[f], f == 1 ? bplane : nullptr, sl.p.z_ref, sl.nx, sl.ny, sl.pitch, b->stream);
+  }
+  if (e == cudaSuccess) e = reset_scalars(b->d_sc + s, b->d_cta + s, 0.0, b->cfl, sl.t_end, b->stream);
+  if (e == cudaSuccess) e = state_stats<T>(fd, sl.p, b->d_sc + s, b->stream);
+  return e;
+}
+
+// A live slot's state to host FP64 arrays and its mass (synchronous).
+template <typename T>
+cudaError_t slot_state(swe_batch *b, Slot &sl, double *const dst[3]) {
+  const Field<T> &fd = field_of<T>(sl);
+  const size_t nb = sizeof(double) * (size_t)sl.nx * sl.ny;
+  const T *src[3] = {fd.h[0], fd.hu[0], fd.hv[0]};
+  cudaError_t e = cudaSuccess;
+  for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
+    void *out = const_cast<void *>(pinned_device_ptr(dst[f], nb));
+    e = export_plane<T>(src[f], out ? out : sl.staging, true, f == 0 ? fd.b : nullptr, sl.p.z_ref, sl.nx, sl.ny,
+                        sl.pitch, b->stream);
+    if (e == cudaSuccess && !out) e = cudaMemcpyAsync(dst[f], sl.staging, nb, cudaMemcpyDeviceToHost, b->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e;
+}
+template <typename T>
+cudaError_t slot_mass(swe_batch *b, Slot &sl, double *mass) {
+  const Field<T> &fd = field_of<T>(sl);
+  cudaError_t e = swe::mass<T>(fd.h[0], fd.b, sl.p.z_ref, sl.nx, sl.ny, sl.pitch, sl.dx * sl.dy, b->d_part,
+                               b->d_part + kMassBlocks, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mass, b->d_part + kMassBlocks, sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e;
+}
 
 }  // namespace
 
@@ -168,16 +249,20 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
   const TraceRange trace("swe_batch_create");
   if (out) *out = nullptr;
   if (!out || !params || nslots < 1 || nslots > 4096 || hbm_budget_bytes == 0) return SWE_EINVAL;
-  if (params->precision != SWE_F32) return SWE_EINVAL;  // the batch path is FP32
-  if (params->fused_step) return SWE_EINVAL;             // and runs the paper's per-stage alpha
+  if (params->fused_step) return SWE_EINVAL;             // the batch runs the paper's per-stage alpha
   if (params->shore) return SWE_EINVAL;                  // and its WENO faces
   if (!valid_params(params)) return SWE_EINVAL;          // sides and physics as for one scenario
+  const bool f64 = params->precision == SWE_F64;         // FP64: one compiled tile shape
+  if (f64 && params->tile != 0 && params->tile != batch64_shape()) return SWE_EINVAL;
   swe_batch *b = new (std::nothrow) swe_batch();
   if (!b) return SWE_ENOMEM;
   b->nslots = nslots;
   b->budget = hbm_budget_bytes;
   b->prm = *params;
-  if (params->tile > 0) b->tile = params->tile;
+  b->prec = f64 ? SWE_F64 : SWE_F32;
+  b->elem = f64 ? sizeof(double) : sizeof(float);
+  if (f64) b->tile = batch64_shape();
+  else if (params->tile > 0) b->tile = params->tile;
   else {
     const int cached = swe_autotune_lookup(SWE_F32, 1, 0.0);
     b->tile = cached > 0 ? cached : 1;
@@ -187,11 +272,11 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = dev_malloc((void **)&b->d_sc, sizeof(DevScalars) * nslots);
   if (e == cudaSuccess) e = dev_malloc((void **)&b->d_cta, sizeof(DevPartials) * nslots);
-  if (e == cudaSuccess) e = dev_malloc((void **)&b->d_table, sizeof(BatchSlot<float>) * nslots);
+  if (e == cudaSuccess) e = dev_malloc(&b->d_table, sizeof(BatchSlot<double>) * nslots);
   if (e == cudaSuccess) e = dev_malloc((void **)&b->d_ctl, sizeof(BatchCtl));
   if (e == cudaSuccess) e = dev_malloc((void **)&b->d_part, sizeof(double) * (kMassBlocks + 1));
   int per_sm = 0, dev = 0, sms = 0;
-  if (e == cudaSuccess) e = batch_resident(b->tile, &per_sm);
+  if (e == cudaSuccess) e = f64 ? batch64_resident(&per_sm) : batch_resident(b->tile, &per_sm);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess && (per_sm < 1 || per_sm * sms > kPartSlots)) e = cudaErrorInvalidConfiguration;
@@ -217,7 +302,7 @@ int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, co
   if (!b || !grid || !bathymetry || !h || !hu || !hv || !slot) return SWE_EINVAL;
   if (grid->nx < 3 || grid->ny < 3 || !(dx > 0.0) || !(dy > 0.0) || !(t_end > 0.0)) return SWE_EINVAL;
   if ((long long)grid->nx * grid->ny > (1ll << 31)) return SWE_EINVAL;
-  const size_t need = slot_bytes(grid->nx, grid->ny);
+  const size_t need = slot_bytes(grid->nx, grid->ny, b->elem);
   if (b->used + need > b->budget) return SWE_EBUDGET;
   int s = -1;
   for (int k = 0; k < b->nslots; ++k)
@@ -230,7 +315,7 @@ int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, co
   sl.dx = dx;
   sl.dy = dy;
   sl.t_end = t_end;
-  const size_t plane = plane_bytes(sl.nx, sl.ny, &sl.pitch);
+  const size_t plane = plane_bytes(sl.nx, sl.ny, &sl.pitch, b->elem);
   cudaError_t e = dev_malloc_async(&sl.mem, need, b->stream);
   if (e == cudaErrorMemoryAllocation) {  // no room now: the batch is unchanged and usable
     (void)cudaGetLastError();
@@ -238,48 +323,8 @@ int swe_batch_admit(swe_batch *b, const swe_grid *grid, double dx, double dy, co
     return SWE_ENOMEM;
   }
   if (e != cudaSuccess) return bfail(b, e);
-  char *q = (char *)sl.mem;
-  sl.fd.b = (const float *)q;
-  float *bplane = (float *)q;
-  q += plane;
-  for (int k = 0; k < 3; ++k) {
-    sl.fd.h[k] = (float *)q; q += plane;
-    sl.fd.hu[k] = (float *)q; q += plane;
-    sl.fd.hv[k] = (float *)q; q += plane;
-  }
-  sl.staging = (double *)q;
-  sl.fd.nx = sl.nx;
-  sl.fd.ny = sl.ny;
-  sl.fd.pitch = sl.pitch;
-  sl.fd.halo = 0;
-  e = make_maps<float>(b->tile, sl.fd, sl.maps);
-  if (e != cudaSuccess) {
-    cudaFreeAsync(sl.mem, b->stream);
-    sl = Slot();
-    return bfail(b, e);
-  }
-  sl.p = phys_of(b->prm, dx, dy);
-#ifdef SWE_CHECKED
-  sl.p.check = &(b->d_sc + s)->check;  // the checked build records out-of-range indexes here
-#endif
-  const size_t nb = sizeof(double) * (size_t)sl.nx * sl.ny;
-  const double zr = sl.p.z_ref;
-  e = cudaMemsetAsync(sl.mem, 0, plane * 10, b->stream);
-  // page-locked host arrays are read by the conversion kernel directly,
-  // pageable ones through the slot's staging plane
   const double *srcs[4] = {bathymetry, h, hu, hv};
-  float *dsts[4] = {bplane, sl.fd.h[0], sl.fd.hu[0], sl.fd.hv[0]};
-  for (int f = 0; f < 4 && e == cudaSuccess; ++f) {
-    const void *in = pinned_device_ptr(srcs[f], nb);
-    if (!in) {
-      e = cudaMemcpyAsync(sl.staging, srcs[f], nb, cudaMemcpyHostToDevice, b->stream);
-      in = sl.staging;
-    }
-    if (e == cudaSuccess)
-      e = import_plane<float>(in, true, dsts[f], f == 1 ? bplane : nullptr, zr, sl.nx, sl.ny, sl.pitch, b->stream);
-  }
-  if (e == cudaSuccess) e = reset_scalars(b->d_sc + s, b->d_cta + s, 0.0, b->cfl, t_end, b->stream);
-  if (e == cudaSuccess) e = state_stats<float>(sl.fd, sl.p, b->d_sc + s, b->stream);
+  e = b->prec == SWE_F64 ? fill_slot<double>(b, sl, s, plane, srcs) : fill_slot<float>(b, sl, s, plane, srcs);
   if (e != cudaSuccess) {
     cudaFreeAsync(sl.mem, b->stream);
     sl = Slot();
@@ -314,7 +359,11 @@ int swe_batch_run(swe_batch *b, int32_t k_steps, double cfl) {
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       cudaError_t le = cudaMemsetAsync(&b->d_ctl->bar_count, 0, sizeof(unsigned), b->cap);
-      if (le == cudaSuccess) le = batch_launch(b->tile, b->d_table, b->d_ctl, k_steps, b->grid, b->strided, b->cap);
+      if (le == cudaSuccess)
+        le = b->prec == SWE_F64
+                 ? batch64_launch((const BatchSlot<double> *)b->d_table, b->d_ctl, k_steps, b->grid, b->strided, b->cap)
+                 : batch_launch(b->tile, (const BatchSlot<float> *)b->d_table, b->d_ctl, k_steps, b->grid, b->strided,
+                                b->cap);
       e = cudaStreamEndCapture(b->cap, &g);
       if (le != cudaSuccess) e = le;
     }
@@ -415,17 +464,8 @@ int swe_batch_get_state(swe_batch *b, int32_t slot, double *h, double *hu, doubl
   const TraceRange trace("swe_batch_get_state");
   if (!valid_slot(b, slot) || !h || !hu || !hv) return SWE_EINVAL;
   Slot &sl = b->slots[slot];
-  const size_t nb = sizeof(double) * (size_t)sl.nx * sl.ny;
   double *dst[3] = {h, hu, hv};
-  const float *src[3] = {sl.fd.h[0], sl.fd.hu[0], sl.fd.hv[0]};
-  cudaError_t e = cudaSuccess;
-  for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
-    void *out = const_cast<void *>(pinned_device_ptr(dst[f], nb));
-    e = export_plane<float>(src[f], out ? out : sl.staging, true, f == 0 ? sl.fd.b : nullptr, sl.p.z_ref, sl.nx,
-                            sl.ny, sl.pitch, b->stream);
-    if (e == cudaSuccess && !out) e = cudaMemcpyAsync(dst[f], sl.staging, nb, cudaMemcpyDeviceToHost, b->stream);
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  const cudaError_t e = b->prec == SWE_F64 ? slot_state<double>(b, sl, dst) : slot_state<float>(b, sl, dst);
   return bfail(b, e);
 }
 
@@ -435,13 +475,8 @@ int swe_batch_retire(swe_batch *b, int32_t slot, double *h, double *hu, double *
   Slot &sl = b->slots[slot];
   int rc = SWE_OK;
   if (h && hu && hv) rc = swe_batch_get_state(b, slot, h, hu, hv);
-  if (rc == SWE_OK && mass) {
-    cudaError_t e = swe::mass<float>(sl.fd.h[0], sl.fd.b, sl.p.z_ref, sl.nx, sl.ny, sl.pitch, sl.dx * sl.dy,
-                                     b->d_part, b->d_part + kMassBlocks, b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(mass, b->d_part + kMassBlocks, sizeof(double), cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    rc = bfail(b, e);
-  }
+  if (rc == SWE_OK && mass)
+    rc = bfail(b, b->prec == SWE_F64 ? slot_mass<double>(b, sl, mass) : slot_mass<float>(b, sl, mass));
   if (rc == SWE_OK && runup_max) {
     swe_diag d;
     swe_batch_diagnostics(b, slot, &d);

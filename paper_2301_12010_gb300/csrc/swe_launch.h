@@ -125,6 +125,11 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn tensor_map_encoder();
+// The FP64 batch kernel (swe_batch64_kernels.cu): one compiled tile shape.
+int batch64_shape();
+cudaError_t batch64_resident(int *per_sm);
+cudaError_t batch64_launch(const BatchSlot<double> *slots, BatchCtl *ctl, int k, int grid, bool strided,
+                           cudaStream_t st);
 // CTAs per SM of the batch kernel for a shape, and one cooperative launch.
 cudaError_t batch_resident(int shape, int *per_sm);
 cudaError_t batch_launch(int shape, const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, bool strided,

@@ -104,6 +104,14 @@ def main():
             assert word == 0, "batch slot %d: check word %#x" % (s, word)
         assert b.status() == swe.OK
     print("batch of %d coasts: check words 0" % len(ens))
+    with swe.Batch(len(ens), 1 << 30, ens[0], stream=ST, precision=swe.F64) as b:
+        slots = [b.admit(sc.copy(t_end=1e6)) for sc in ens]
+        b.run(4)
+        for s in slots:
+            word = b.check_word(s)
+            assert word == 0, "FP64 batch slot %d: check word %#x" % (s, word)
+        assert b.status() == swe.OK
+    print("FP64 batch of %d coasts: check words 0" % len(ens))
     print("CHECKED OK")
 
 

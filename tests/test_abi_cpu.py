@@ -97,7 +97,7 @@ def test_batch_arguments_rejected_without_gpu(swe):
     assert swe.lib.swe_batch_create(0, 1 << 30, ctypes.byref(p), ctypes.byref(b)) == swe.EINVAL
     assert swe.lib.swe_batch_create(4, 0, ctypes.byref(p), ctypes.byref(b)) == swe.EINVAL
     q = swe.Params.from_buffer_copy(p)
-    q.precision = swe.F64  # the batch path is FP32
+    q.precision, q.tile = swe.F64, 7  # FP64 batches run on their one compiled shape
     assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
     q = swe.Params.from_buffer_copy(p)
     q.bc[0] = swe.INFLOW  # an inflow edge needs the N-wave's depth and period

@@ -190,6 +190,33 @@ def test_batch_with_periodic_sides_matches_fp64_oracle():
         assert np.sqrt(((hu - ref.hu) ** 2).sum() / (ref.hu ** 2).sum()) <= 1e-4
 
 
+def test_fp64_batch_matches_fp64_oracle_and_is_the_same_alone_and_in_the_mix():
+    # the batch path's parity mode: every scenario of an FP64 batch against
+    # the oracle to 1e-10, and one of them run alone bit for bit
+    ens = small_ensemble(4, seed=13)
+    with swe.Batch(4, GB, ens[0], stream=stream(), precision=swe.F64) as b:
+        slots = [b.admit(sc) for sc in ens]
+        b.run(25)
+        mix = [(b.get_state(s), b.diagnostics(s)) for s in slots]
+        _, m0, _ = b.retire(slots[0])
+    ref0 = oracle.Simulation(ens[0])
+    ref0.step(25)
+    assert abs(m0 - ref0.diag()["mass"]) <= 1e-11 * m0
+    for sc, ((h, hu, hv), d) in zip(ens, mix):
+        ref = oracle.Simulation(sc)
+        ref.step(25)
+        for x, r in ((h, ref.h), (hu, ref.hu), (hv, ref.hv)):
+            assert np.abs(x - r).max() <= 1e-10, sc.name
+        assert d["t"] == pytest.approx(ref.t, rel=1e-12)
+        assert d["clamp_mass"] == pytest.approx(ref.diag()["clamp_mass"], rel=1e-8, abs=1e-9)
+    with swe.Batch(1, GB, ens[2], stream=stream(), precision=swe.F64) as b:
+        s = b.admit(ens[2])
+        b.run(25)
+        alone = b.get_state(s)
+    for x, y in zip(alone, mix[2][0]):
+        assert np.array_equal(x, y)
+
+
 def test_batch_stops_at_t_end_and_reports_done():
     ens = small_ensemble(3, seed=8)
     with swe.Batch(4, GB, ens[0], stream=stream()) as b:
