@@ -77,6 +77,7 @@ struct swe_batch {
   unsigned extra = 0;
   double cfl = 0.4;  // CFL number in the slots' device scalars
   bool strided = false;  // work order of the current table (the launch must match it)
+  bool small = false;    // few tiles per CTA and stage: the run-time-stage form of the kernel
   int sticky = SWE_OK;
 };
 
@@ -153,6 +154,7 @@ int upload_table_t(swe_batch *b) {
   for (const auto &e : tab) big = big && e.ntiles >= 2 * b->grid;
   c.strided = big ? 1 : 0;
   b->strided = big;
+  b->small = total < kSmallItemsPerCta * b->grid;
   cudaError_t e = cudaSuccess;
   if (!tab.empty())
     e = cudaMemcpyAsync(b->d_table, tab.data(), sizeof(BatchSlot<T>) * tab.size(), cudaMemcpyHostToDevice,
@@ -351,7 +353,8 @@ int swe_batch_run(swe_batch *b, int32_t k_steps, double cfl) {
     if (e != cudaSuccess) return bfail(b, e);
     b->cfl = cfl;
   }
-  const int key = 2 * k_steps + (b->strided ? 1 : 0);  // one graph per step count and work order
+  // one graph per step count, work order and kernel form
+  const int key = 4 * k_steps + (b->small ? 2 : 0) + (b->strided ? 1 : 0);
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
     cudaGraph_t g = nullptr;
@@ -363,7 +366,7 @@ int swe_batch_run(swe_batch *b, int32_t k_steps, double cfl) {
         le = b->prec == SWE_F64
                  ? batch64_launch((const BatchSlot<double> *)b->d_table, b->d_ctl, k_steps, b->grid, b->strided, b->cap)
                  : batch_launch(b->tile, (const BatchSlot<float> *)b->d_table, b->d_ctl, k_steps, b->grid, b->strided,
-                                b->cap);
+                                b->small, b->cap);
       e = cudaStreamEndCapture(b->cap, &g);
       if (le != cudaSuccess) e = le;
     }

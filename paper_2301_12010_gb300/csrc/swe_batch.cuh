@@ -116,7 +116,8 @@ __host__ __device__ __forceinline__ StageIO<T> io_of(const Field<T> &fd, int sta
 // table on the way to a tile.
 template <typename T, int TX, int TY, int NT, int S, int STAGE, bool STRIDED>
 __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T *smem, RedSmem &red, Phys &sp,
-                            BatchCtl *ctl) {
+                            BatchCtl *ctl, int stage_rt = 0) {
+  const int st = STAGE ? STAGE : stage_rt;  // STAGE 0: the stage is given at run time
   using G = TileGeom<T, TX, TY>;
   constexpr unsigned kBoxBytes = 4u * G::BH * G::P * (unsigned)sizeof(T);
   __shared__ unsigned long long bar[2];
@@ -150,7 +151,7 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
     const int i0 = (STRIDED ? c.i % c.tx : c.i) * TX, j0 = (STRIDED ? c.i / c.tx : c.j) * TY;
     s_item[bb] = make_int4(c.slot, i0, j0, 0);
     mbar_expect_tx(b, kBoxBytes);
-    const CUtensorMap *m = slots[c.slot].maps[STAGE - 1].m;
+    const CUtensorMap *m = slots[c.slot].maps[st - 1].m;
     T *dst = bb ? box1 : box0;
 #pragma unroll
     for (int f = 0; f < 4; ++f) tma_load_2d(dst + f * G::FIELD, &m[f], i0 - G::OX, j0 - G::OY, b);
@@ -203,15 +204,15 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
     const int4 inf = s_item[bsel];
     const int s = inf.x;
     if (s != cur) {
-      if (cur >= 0 && !s_skip) publish<T, NT, STAGE>(sp, slots[cur].sc, s_lead != 0u, red, red.dt, acc);
+      if (cur >= 0 && !s_skip) publish<T, NT, STAGE>(sp, slots[cur].sc, s_lead != 0u, red, red.dt, acc, st);
       acc = Acc<T>();
       __syncthreads();
       if (tid == 0) {
         const BatchSlot<T> &sl = slots[s];
         sp = sl.p;
-        s_io = io_of(sl.fd, STAGE);
+        s_io = io_of(sl.fd, st);
         const bool ld = (STRIDED ? sl.first_item % (int)gridDim.x : sl.first_item / W) == (int)blockIdx.x;
-        stage_scalars<T, STAGE>(sp, sl.sc, ld, red);
+        stage_scalars<T, STAGE>(sp, sl.sc, ld, red, st);
         s_skip = red.skip;
         s_lead = ld ? 1u : 0u;
       }
@@ -231,10 +232,10 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
         __syncthreads();
       }
       tile_compute<T, TX, TY, NT, S, STAGE>(s_io, sp, i0, j0, box, sL, red_v<T>(red, SV_DT), red_v<T>(red, SV_RCAP),
-                                            red_v<T>(red, SV_AX), red_v<T>(red, SV_AY), acc);
+                                            red_v<T>(red, SV_AX), red_v<T>(red, SV_AY), acc, st);
     }
   }
-  if (cur >= 0 && !s_skip) publish<T, NT, STAGE>(sp, slots[cur].sc, s_lead != 0u, red, red.dt, acc);
+  if (cur >= 0 && !s_skip) publish<T, NT, STAGE>(sp, slots[cur].sc, s_lead != 0u, red, red.dt, acc, st);
 }
 
 }  // namespace swe

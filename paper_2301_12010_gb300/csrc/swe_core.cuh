@@ -891,8 +891,10 @@ struct CellEpilogue {
   bool friction;  // Manning n > 0
   const T (&u0)[3][S];
   Acc<T> &acc;
+  int stage_rt;  // the stage when STAGE is 0 (given at run time)
 
   __device__ __forceinline__ void operator()(int k, T dF0, T dF1, T dF2, T dbk) const {
+    const int st = STAGE ? STAGE : stage_rt;
     const T *bha = box, *bhu = box + G::FIELD, *bhv = box + 2 * G::FIELD, *bb = box + 3 * G::FIELD;
     if (X) {
       const int o = xr * G::LP + xc0 + k;
@@ -924,7 +926,7 @@ struct CellEpilogue {
     T nha = ha + tdt * Lh, nhu = hu + tdt * Lhu, nhv = hv + tdt * Lhv;
     const size_t go = (size_t)j * io.pitch + i;
     if (!SWE_CHK(p, go, (long long)io.ny * io.pitch, CK_OUT)) return;
-    if (STAGE != 1) {
+    if (st != 1) {
       nha = u0[0][k] + wrk * (nha - u0[0][k]);
       nhu = u0[1][k] + wrk * (nhu - u0[1][k]);
       nhv = u0[2][k] + wrk * (nhv - u0[2][k]);
@@ -951,7 +953,7 @@ struct CellEpilogue {
     acc.chk += sx + sy;  // non-finite values propagate to the per-CTA check
     acc.ax = sx > acc.ax ? sx : acc.ax;
     acc.ay = sy > acc.ay ? sy : acc.ay;
-    if (STAGE == 3 && !Num<T>::below(nh, p.h_wet32, p.h_wet) && bc > T(0)) {
+    if (st == 3 && !Num<T>::below(nh, p.h_wet32, p.h_wet) && bc > T(0)) {
       const T e = nh + bc;
       acc.ru = e > acc.ru ? e : acc.ru;
     }
@@ -968,7 +970,8 @@ struct CellEpilogue {
 // pass loop is unrolled, so each pass runs code specialised for its frame.
 template <typename T, int TX, int TY, int NT, int S, int STAGE, bool SHORE = false>
 __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p, int i0, int j0, const T *box,
-                                             T *sL, T tdt, T rcap, T alx, T aly, Acc<T> &acc) {
+                                             T *sL, T tdt, T rcap, T alx, T aly, Acc<T> &acc, int stage_rt = 0) {
+  const int st = STAGE ? STAGE : stage_rt;  // STAGE 0: the stage is given at run time
   using G = TileGeom<T, TX, TY>;
   static_assert(TX % S == 0 && TY % S == 0, "strip length must divide the tile");
   static_assert((TX / S) * TY == NT && (TY / S) * TX == NT, "one strip per thread in both passes");
@@ -990,7 +993,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
   const int yc = tid % TX, yr0 = (tid / TX) * S;
   const int i = i0 + yc;
 
-  const T wrk = (STAGE == 2) ? T(0.25) : T(2.0 / 3.0);
+  const T wrk = (st == 2) ? T(0.25) : T(2.0 / 3.0);
   const bool friction = K.gn2 > T(0);  // FP32 compare (g n^2 > 0 iff n > 0)
   // one body per pass, specialised at compile time (X: the x pass)
   auto pass = [&](auto xflag) {
@@ -998,7 +1001,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
     // U^n of the y-pass cells (stages 2, 3), fetched before the sweep so that
     // the global-memory latency hides behind it
     T u0[3][S];
-    if (STAGE != 1 && !X) {
+    if (st != 1 && !X) {
 #pragma unroll
       for (int k = 0; k < S; ++k) {
         const int j = j0 + yr0 + k;
@@ -1009,7 +1012,7 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
         u0[2][k] = ok ? io.hv0[go] : T(0);
       }
     }
-    const CellEpilogue<T, TX, TY, S, STAGE> emit{io, p, K, box, sL, X, xr, xc0, yc, yr0, i, j0, tdt, rcap, wrk, friction, u0, acc};
+    const CellEpilogue<T, TX, TY, S, STAGE> emit{io, p, K, box, sL, X, xr, xc0, yc, yr0, i, j0, tdt, rcap, wrk, friction, u0, acc, st};
     sweep_strip<T, S, X, G::FIELD, CellEpilogue<T, TX, TY, S, STAGE>, SHORE>(bha, X ? bhu : bhv, X ? bhv : bhu, bb,
                          X ? (xr + G::OY) * G::P + xc0 + G::OX - 3 : yr0 * G::P + yc + G::OX,
                          X ? 1 : G::P, X ? alx : aly, K, p, X ? i0 + xc0 : j0 + yr0, X ? nx : ny,
@@ -1026,15 +1029,17 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
 // output to slot s mod 3 and clears slot (s+1) mod 3, which nothing reads or
 // writes during stage s.
 template <typename T, int STAGE>
-__device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, bool lead, RedSmem &red) {
+__device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, bool lead, RedSmem &red,
+                                              int stage_rt = 0) {
+  const int st = STAGE ? STAGE : stage_rt;  // STAGE 0: the stage is given at run time
   double ax, ay;
   // read through L2 (other CTAs wrote these before the last grid barrier or launch)
-  ax = bitsd(__ldcg(&sc->alpha[STAGE - 1][0]));
-  ay = bitsd(__ldcg(&sc->alpha[STAGE - 1][1]));
+  ax = bitsd(__ldcg(&sc->alpha[st - 1][0]));
+  ay = bitsd(__ldcg(&sc->alpha[st - 1][1]));
   const double t_now = __ldcg(&sc->t), t_end = __ldcg(&sc->t_end);
   double dt = 0.0;
   unsigned skip = __ldcg(&sc->status) != 0u;
-  if (STAGE == 1) {
+  if (st == 1) {
     if (t_end > 0.0 && t_now >= t_end) skip = 1;
     if (p.fixed_dt > 0.0) dt = p.fixed_dt;
     else {
@@ -1059,15 +1064,15 @@ __device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, boo
     if (!__ldcg(&sc->running)) skip = 1;
     dt = __ldcg(&sc->dt);
     if (lead && !skip) {
-      sc->alpha[STAGE == 2 ? 0 : 1][0] = 0ull;
-      sc->alpha[STAGE == 2 ? 0 : 1][1] = 0ull;
+      sc->alpha[st == 2 ? 0 : 1][0] = 0ull;
+      sc->alpha[st == 2 ? 0 : 1][1] = 0ull;
     }
   }
   red.skip = skip;
   red.bad = 0u;
   red.dt = dt;
-  const double tst = (STAGE == 1) ? t_now : __ldcg(&sc->t_step);
-  const double ts = (STAGE == 1) ? tst : (STAGE == 2 ? tst + dt : tst + 0.5 * dt);
+  const double tst = (st == 1) ? t_now : __ldcg(&sc->t_step);
+  const double ts = (st == 1) ? tst : (st == 2 ? tst + dt : tst + 0.5 * dt);
   const bool inflow = p.bc[0] == BC_INFLOW;
   const T eta = inflow ? inflow_eta<T>(p, ts) : T(0);
   const T v[SV_N] = {T(dt), dt > 0.0 ? T(1) / T(dt) : T(0), T(ax), T(ay), eta, inflow ? eta * T(p.in_uf) : T(0)};
@@ -1085,7 +1090,8 @@ __device__ __forceinline__ void stage_scalars(const Phys &p, DevScalars *sc, boo
 // publication for one scenario.
 template <typename T, int NT, int STAGE>
 __device__ __noinline__ void publish(const Phys &p, DevScalars *sc, bool lead, RedSmem &red, double dt,
-                                     const Acc<T> &acc) {
+                                     const Acc<T> &acc, int stage_rt = 0) {
+  const int st = STAGE ? STAGE : stage_rt;  // STAGE 0: the stage is given at run time
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   // in the state's precision (FP64 arithmetic is slow on this part); one
   // conversion per published value
@@ -1112,20 +1118,20 @@ __device__ __noinline__ void publish(const Phys &p, DevScalars *sc, bool lead, R
       fsum += wv[5 * q + 3];
       rmax = fmax(rmax, wv[5 * q + 4]);
     }
-    atomicMax(&sc->alpha[STAGE % 3][0], dbits((double)mx));
-    atomicMax(&sc->alpha[STAGE % 3][1], dbits((double)my));
-    constexpr double wgt = (STAGE == 3) ? 1.0 : (STAGE == 2 ? 2.0 / 3.0 : 1.0 / 6.0);
-    constexpr double wfl = (STAGE == 3) ? 2.0 / 3.0 : 1.0 / 6.0;
+    atomicMax(&sc->alpha[st % 3][0], dbits((double)mx));
+    atomicMax(&sc->alpha[st % 3][1], dbits((double)my));
+    const double wgt = (st == 3) ? 1.0 : (st == 2 ? 2.0 / 3.0 : 1.0 / 6.0);
+    const double wfl = (st == 3) ? 2.0 / 3.0 : 1.0 / 6.0;
     // this CTA's own FP64 slot (no other CTA writes it: deterministic totals)
     if (dsum != T(0)) sc->part->clamp[blockIdx.x] += (wgt * p.area) * (double)dsum;
     if (fsum != T(0)) sc->part->edge[blockIdx.x] += wfl * dt * (double)fsum;
-    if (STAGE == 3 && rmax > T(0)) {
+    if (st == 3 && rmax > T(0)) {
       const unsigned long long rb = dbits((double)rmax);
       atomicMax(&sc->runup_now[__ldcg(&sc->parity)], rb);
       atomicMax(&sc->runup_max, rb);
     }
     if (red.bad) atomicOr(&sc->status, ST_NONFINITE);
-    if (STAGE == 3 && lead) {
+    if (st == 3 && lead) {
       const double tn = __ldcg(&sc->t_step) + dt, te = __ldcg(&sc->t_end);
       sc->t = (te > 0.0 && tn >= te) ? te : tn;
       sc->steps = __ldcg(&sc->steps) + 1;

@@ -50,7 +50,7 @@ SWE_SHAPES(SWE_PICK)
   cudaError_t make_maps_##K(const Field<T> &fd, BoxMaps out[3]);                                 \
   cudaError_t batch_resident_##K(int *per_sm);                                                   \
   cudaError_t batch_launch_##K(const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, bool strided, \
-                               cudaStream_t st);
+                               bool small, cudaStream_t st);
 SWE_SHAPES(SWE_DECL)
 #undef SWE_DECL
 
@@ -130,9 +130,12 @@ int batch64_shape();
 cudaError_t batch64_resident(int *per_sm);
 cudaError_t batch64_launch(const BatchSlot<double> *slots, BatchCtl *ctl, int k, int grid, bool strided,
                            cudaStream_t st);
-// CTAs per SM of the batch kernel for a shape, and one cooperative launch.
+// CTAs per SM of the batch kernel for a shape, and one cooperative launch
+// (small: the form with one run-time-stage copy of the stage code, for
+// launches with few tiles per CTA and stage).
+constexpr int kSmallItemsPerCta = 24;  // below this many tiles per CTA and stage a launch is small
 cudaError_t batch_resident(int shape, int *per_sm);
 cudaError_t batch_launch(int shape, const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, bool strided,
-                         cudaStream_t st);
+                         bool small, cudaStream_t st);
 
 }  // namespace swe

@@ -85,10 +85,10 @@ cudaError_t batch_resident(int k, int *per_sm) {
 }
 
 cudaError_t batch_launch(int k, const BatchSlot<float> *slots, BatchCtl *ctl, int steps, int grid, bool strided,
-                         cudaStream_t st) {
+                         bool small, cudaStream_t st) {
   switch (k) {
 #define SWE_CASE(K, TX, TY, NT, S, M32, M64) \
-  case K: return batch_launch_##K(slots, ctl, steps, grid, strided, st);
+  case K: return batch_launch_##K(slots, ctl, steps, grid, strided, small, st);
     SWE_SHAPES(SWE_CASE)
 #undef SWE_CASE
   }

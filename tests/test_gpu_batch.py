@@ -61,6 +61,27 @@ def test_batch_result_is_the_same_alone_and_in_the_mix(tile):
         assert d_alone["t"] == d_mix["t"] and d_mix["steps"] == 35
 
 
+def test_result_is_the_same_whichever_kernel_form_the_launch_takes():
+    # a launch with few tiles per CTA runs the run-time-stage form of the
+    # batch kernel, a large one the inlined form: a coast alone (small launch)
+    # and inside a mix of 4000+ tiles (large launch) must agree bit for bit
+    ens = W.mitigation_ensemble()
+    sc = small_ensemble(1, seed=9)[0]
+    assert sum(e.cells for e in ens) // 3072 > 24 * 152
+    with swe.Batch(80, 16 * GB, sc, stream=stream(), tile=7) as b:
+        s = b.admit(sc)
+        b.run(12)
+        alone = b.get_state(s)
+    with swe.Batch(80, 16 * GB, sc, stream=stream(), tile=7) as b:
+        for e in ens:
+            b.admit(e.copy(t_end=1e6))
+        s = b.admit(sc)
+        b.run(12)
+        mixed = b.get_state(s)
+    for x, y in zip(alone, mixed):
+        assert np.array_equal(x, y)
+
+
 def test_work_chunks_that_cross_many_scenarios():
     # sixty one-tile grids among four larger ones, more tiles than CTAs: each
     # CTA's chunk of the work list crosses several scenarios (the per-CTA
