@@ -69,6 +69,16 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl *ctl, unsigned nblocks) {
   return ok != 0u;
 }
 
+// The batch kernel reads the tensor maps of its halo-box copies from the slot
+// table in global memory, which the host rewrites between launches (a new
+// mix, a paused scenario's place taken by another): before a CTA's first copy
+// with a scenario's map it acquires that map for the tensor-map proxy, so
+// that the copy unit does not act on an older descriptor at that address.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(reinterpret_cast<unsigned long long>(m))
+               : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ int slot_of_item(const BatchSlot<T> *slots, int n, int item) {
   int lo = 0, hi = n - 1;
@@ -144,6 +154,7 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
     int slot, i, j, tx, n;
   };
   __shared__ Cursor q;
+  __shared__ int s_acq;  // slot whose maps this CTA acquired last (thread 0)
   // halo box of the cursor's item by tensor copies into buffer bb, with the
   // tensor maps of its scenario; then the cursor moves to the next item
   auto issue = [&](int bb, unsigned long long *b) {
@@ -152,6 +163,11 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
     s_item[bb] = make_int4(c.slot, i0, j0, 0);
     mbar_expect_tx(b, kBoxBytes);
     const CUtensorMap *m = slots[c.slot].maps[st - 1].m;
+    if (c.slot != s_acq) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) tensormap_acquire(&m[f]);
+      s_acq = c.slot;
+    }
     T *dst = bb ? box1 : box0;
 #pragma unroll
     for (int f = 0; f < 4; ++f) tma_load_2d(dst + f * G::FIELD, &m[f], i0 - G::OX, j0 - G::OY, b);
@@ -179,10 +195,14 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
     mbar_init(&bar[1], 1u);
     mbar_fence_init();
     s_fail = 0u;
+    s_acq = -1;
     if (item < item_end) {
       const int s0 = slot_of_item(slots, nslots, item);
       const int t = item - slots[s0].first_item, tx = slots[s0].tiles_x;
       q = STRIDED ? Cursor{s0, t, 0, tx, slots[s0].ntiles} : Cursor{s0, t % tx, t / tx, tx, slots[s0].ntiles - t};
+      // the buffer may hold the previous stage's ghost patching (generic
+      // writes): order them before the tensor copy overwrites it
+      fence_proxy_async();
       issue(0, &bar[0]);
     }
   }

@@ -562,11 +562,13 @@ __device__ __noinline__ void patch_box(const StageIO<T> &io, const Phys &p, int 
       else { sj = j < 0 ? j + ny : j - ny; shift = T(j < 0 ? -p.b_jump_y : p.b_jump_y); }
       const size_t go = (size_t)sj * io.pitch + si;
       if (!SWE_CHK(p, go, (long long)io.ny * io.pitch, CK_PATCH_GLOBAL)) continue;
-      const T bs = io.b[go], cb = bs + shift;
+      // through L2: in the batch kernel other CTAs wrote these planes earlier
+      // in the same launch, and an SM's L1 is not refreshed within a launch
+      const T bs = __ldcg(io.b + go), cb = bs + shift;
       bb[o] = cb;
-      bha[o] = (io.ha[go] + still_depth(bs, zref)) - still_depth(cb, zref);
-      bhu[o] = io.hu[go];
-      bhv[o] = io.hv[go];
+      bha[o] = (__ldcg(io.ha + go) + still_depth(bs, zref)) - still_depth(cb, zref);
+      bhu[o] = __ldcg(io.hu + go);
+      bhv[o] = __ldcg(io.hv + go);
       continue;
     }
     // mirror source: a real cell of the same box
@@ -1007,9 +1009,11 @@ __device__ __forceinline__ void tile_compute(const StageIO<T> &io, const Phys &p
         const int j = j0 + yr0 + k;
         const bool ok = i < nx && j < ny && SWE_CHK(p, (size_t)j * io.pitch + i, (long long)ny * io.pitch, CK_U0);
         const size_t go = ok ? (size_t)j * io.pitch + i : 0;
-        u0[0][k] = ok ? io.ha0[go] : T(0);
-        u0[1][k] = ok ? io.hu0[go] : T(0);
-        u0[2][k] = ok ? io.hv0[go] : T(0);
+        // through L2 (the batch kernel's U^n was written by other CTAs in
+        // an earlier step of the same launch; L1 is not refreshed within it)
+        u0[0][k] = ok ? __ldcg(io.ha0 + go) : T(0);
+        u0[1][k] = ok ? __ldcg(io.hu0 + go) : T(0);
+        u0[2][k] = ok ? __ldcg(io.hv0 + go) : T(0);
       }
     }
     const CellEpilogue<T, TX, TY, S, STAGE> emit{io, p, K, box, sL, X, xr, xc0, yc, yr0, i, j0, tdt, rcap, wrk, friction, u0, acc, st};

@@ -82,6 +82,36 @@ def test_result_is_the_same_whichever_kernel_form_the_launch_takes():
         assert np.array_equal(x, y)
 
 
+def test_paused_and_resumed_in_turn_is_the_same_as_alone():
+    # scenarios advanced in turn, one or two per launch, the others paused
+    # (swe_batch_select): every launch puts another scenario at the same
+    # place of the slot table, whose tensor maps the kernel must then read
+    # afresh; each result equals the scenario run alone, bit for bit
+    ens = small_ensemble(5, seed=17)
+    alone_res = []
+    for sc in ens:
+        with swe.Batch(2, GB, sc, stream=stream()) as b:
+            s = b.admit(sc.copy(t_end=0.6))
+            while not b.poll():
+                b.run(6)
+            alone_res.append(b.get_state(s))
+    for width in (1, 2):
+        with swe.Batch(8, GB, ens[0], stream=stream()) as b:
+            slots = [b.admit(sc.copy(t_end=0.6)) for sc in ens]
+            done, it = {}, 0
+            while len(done) < len(slots) and it < 400:
+                live = [s for s in slots if s not in done]
+                b.select([live[(it + j) % len(live)] for j in range(min(width, len(live)))])
+                b.run(6)
+                for s in b.poll():
+                    if s not in done:
+                        done[s] = b.get_state(s)
+                it += 1
+            for k, s in enumerate(slots):
+                for x, y in zip(done[s], alone_res[k]):
+                    assert np.array_equal(x, y), (width, k)
+
+
 def test_work_chunks_that_cross_many_scenarios():
     # sixty one-tile grids among four larger ones, more tiles than CTAs: each
     # CTA's chunk of the work list crosses several scenarios (the per-CTA
