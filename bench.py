@@ -49,11 +49,11 @@ BYTES_PER_CELL_STAGE = {1: 28.0, 2: 40.0, 3: 40.0}
 NCU_CAPTURE = {"tile": 7, "cells": 4096 * 4096,
                "profile": "profiles/stage_kernel_f32_coastal_dem_4096_dram.md, "
                           "profiles/stage_kernel_f32_coastal_dem_2048_pipes.md",
-               "dram_bytes": {1: 269528064 + 167055872, 2: 470991104 + 176387072, 3: 470633216 + 165647104},
-               "thread_inst_per_cell": {1: 566.3, 2: 593.1, 3: 601.1},
-               "issue_active_pct": {1: 61.13, 2: 62.72, 3: 63.54},
+               "dram_bytes": {1: 269509376 + 166968320, 2: 471001088 + 176913152, 3: 470624768 + 165502720},
+               "thread_inst_per_cell": {1: 566.3, 2: 594.7, 3: 601.2},
+               "issue_active_pct": {1: 60.21, 2: 62.47, 3: 63.17},
                "sources": ("swe_core.cuh", "swe_kernels.cu", "swe_launch.h:SWE_SHAPES"),
-               "sha256": "b752e6bb6b0fd3f0f49b5412dd8a5de491946f9681b52c6d324ef25b0b3c653f"}
+               "sha256": "501cf24d13dfc1104f44c2ed62e947f3d2da19f4c8293ae4ce8015d31a2bb9e0"}
 
 
 def kernel_sources_sha256() -> str:
