@@ -77,6 +77,8 @@ def test_invalid_arguments_rejected_without_gpu(swe):
     q.fused_step = 1
     q.bc[0] = q.bc[1] = swe.PERIODIC
     assert swe.lib.swe_create(ctypes.byref(swe.Grid(4, 4)), 1.0, 1.0, dp, ctypes.byref(q), ctypes.byref(h)) == swe.EINVAL
+    # more than 2^31 cells: rejected before anything is read or allocated
+    assert swe.lib.swe_create(ctypes.byref(swe.Grid(65536, 32769)), 1.0, 1.0, dp, ctypes.byref(p), ctypes.byref(h)) == swe.EINVAL
     assert not h.value
     assert swe.lib.swe_step(None, 1, 0.4) == swe.EINVAL
 

@@ -147,6 +147,17 @@ def test_fused_nonfinite_is_reported_and_skipped_steps_keep_the_state():
                 assert np.array_equal(x, y, equal_nan=True)
 
 
+def test_fused_dry_still_domain_reports_einval():
+    # no water, no CFL step: the step's preparation flags it, nothing moves
+    sc = W.lake_at_rest(16, 16, eta0=-100.0, depth=10.0, rms=1.0).copy(alpha_margin=MARGIN)
+    assert sc.h.max() == 0.0
+    with swe.Solver(sc, precision=swe.F32, stream=stream()) as s:
+        s.step(3)
+        with pytest.raises(swe.SweError) as ei:
+            s.sync()
+        assert ei.value.code == swe.EINVAL
+
+
 def test_fused_is_deterministic():
     sc = W.coastal_dem(n=128, dx=120.0, t0=500.0).copy(alpha_margin=MARGIN)
     outs = []
