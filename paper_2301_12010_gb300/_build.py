@@ -48,6 +48,7 @@ UNITS: List[Tuple[str, List[str], str]] = (
        ("swe_noalloc.cu", [], "swe_noalloc.o"), ("swe_batch.cu", [], "swe_batch.o"),
        ("swe_multi.cu", [], "swe_multi.o"), ("swe_fused.cu", [], "swe_fused.o"),
        ("swe_shore.cu", [], "swe_shore.o"), ("swe_batch64_kernels.cu", [], "swe_batch64_kernels.o"),
+       ("swe_batch_shore.cu", [], "swe_batch_shore.o"),
        ("swe_autotune.cu", [], "swe_autotune.o")]
 )
 

@@ -124,7 +124,7 @@ __host__ __device__ __forceinline__ StageIO<T> io_of(const Field<T> &fd, int sta
 // and hands each item's slot and tile origin to the CTA through shared
 // memory when it issues the item's halo-box copies: no thread reads the slot
 // table on the way to a tile.
-template <typename T, int TX, int TY, int NT, int S, int STAGE, bool STRIDED>
+template <typename T, int TX, int TY, int NT, int S, int STAGE, bool STRIDED, bool SHORE = false>
 __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T *smem, RedSmem &red, Phys &sp,
                             BatchCtl *ctl, int stage_rt = 0) {
   const int st = STAGE ? STAGE : stage_rt;  // STAGE 0: the stage is given at run time
@@ -251,7 +251,7 @@ __device__ void batch_stage(const BatchSlot<T> *slots, int nslots, int total, T 
                                  red_v<T>(red, SV_UIN));
         __syncthreads();
       }
-      tile_compute<T, TX, TY, NT, S, STAGE>(s_io, sp, i0, j0, box, sL, red_v<T>(red, SV_DT), red_v<T>(red, SV_RCAP),
+      tile_compute<T, TX, TY, NT, S, STAGE, SHORE>(s_io, sp, i0, j0, box, sL, red_v<T>(red, SV_DT), red_v<T>(red, SV_RCAP),
                                             red_v<T>(red, SV_AX), red_v<T>(red, SV_AY), acc, st);
     }
   }

@@ -125,6 +125,12 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn tensor_map_encoder();
+// The shoreline variant's batch kernel (swe_batch_shore.cu): FP32, one
+// compiled tile shape.
+int batch_shore_shape();
+cudaError_t batch_shore_resident(int *per_sm);
+cudaError_t batch_shore_launch(const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, bool strided,
+                               cudaStream_t st);
 // The FP64 batch kernel (swe_batch64_kernels.cu): one compiled tile shape.
 int batch64_shape();
 cudaError_t batch64_resident(int *per_sm);

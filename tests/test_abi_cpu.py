@@ -110,9 +110,10 @@ def test_batch_arguments_rejected_without_gpu(swe):
     q = swe.Params.from_buffer_copy(p)
     q.bc[2] = swe.PERIODIC  # periodic sides come in pairs
     assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
-    q = swe.Params.from_buffer_copy(p)
-    q.shore = 1  # the batch runs the paper's WENO faces
-    assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
+    for prec, tile in ((swe.F64, 0), (swe.F32, 1)):  # the shoreline batch: FP32 on its one shape
+        q = swe.Params.from_buffer_copy(p)
+        q.shore, q.precision, q.tile = 1, prec, tile
+        assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
     q = swe.Params.from_buffer_copy(p)
     q.fused_step = 1  # the batch runs the per-stage alpha
     assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL

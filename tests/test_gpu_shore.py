@@ -117,3 +117,26 @@ def test_other_tile_shapes_are_rejected():
     with pytest.raises(swe.SweError) as ei:
         swe.Solver(sc, precision=swe.F32, stream=stream(), tile=1)
     assert ei.value.code == swe.EINVAL
+
+
+def test_batch_with_shoreline_faces_matches_oracle_and_alone():
+    # the ensemble path with the shoreline variant: coasts with hills and a
+    # dry shore in one batch against the oracle's variant, and one of them
+    # run alone bit for bit
+    ens = [sc.copy(t_end=1e6, shore=1) for sc in
+           W.mitigation_ensemble(count=4, seed=23, nx_range=(96, 224), ny_range=(32, 160), land_width=90.0)]
+    with swe.Batch(4, 1 << 30, ens[0], stream=stream()) as b:
+        slots = [b.admit(sc) for sc in ens]
+        b.run(25)
+        mix = [b.get_state(s) for s in slots]
+    for sc, (h, hu, hv) in zip(ens, mix):
+        ref = oracle.Simulation(sc)
+        ref.step(25)
+        assert rel_l2(eta_tilde(h, sc.b), eta_tilde(ref.h, sc.b)) <= 1e-4, sc.name
+        assert rel_l2(np.stack([hu, hv]), np.stack([ref.hu, ref.hv])) <= 1e-4, sc.name
+    with swe.Batch(1, 1 << 30, ens[1], stream=stream()) as b:
+        s = b.admit(ens[1])
+        b.run(25)
+        alone = b.get_state(s)
+    for x, y in zip(alone, mix[1]):
+        assert np.array_equal(x, y)
