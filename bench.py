@@ -315,6 +315,23 @@ def shore_bench(swe, W, torch, sc, steps: int = 20, warmup: int = 4, per_stage_m
     return out
 
 
+def profile_shore_case(n: int = 2048) -> int:
+    """A few steps of the shoreline variant on the n x n coastal DEM, for ncu; no timing."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2301_12010_gb300 as swe
+    import workloads as W
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream().cuda_stream
+    with swe.Solver(W.coastal_dem(n=n).copy(shore=1), precision=swe.F32, stream=st) as s:
+        s.step(3)
+        s.sync()
+    print("profile-shore: ok")
+    return 0
+
+
 def profile_fused_case(n: int = 2048) -> int:
     """A few fused steps on the n x n coastal DEM, for ncu; no timing."""
     import torch
@@ -547,6 +564,8 @@ def main():
                          "single-scenario kernels: a short case for a profiler")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused-step variant's measurement")
     ap.add_argument("--no-shore", action="store_true", help="skip the shoreline variant's measurement")
+    ap.add_argument("--profile-shore", action="store_true",
+                    help="only three steps of the shoreline variant on the --n coastal DEM: a short case for a profiler")
     ap.add_argument("--profile-fused", action="store_true",
                     help="only four fused steps on the --n coastal DEM: a short case for a profiler")
     ap.add_argument("--config-table", action="store_true",
@@ -559,6 +578,8 @@ def main():
         return profile_batch_case()
     if args.profile_fused:
         return profile_fused_case(args.n)
+    if args.profile_shore:
+        return profile_shore_case(args.n)
     if args.config_table:
         return config_table()
     if args.serving_sweep:
