@@ -714,6 +714,63 @@ struct Window {
 // (the cell update then adds g (h_s - d_s) b_s), which puts a lake at rest
 // beside dry land in balance at any level at or below z_ref.  The face values
 // enter the differences as corrections to the WENO values of the face.
+template <typename T>
+struct ShoreFace {
+  T f0, f2;    // 6 sqrt(3) F_0, 6 sqrt(3) F_2 of the face (both sides)
+  T f1l, f1r;  // 6 sqrt(3) of the normal-momentum flux as the left and the right cell see it
+  T bl, br;    // 12 b_L, 12 b_R
+};
+struct ChkWord {
+  unsigned long long *check;
+};
+
+// The hydrostatic-reconstruction values of the face between box cells oL and
+// oL + st (SHORE, see sweep_strip), out of line: only faces next to dry cells
+// take it, and one copy keeps the sweeps' unrolled face bodies small enough
+// for the instruction cache.
+template <typename T>
+__device__ __noinline__ ShoreFace<T> shore_face(const T *bha, const T *bqn, const T *bqt, const T *bb, int oL, int st,
+                                                int field, T alpha, T g, T zref, float thr32, double thr,
+                                                unsigned long long *check) {
+  const ChkWord ck{check};
+  (void)ck;
+  (void)field;
+  T ha_[2], qn_[2], qt_[2], b_[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int o = oL + s * st;
+    const bool ok = SWE_CHK(ck, o, field, CK_CELL);
+    ha_[s] = ok ? bha[o] : T(0);
+    qn_[s] = ok ? bqn[o] : T(0);
+    qt_[s] = ok ? bqt[o] : T(0);
+    b_[s] = ok ? bb[o] : T(0);
+  }
+  const T bL = b_[0], bR = b_[1];
+  const T dL = still_depth(bL, zref), dR = still_depth(bR, zref);
+  const T hL = ha_[0] + dL, hR = ha_[1] + dR;
+  T uL = T(0), vL = T(0), uR = T(0), vR = T(0);
+  if (!Num<T>::below(hL, thr32, thr)) { uL = qn_[0] / hL; vL = qt_[0] / hL; }
+  if (!Num<T>::below(hR, thr32, thr)) { uR = qn_[1] / hR; vR = qt_[1] / hR; }
+  const T bf = bL > bR ? bL : bR;
+  T sL = hL + (bL - bf), sR = hR + (bR - bf);  // bed difference first: films keep their digits
+  sL = sL > T(0) ? sL : T(0);
+  sR = sR > T(0) ? sR : T(0);
+  const T g2 = T(0.5) * g, ah = T(0.5) * alpha;
+  const T qL = sL * uL, qR = sR * uR;
+  const T F0 = T(0.5) * (qL + qR) - ah * (sR - sL);
+  const T F1 = T(0.5) * (qL * uL + g2 * sL * sL + qR * uR + g2 * sR * sR) - ah * (qR - qL);
+  const T F2 = T(0.5) * (qL * vL + qR * vR) - ah * (sR * vR - sL * vL);
+  const T c6 = T(10.392304845413264);  // 6 sqrt 3
+  ShoreFace<T> r;
+  r.f0 = c6 * F0;
+  r.f2 = c6 * F2;
+  r.f1l = c6 * (F1 + g2 * (hL * hL - sL * sL - dL * dL));
+  r.f1r = c6 * (F1 + g2 * (hR * hR - sR * sR - dR * dR));
+  r.bl = T(12) * bL;
+  r.br = T(12) * bR;
+  return r;
+}
+
 template <typename T, int S, bool XP, int FIELD, typename E, bool SHORE = false>
 __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T *bqt, const T *bb, int o0, int st,
                                             T alpha, const Consts<T> &K, const Phys &p, int ia, int n, bool edge_ok,
@@ -802,23 +859,8 @@ __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T 
     }
     if constexpr (SHORE) {
       if (hr) {
-        T haL, qnL, qtL, bL, haR, qnR, qtR, bR;
-        cell(k + 2, haL, qnL, qtL, bL);  // window slot 2: the face's left cell
-        cell(k + 3, haR, qnR, qtR, bR);  // window slot 3: its right cell
-        const T dL = still_depth(bL, zref), dR = still_depth(bR, zref);
-        const T hL = haL + dL, hR = haR + dR;
-        T uL = T(0), vL = T(0), uR = T(0), vR = T(0);
-        if (!Num<T>::below(hL, p.h_dry32, p.h_dry)) { uL = qnL / hL; vL = qtL / hL; }
-        if (!Num<T>::below(hR, p.h_dry32, p.h_dry)) { uR = qnR / hR; vR = qtR / hR; }
-        const T bf = bL > bR ? bL : bR;
-        T sL = hL + (bL - bf), sR = hR + (bR - bf);  // bed difference first: films keep their digits
-        sL = sL > T(0) ? sL : T(0);
-        sR = sR > T(0) ? sR : T(0);
-        const T g2 = T(0.5) * K.g, ah = T(0.5) * alpha;
-        const T qL = sL * uL, qR = sR * uR;
-        const T F0 = T(0.5) * (qL + qR) - ah * (sR - sL);
-        const T F1 = T(0.5) * (qL * uL + g2 * sL * sL + qR * uR + g2 * sR * sR) - ah * (qR - qL);
-        const T F2 = T(0.5) * (qL * vL + qR * vR) - ah * (sR * vR - sL * vL);
+        const ShoreFace<T> f = shore_face<T>(bha, bqn, bqt, bb, o0 + (k + 2) * st, st, FIELD, alpha, K.g, zref,
+                                             p.h_dry32, p.h_dry, p.check);
         // the WENO values of this face, carried: Fs_c = 6 (f+_c(2) + f-_c(3)) + X_c
         const V2 fp2 = vsub(vsub(vsub(win.lp01, win.dp01[5]), win.dp01[4]), win.dp01[3]);
         const V2 fm3 = vsub(vsub(win.lm01, win.dm01[5]), win.dm01[4]);
@@ -826,13 +868,12 @@ __device__ __forceinline__ void sweep_strip(const T *bha, const T *bqn, const T 
         const T w2 = fma(T(6), (win.lp2 - win.dp2[5] - win.dp2[4] - win.dp2[3]) + (win.lm2 - win.dm2[5] - win.dm2[4]),
                          x2);
         const T wb = fma(T(6), (win.lb - win.db[5] - win.db[4] - win.db[3]) + (win.lb - win.db[5] - win.db[4]), x3);
-        const T c6 = T(10.392304845413264);  // 6 sqrt 3
-        l0 = n0 = c6 * F0 - w01.x;
-        l2 = n2 = c6 * F2 - w2;
-        l1 = c6 * (F1 + g2 * (hL * hL - sL * sL - dL * dL)) - w01.y;
-        n1 = c6 * (F1 + g2 * (hR * hR - sR * sR - dR * dR)) - w01.y;
-        lb = T(12) * bL - wb;
-        nb = T(12) * bR - wb;
+        l0 = n0 = f.f0 - w01.x;
+        l2 = n2 = f.f2 - w2;
+        l1 = f.f1l - w01.y;
+        n1 = f.f1r - w01.y;
+        lb = f.bl - wb;
+        nb = f.br - wb;
       }
     }
     if (edge_ok && ((k == 0 && ia == 0) || (k > 0 && ia + k == n))) {
