@@ -135,8 +135,10 @@ int swe_set_state_device(swe_handle *s, const void *h, const void *hu, const voi
  * stream, so that the next swe_step uses the new state.  The time is kept.
  * The arrays must stay unchanged until the next synchronising call
  * (swe_sync, swe_get_state, swe_wait_state, swe_diagnostics).  Pageable
- * arrays: swe_set_state (synchronous).  Allocates its staging (3 FP64
- * planes) at the first call; SWE_ENOMEM leaves the handle usable. */
+ * arrays: swe_set_state (synchronous).  Two staging slots of 3 FP64 planes
+ * each are used in turn, so that an upload need not wait for the conversion
+ * of the one before it (only for that of the one before last); they are
+ * allocated at the first call, and SWE_ENOMEM leaves the handle usable. */
 int swe_set_state_async(swe_handle *s, const double *h, const double *hu, const double *hv);
 
 /* Enqueue n RK3 steps (Eq. (8)) on the handle's stream.  Each step runs three
@@ -156,15 +158,18 @@ int swe_sync(swe_handle *s);
 int swe_get_state(swe_handle *s, double *h, double *hu, double *hv);
 
 /* Start copying the current state to host FP64 arrays [ny][nx] and return at
- * once: the state is snapshot on the device (in stream order after the steps
- * enqueued so far) and converted into the arrays on a second stream, so that
- * later calls (swe_set_state, swe_step) overlap the read-back.  The arrays
- * must each be one page-locked allocation (cudaHostAlloc, cudaHostRegister, a
- * pinned torch tensor); they hold the state once swe_wait_state returns and
- * must not be read or freed before.  With pageable arrays this is
- * swe_get_state (synchronous).  A second call waits on the device for the
- * first read-back before it snapshots again.  No counterpart in the paper:
- * an interface for pipelining input upload and result read-back. */
+ * once: the state is converted on the device into one of two staging slots
+ * of 3 FP64 planes (on the handle's stream, in stream order after the steps
+ * enqueued so far) and a copy engine carries the slot to the arrays on a
+ * second stream, so that later calls (swe_set_state, swe_step) overlap the
+ * copy.  The arrays must each be one page-locked allocation (cudaHostAlloc,
+ * cudaHostRegister, a pinned torch tensor); they hold the state once
+ * swe_wait_state returns and must not be read or freed before.  With
+ * pageable arrays this is swe_get_state (synchronous).  The slots are used in
+ * turn: a call waits on the device for the copy of the read-back before last
+ * to finish before it converts into that slot.  The slots are allocated at
+ * the first call; SWE_ENOMEM leaves the handle usable.  No counterpart in the
+ * paper: an interface for pipelining input upload and result read-back. */
 int swe_get_state_async(swe_handle *s, double *h, double *hu, double *hv);
 
 /* Bounded-wait settings of the halo-box copies of the stage kernels: a wait
@@ -186,7 +191,7 @@ int swe_set_wait(swe_handle *s, double timeout_s, int32_t extra_copy_bytes);
  * counterpart in the paper. */
 int swe_debug_fail_alloc(int32_t n);
 
-/* Wait for the read-back started by swe_get_state_async (no-op if none);
+/* Wait for the read-backs started by swe_get_state_async (no-op if none);
  * returns the handle's first error, if any. */
 int swe_wait_state(swe_handle *s);
 

@@ -194,6 +194,7 @@ class Solver:
         self.precision = precision
         self.nx, self.ny = sc.nx, sc.ny
         self._h = ctypes.c_void_p()
+        self._async_in, self._async_out = [], []  # host arrays of uploads and read-backs in flight
         b = np.ascontiguousarray(sc.b, dtype=np.float64)
         g = Grid(sc.nx, sc.ny)
         self.params = params_for(sc, precision, stream, tile)
@@ -238,7 +239,7 @@ class Solver:
         for x in (h, hu, hv):
             if x.dtype != np.float64 or not x.flags.c_contiguous or x.shape != (self.ny, self.nx):
                 raise ValueError("set_state_async needs contiguous float64 arrays of shape (ny, nx)")
-        self._async_in = (h, hu, hv)  # kept alive until the upload is done
+        self._async_in.append((h, hu, hv))  # kept alive until the stream is synchronised
         _check(lib.swe_set_state_async(self._h, *[_dp(x) for x in (h, hu, hv)]), "swe_set_state_async")
 
     def set_state_device(self, h, hu, hv) -> None:
@@ -250,6 +251,7 @@ class Solver:
         if out is None:
             out = tuple(np.empty((self.ny, self.nx), dtype=np.float64) for _ in range(3))
         _check(lib.swe_get_state(self._h, *[_dp(x) for x in out]), "swe_get_state")
+        self._async_in = []  # the stream is synchronised
         return out
 
     def get_state_async(self, out) -> None:
@@ -259,7 +261,7 @@ class Solver:
         for x in out:
             if x.dtype != np.float64 or not x.flags.c_contiguous or x.shape != (self.ny, self.nx):
                 raise ValueError("get_state_async needs contiguous float64 arrays of shape (ny, nx)")
-        self._async_out = out  # keep the arrays alive until wait_state
+        self._async_out.append(out)  # kept alive until wait_state
         _check(lib.swe_get_state_async(self._h, *[_dp(x) for x in out]), "swe_get_state_async")
 
     def set_wait(self, timeout_s: float = 1.0, extra_copy_bytes: int = 0) -> None:
@@ -269,7 +271,7 @@ class Solver:
 
     def wait_state(self) -> None:
         _check(lib.swe_wait_state(self._h), "swe_wait_state")
-        self._async_out = None
+        self._async_out = []
 
     def get_state_device(self, h, hu, hv) -> None:
         _check(lib.swe_get_state_device(self._h, h.data_ptr(), hu.data_ptr(), hv.data_ptr()),
@@ -282,6 +284,7 @@ class Solver:
 
     def sync(self) -> None:
         _check(lib.swe_sync(self._h), "swe_sync")
+        self._async_in = []
 
     def status(self) -> int:
         return int(lib.swe_status(self._h))

@@ -59,22 +59,25 @@ struct swe_handle {
   cudaGraphExec_t graph1 = nullptr;  // fused_step: one step 0 -> 1 and the copy of set 1 back to set 0
   double cfl_dev = -1.0;          // CFL value last written to the device scalars
   int sticky = SWE_OK;            // first host-visible error
-  // asynchronous read-back (swe_get_state_async): U^n is copied to snap on the
-  // caller's stream and converted into the host arrays on the read-back stream
-  void *snap = nullptr;           // three planes of U^n
-  double *xstage = nullptr;       // three FP64 [ny][nx] planes: the read-back's host format
-  cudaStream_t xfer = nullptr;    // read-back stream (non-blocking)
-  cudaEvent_t ev_snap = nullptr;  // snapshot taken
-  cudaEvent_t ev_done = nullptr;  // read-back finished (snapshot free again)
-  bool pending = false;
-  // asynchronous upload (swe_set_state_async): copy engines carry the host FP64
-  // state into instage on the upload stream; the conversion into U^n runs on
-  // the caller's stream after it
-  double *instage = nullptr;      // three FP64 [ny][nx] planes
-  cudaStream_t upl = nullptr;     // upload stream (non-blocking)
-  cudaEvent_t ev_up = nullptr;    // upload landed
-  cudaEvent_t ev_used = nullptr;  // instage converted (free for the next upload)
-  bool up_used = false;
+  // asynchronous read-back (swe_get_state_async), two slots used in turn:
+  // U^n is converted into slot k's FP64 planes on the caller's stream and a
+  // copy engine carries them to the host on the read-back stream, so that the
+  // next step and conversion need not wait for this copy
+  double *xstage[2] = {nullptr, nullptr};  // three FP64 [ny][nx] planes each: the host format
+  cudaStream_t xfer = nullptr;             // read-back stream (non-blocking)
+  cudaEvent_t ev_conv[2] = {nullptr, nullptr};  // slot converted
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};  // slot's copy to the host finished (slot free again)
+  bool pending[2] = {false, false};
+  int xk = 0;  // slot of the next read-back
+  // asynchronous upload (swe_set_state_async), two slots used in turn: copy
+  // engines carry the host FP64 state into slot k on the upload stream; the
+  // conversion into U^n runs on the caller's stream after it
+  double *instage[2] = {nullptr, nullptr};  // three FP64 [ny][nx] planes each
+  cudaStream_t upl = nullptr;               // upload stream (non-blocking)
+  cudaEvent_t ev_up[2] = {nullptr, nullptr};    // upload landed
+  cudaEvent_t ev_used[2] = {nullptr, nullptr};  // slot converted (free for the upload after next)
+  bool up_used[2] = {false, false};
+  int uk = 0;  // slot of the next upload
 };
 
 namespace {
@@ -163,11 +166,13 @@ int device_status(swe_handle *s) {
 // copy engines carry both directions of the link at once, a kernel reading
 // host memory beside them does not.
 bool readback_in_flight(swe_handle *s) {
-  if (!s->pending) return false;
-  const cudaError_t e = cudaEventQuery(s->ev_done);
-  if (e == cudaErrorNotReady) {
-    (void)cudaGetLastError();
-    return true;
+  for (int k = 0; k < 2; ++k) {
+    if (!s->pending[k]) continue;
+    const cudaError_t e = cudaEventQuery(s->ev_done[k]);
+    if (e == cudaErrorNotReady) {
+      (void)cudaGetLastError();
+      return true;
+    }
   }
   return false;
 }
@@ -489,50 +494,57 @@ int swe_set_state_async(swe_handle *s, const double *h, const double *hu, const 
   if (!pinned_device_ptr(h, nb) || !pinned_device_ptr(hu, nb) || !pinned_device_ptr(hv, nb))
     return swe_set_state(s, h, hu, hv);  // pageable: synchronous
   cudaError_t e = cudaSuccess;
-  if (!s->instage) {  // first asynchronous upload: its buffers, stream and events
-    double *st = nullptr;
+  if (!s->instage[0]) {  // first asynchronous upload: its buffers, stream and events
+    double *st[2] = {nullptr, nullptr};
     cudaStream_t us = nullptr;
-    cudaEvent_t e1 = nullptr, e2 = nullptr;
-    e = dev_malloc((void **)&st, 3 * nb);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = dev_malloc((void **)&st[k], 3 * nb);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&e2, cudaEventDisableTiming);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {  // nothing half-made stays behind
-      if (e2) cudaEventDestroy(e2);
-      if (e1) cudaEventDestroy(e1);
+      for (int k = 0; k < 4; ++k)
+        if (ev[k]) cudaEventDestroy(ev[k]);
       if (us) cudaStreamDestroy(us);
-      if (st) cudaFree(st);
+      for (int k = 0; k < 2; ++k)
+        if (st[k]) cudaFree(st[k]);
       if (e == cudaErrorMemoryAllocation) {  // no room now: the handle is unchanged and usable
         (void)cudaGetLastError();
         return SWE_ENOMEM;
       }
       return cuda_check(s, e);
     }
-    s->instage = st;
     s->upl = us;
-    s->ev_up = e1;
-    s->ev_used = e2;
+    for (int k = 0; k < 2; ++k) {
+      s->instage[k] = st[k];
+      s->ev_up[k] = ev[2 * k];
+      s->ev_used[k] = ev[2 * k + 1];
+    }
   }
-  // the copy engines fill the staging planes once the previous upload's
-  // conversion is done with them; the conversion into U^n follows on the
-  // caller's stream, after the work enqueued so far (steps, a snapshot)
-  if (s->up_used) e = cudaStreamWaitEvent(s->upl, s->ev_used, 0);
+  // the copy engines fill slot k once the conversion of the upload before
+  // last is done with it; the conversion into U^n follows on the caller's
+  // stream, after the work enqueued so far (steps, read-back conversions)
+  const int k = s->uk;
+  double *in = s->instage[k];
+  if (s->up_used[k]) e = cudaStreamWaitEvent(s->upl, s->ev_used[k], 0);
   const double *src[3] = {h, hu, hv};
   for (int f = 0; f < 3 && e == cudaSuccess; ++f)
-    e = cudaMemcpyAsync(s->instage + f * n, src[f], nb, cudaMemcpyHostToDevice, s->upl);
-  if (e == cudaSuccess) e = cudaEventRecord(s->ev_up, s->upl);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_up, 0);
+    e = cudaMemcpyAsync(in + f * n, src[f], nb, cudaMemcpyHostToDevice, s->upl);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_up[k], s->upl);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_up[k], 0);
   void *dst[3] = {s->h[0], s->hu[0], s->hv[0]};
   for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
     if (s->prec == SWE_F64)
-      e = import_plane<double>(s->instage + f * n, true, (double *)dst[f], f == 0 ? (const double *)s->b : nullptr,
+      e = import_plane<double>(in + f * n, true, (double *)dst[f], f == 0 ? (const double *)s->b : nullptr,
                                s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
     else
-      e = import_plane<float>(s->instage + f * n, true, (float *)dst[f], f == 0 ? (const float *)s->b : nullptr,
+      e = import_plane<float>(in + f * n, true, (float *)dst[f], f == 0 ? (const float *)s->b : nullptr,
                               s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
   }
-  if (e == cudaSuccess) e = cudaEventRecord(s->ev_used, s->stream);
-  if (e == cudaSuccess) s->up_used = true;
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_used[k], s->stream);
+  if (e == cudaSuccess) {
+    s->up_used[k] = true;
+    s->uk = 1 - k;
+  }
   // the scalars of the new state, on the stream: time kept, the rest cleared,
   // wave speeds and runup of U^n
   if (s->cfl_dev <= 0) s->cfl_dev = 0.4;
@@ -618,73 +630,70 @@ int swe_get_state_async(swe_handle *s, double *h, double *hu, double *hv) {
   void *out[3] = {const_cast<void *>(pinned_device_ptr(h, bytes)), const_cast<void *>(pinned_device_ptr(hu, bytes)),
                   const_cast<void *>(pinned_device_ptr(hv, bytes))};
   if (!out[0] || !out[1] || !out[2]) return swe_get_state(s, h, hu, hv);  // pageable: synchronous
-  const size_t plane = s->elem * (size_t)s->pitch * s->ny;
   cudaError_t e = cudaSuccess;
   const size_t nb = sizeof(double) * (size_t)s->nx * s->ny;
-  if (!s->snap) {  // first asynchronous read-back: its buffers, stream and events
-    void *snap = nullptr;
-    double *xs = nullptr;
+  if (!s->xstage[0]) {  // first asynchronous read-back: its buffers, stream and events
+    double *xs[2] = {nullptr, nullptr};
     cudaStream_t xf = nullptr;
-    cudaEvent_t ev1 = nullptr, ev2 = nullptr;
-    e = dev_malloc(&snap, 3 * plane);
-    if (e == cudaSuccess) e = dev_malloc((void **)&xs, 3 * nb);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = dev_malloc((void **)&xs[k], 3 * nb);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&xf, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev2, cudaEventDisableTiming);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {  // nothing half-made stays behind
-      if (ev2) cudaEventDestroy(ev2);
-      if (ev1) cudaEventDestroy(ev1);
+      for (int k = 0; k < 4; ++k)
+        if (ev[k]) cudaEventDestroy(ev[k]);
       if (xf) cudaStreamDestroy(xf);
-      if (xs) cudaFree(xs);
-      if (snap) cudaFree(snap);
+      for (int k = 0; k < 2; ++k)
+        if (xs[k]) cudaFree(xs[k]);
       if (e == cudaErrorMemoryAllocation) {  // no room now: the handle is unchanged and usable
         (void)cudaGetLastError();
         return SWE_ENOMEM;
       }
       return cuda_check(s, e);
     }
-    s->snap = snap;
-    s->xstage = xs;
     s->xfer = xf;
-    s->ev_snap = ev1;
-    s->ev_done = ev2;
+    for (int k = 0; k < 2; ++k) {
+      s->xstage[k] = xs[k];
+      s->ev_conv[k] = ev[2 * k];
+      s->ev_done[k] = ev[2 * k + 1];
+    }
   }
-  // the previous read-back must be done with the snapshot
-  if (s->pending) e = cudaStreamWaitEvent(s->stream, s->ev_done, 0);
-  char *snap = (char *)s->snap;
-  const void *src[3] = {s->h[0], s->hu[0], s->hv[0]};
-  for (int f = 0; f < 3 && e == cudaSuccess; ++f)
-    e = cudaMemcpyAsync(snap + f * plane, src[f], plane, cudaMemcpyDeviceToDevice, s->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(s->ev_snap, s->stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->xfer, s->ev_snap, 0);
-  // convert on the device, then let a copy engine carry the bytes (it
-  // overlaps an upload in the other direction better than a kernel writing
-  // host memory)
-  double *xs = s->xstage;
+  // slot k is free once the read-back before last has reached the host; the
+  // conversion reads U^n in stream order (after the steps enqueued so far),
+  // then a copy engine carries the slot to the host (it overlaps an upload in
+  // the other direction better than a kernel writing host memory)
+  const int k = s->xk;
+  double *xs = s->xstage[k];
+  if (s->pending[k]) e = cudaStreamWaitEvent(s->stream, s->ev_done[k], 0);
   const size_t n = (size_t)s->nx * s->ny;
+  const void *src[3] = {s->h[0], s->hu[0], s->hv[0]};
   for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
     if (s->prec == SWE_F64)
-      e = export_plane<double>((const double *)(snap + f * plane), xs + f * n, true,
-                               f == 0 ? (const double *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->xfer);
+      e = export_plane<double>((const double *)src[f], xs + f * n, true, f == 0 ? (const double *)s->b : nullptr,
+                               s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
     else
-      e = export_plane<float>((const float *)(snap + f * plane), xs + f * n, true,
-                              f == 0 ? (const float *)s->b : nullptr, s->phys.z_ref, s->nx, s->ny, s->pitch, s->xfer);
+      e = export_plane<float>((const float *)src[f], xs + f * n, true, f == 0 ? (const float *)s->b : nullptr,
+                              s->phys.z_ref, s->nx, s->ny, s->pitch, s->stream);
   }
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_conv[k], s->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->xfer, s->ev_conv[k], 0);
   double *hosts[3] = {h, hu, hv};
   for (int f = 0; f < 3 && e == cudaSuccess; ++f)
     e = cudaMemcpyAsync(hosts[f], xs + f * n, nb, cudaMemcpyDeviceToHost, s->xfer);
-  if (e == cudaSuccess) e = cudaEventRecord(s->ev_done, s->xfer);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_done[k], s->xfer);
   if (e != cudaSuccess) return cuda_check(s, e);
-  s->pending = true;
+  s->pending[k] = true;
+  s->xk = 1 - k;
   return SWE_OK;
 }
 
 int swe_wait_state(swe_handle *s) {
   const TraceRange trace("swe_wait_state");
   if (!s) return SWE_EINVAL;
-  if (s->pending) {
-    const cudaError_t e = cudaEventSynchronize(s->ev_done);
-    s->pending = false;
+  for (int k = 0; k < 2; ++k) {
+    if (!s->pending[k]) continue;
+    const cudaError_t e = cudaEventSynchronize(s->ev_done[k]);
+    s->pending[k] = false;
     if (e != cudaSuccess) return cuda_check(s, e);
   }
   return s->sticky;
@@ -800,13 +809,14 @@ int swe_destroy(swe_handle *s) {
     cudaStreamSynchronize(s->upl);
     cudaStreamDestroy(s->upl);
   }
-  if (s->ev_up) cudaEventDestroy(s->ev_up);
-  if (s->ev_used) cudaEventDestroy(s->ev_used);
-  if (s->instage) cudaFree(s->instage);
-  if (s->ev_snap) cudaEventDestroy(s->ev_snap);
-  if (s->ev_done) cudaEventDestroy(s->ev_done);
-  if (s->snap) cudaFree(s->snap);
-  if (s->xstage) cudaFree(s->xstage);
+  for (int k = 0; k < 2; ++k) {
+    if (s->ev_up[k]) cudaEventDestroy(s->ev_up[k]);
+    if (s->ev_used[k]) cudaEventDestroy(s->ev_used[k]);
+    if (s->instage[k]) cudaFree(s->instage[k]);
+    if (s->ev_conv[k]) cudaEventDestroy(s->ev_conv[k]);
+    if (s->ev_done[k]) cudaEventDestroy(s->ev_done[k]);
+    if (s->xstage[k]) cudaFree(s->xstage[k]);
+  }
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->graph1) cudaGraphExecDestroy(s->graph1);
   if (s->cap) cudaStreamDestroy(s->cap);

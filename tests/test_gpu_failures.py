@@ -44,7 +44,7 @@ def test_failed_readback_buffers_leave_the_handle_usable():
         s.step(5)
         ref = s.get_state()
         out = pinned(sc.h.shape)
-        for n in (1, 2):  # the snapshot, then the conversion buffer
+        for n in (1, 2):  # the first staging slot, then the second
             swe.debug_fail_alloc(n)
             with pytest.raises(swe.SweError) as ei:
                 s.get_state_async(out)
@@ -57,6 +57,28 @@ def test_failed_readback_buffers_leave_the_handle_usable():
             assert np.array_equal(a, b)
         s.step(5)
         assert s.status() == swe.OK
+
+
+def test_failed_upload_buffers_leave_the_handle_usable():
+    sc, other = W.gaussian_hump(n=64), W.gaussian_hump(n=64, amp=0.3)
+    with swe.Solver(other, precision=swe.F32, stream=stream()) as r:
+        ref = r.get_state()
+    src = pinned(sc.h.shape)
+    for a, x in zip(src, (other.h, other.hu, other.hv)):
+        a[...] = x
+    with swe.Solver(sc, precision=swe.F32, stream=stream()) as s:
+        for n in (1, 2):  # the first staging slot, then the second
+            swe.debug_fail_alloc(n)
+            with pytest.raises(swe.SweError) as ei:
+                s.set_state_async(*src)
+            assert ei.value.code == swe.ENOMEM
+            swe.debug_fail_alloc(0)
+            assert s.status() == swe.OK
+        s.set_state_async(*src)
+        for a, b in zip(s.get_state(), ref):
+            assert np.array_equal(a, b)
+        s.step(5)
+        s.sync()
 
 
 def test_failed_batch_creation_and_admission_leave_no_trace():

@@ -108,8 +108,10 @@ def test_async_read_back_into_pageable_arrays_is_synchronous():
 def test_async_upload_gives_the_synchronous_state(precision):
     # swe_set_state_async from page-locked arrays, pipelined with steps and
     # asynchronous read-backs as a streaming caller does: every step's result
-    # equals the synchronous upload + step, bit for bit, and the time is kept
-    states = [_wavy(seed=20 + k) for k in range(3)]
+    # equals the synchronous upload + step, bit for bit, and the time is kept;
+    # five rounds, so that each of the two staging slots per direction is
+    # reused while the other is in flight
+    states = [_wavy(seed=20 + k) for k in range(5)]
     pin = [[pinned_like(x) for x in (sc.h, sc.hu, sc.hv)] for sc in states]
     outs = [[torch.empty(states[0].h.shape, dtype=torch.float64, pin_memory=True) for _ in range(3)]
             for _ in states]
