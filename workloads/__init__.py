@@ -344,16 +344,27 @@ def _is_number(t: str) -> bool:
         return False
 
 
+def read_dem(path: str):
+    """An elevation grid from a GeoTIFF (recognised by the TIFF header) or an
+    ESRI ASCII file, as (z, dx, dy, x0, y0, nodata) of read_esri_ascii."""
+    with open(path, "rb") as f:
+        head = f.read(4)
+    if head in (b"II*\0", b"MM\0*", b"II+\0", b"MM\0+"):
+        from workloads.geotiff import read_geotiff
+        return read_geotiff(path)
+    return read_esri_ascii(path)
+
+
 def dem_scenario(path: str, sea_level: float = 0.0, nodata_elevation: Optional[float] = None,
                  crop: Optional[Tuple[int, int, int, int]] = None, stride: int = 1, **settings) -> Scenario:
-    """Still water at sea_level over the bed of an ESRI ASCII grid of
-    elevations (m, positive up).  NODATA cells take nodata_elevation (default:
+    """Still water at sea_level over the bed of an elevation grid (m, positive
+    up): a GeoTIFF or an ESRI ASCII file (read_dem).  NODATA cells take nodata_elevation (default:
     the highest valid elevation, i.e. dry land behind walls).  crop =
     (j0, j1, i0, i1) selects rows j0..j1-1 and columns i0..i1-1 (after the
     flip to y-up order) and stride keeps every stride-th cell.  Further keyword
     arguments set Scenario fields (boundary types, inflow wave, friction ...);
     z_ref defaults to sea_level."""
-    z, dx, dy, _, _, nodata = read_esri_ascii(path)
+    z, dx, dy, _, _, nodata = read_dem(path)
     if nodata.any():
         if nodata.all():
             raise ValueError("%s holds no valid elevation" % path)
