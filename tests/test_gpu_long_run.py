@@ -4,8 +4,9 @@ about five minutes of oracle time: SWE_SLOW_TESTS=1) both against the oracle.
 The parity tests compare the kernels with the oracle over tens to thousands
 of steps; a coast of the mitigation ensemble runs 36,000 steps to its 1200 s
 horizon, with the N-wave running up rough land and hills, where rounding
-differences could grow.  The FP64 kernels follow the oracle to 1e-10 m, so
-FP32 is held here against FP64 over the whole horizon, at five times: the
+differences could grow.  The FP64 kernels follow the oracle to 1e-10 m over
+the parity tests' horizons; FP32 is held here against FP64 over the whole
+horizon, at five times: the
 same time, the same wet/dry state of every cell (to a thousandth of the
 cells), the same runup (1 cm), mass (2e-6 relative) and the surface anomaly
 (relative L2 5e-4).  Observed: runup equal to 0.1 mm, no cell differing in
