@@ -213,6 +213,13 @@ int swe_get_time(swe_handle *s, double *t, int64_t *steps);
 /* Set the simulated time (resume from a checkpoint); resets the step count. */
 int swe_set_time(swe_handle *s, double t);
 
+/* Simulated-time horizon: with t_end > 0 the step that would pass t_end is
+ * shortened to end on it and later steps do nothing (no error; the step count
+ * stops), as a run to a set output time does; 0 removes the horizon.  Kept
+ * across swe_set_state*.  Synchronises.  SWE_EINVAL for a negative or
+ * non-finite t_end. */
+int swe_set_horizon(swe_handle *s, double t_end);
+
 /* All diagnostics at once.  Synchronises. */
 int swe_diagnostics(swe_handle *s, swe_diag *d);
 

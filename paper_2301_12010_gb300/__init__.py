@@ -77,6 +77,7 @@ def _load() -> ctypes.CDLL:
         "swe_get_state": (ip, [H, dp, dp, dp]),
         "swe_get_state_async": (ip, [H, dp, dp, dp]),
         "swe_wait_state": (ip, [H]),
+        "swe_set_horizon": (ip, [H, ctypes.c_double]),
         "swe_set_wait": (ip, [H, ctypes.c_double, ctypes.c_int32]),
         "swe_get_state_device": (ip, [H, vp, vp, vp]),
         "swe_mass": (ip, [H, dp, dp]),
@@ -297,6 +298,11 @@ class Solver:
 
     def set_time(self, t: float) -> None:
         _check(lib.swe_set_time(self._h, float(t)), "swe_set_time")
+
+    def set_horizon(self, t_end: float) -> None:
+        """Stop at simulated time t_end (the last step shortened to end on
+        it, later steps doing nothing); 0 removes the horizon."""
+        _check(lib.swe_set_horizon(self._h, float(t_end)), "swe_set_horizon")
 
     # -- diagnostics
     def diagnostics(self, check: bool = True) -> Dict[str, float]:

@@ -58,6 +58,7 @@ struct swe_handle {
   cudaGraphExec_t graph = nullptr;   // one step (fused_step: two steps, plane sets 0 -> 1 -> 0)
   cudaGraphExec_t graph1 = nullptr;  // fused_step: one step 0 -> 1 and the copy of set 1 back to set 0
   double cfl_dev = -1.0;          // CFL value last written to the device scalars
+  double t_end = 0.0;             // horizon (swe_set_horizon), kept when the state changes
   int sticky = SWE_OK;            // first host-visible error
   // asynchronous read-back (swe_get_state_async), two slots used in turn:
   // U^n is converted into slot k's FP64 planes on the caller's stream and a
@@ -233,7 +234,7 @@ int after_state_change(swe_handle *s) {
   cudaError_t e = cudaMemcpyAsync(&t, &s->sc->t, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_check(s, e);
-  e = reset_scalars(s->sc, s->cta, t, s->cfl_dev > 0 ? s->cfl_dev : 0.4, 0.0, s->stream);
+  e = reset_scalars(s->sc, s->cta, t, s->cfl_dev > 0 ? s->cfl_dev : 0.4, s->t_end, s->stream);
   if (e == cudaSuccess)
     e = s->prec == SWE_F64 ? state_stats<double>(field_of<double>(s), s->phys, s->sc, s->stream)
                            : state_stats<float>(field_of<float>(s), s->phys, s->sc, s->stream);
@@ -548,7 +549,7 @@ int swe_set_state_async(swe_handle *s, const double *h, const double *hu, const 
   // the scalars of the new state, on the stream: time kept, the rest cleared,
   // wave speeds and runup of U^n
   if (s->cfl_dev <= 0) s->cfl_dev = 0.4;
-  if (e == cudaSuccess) e = reset_scalars(s->sc, s->cta, NAN, s->cfl_dev, 0.0, s->stream);
+  if (e == cudaSuccess) e = reset_scalars(s->sc, s->cta, NAN, s->cfl_dev, s->t_end, s->stream);
   if (e == cudaSuccess)
     e = s->prec == SWE_F64 ? state_stats<double>(field_of<double>(s), s->phys, s->sc, s->stream)
                            : state_stats<float>(field_of<float>(s), s->phys, s->sc, s->stream);
@@ -776,6 +777,15 @@ int swe_set_time(swe_handle *s, double t) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(&s->sc->t_step, &t, sizeof(double), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&s->sc->steps, &zero, sizeof(long long), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_check(s, e);
+}
+
+int swe_set_horizon(swe_handle *s, double t_end) {
+  const TraceRange trace("swe_set_horizon");
+  if (!s || !std::isfinite(t_end) || t_end < 0.0) return SWE_EINVAL;
+  cudaError_t e = cudaMemcpyAsync(&s->sc->t_end, &t_end, sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e == cudaSuccess) s->t_end = t_end;
   return cuda_check(s, e);
 }
 

@@ -338,3 +338,45 @@ def test_diagnostic_volumes_are_the_same_run_to_run(precision):
                 s.step(steps)
                 seen.append(s.diagnostics()[key])
         assert seen[0] != 0.0 and seen[0] == seen[1] == seen[2], (key, seen)
+
+
+@pytest.mark.parametrize("precision", [swe.F64, swe.F32])
+@pytest.mark.parametrize("fused", [False, True])
+def test_horizon_ends_the_run_on_t_end(precision, fused):
+    # swe_set_horizon: the step that would pass t_end is shortened to end on
+    # it and later steps do nothing, as the oracle runs to a set time; the
+    # horizon survives a new state and 0 removes it
+    sc = W.gaussian_hump(n=96)
+    if fused:
+        sc = sc.copy(alpha_margin=1.1)
+    t_end = 0.4137
+    ref = oracle.Simulation(sc)
+    n = ref.run_until(t_end)
+    rd = ref.diag()
+    assert rd["t"] == t_end and n > 5
+    with swe.Solver(sc, precision=precision, stream=stream()) as s:
+        s.set_horizon(t_end)
+        s.step(n + 7)
+        d = s.diagnostics()
+        assert d["t"] == t_end and d["steps"] == n
+        h, hu, hv = s.get_state()
+        if precision == swe.F64:
+            for a, r in ((h, ref.h), (hu, ref.hu), (hv, ref.hv)):
+                assert np.abs(a - r).max() <= 1e-10
+        else:
+            assert rel_l2(eta_tilde(h, sc.b), eta_tilde(ref.h, sc.b)) <= 1e-4
+        s.step(3)  # past the horizon: nothing changes, no error
+        s.sync()
+        assert s.diagnostics()["steps"] == n
+        for a, b in zip(s.get_state(), (h, hu, hv)):
+            assert np.array_equal(a, b)
+        s.set_state(h, hu, hv)  # the horizon is kept across a new state (which restarts the step count)
+        s.step(2)
+        d = s.diagnostics()
+        assert d["t"] == t_end and d["steps"] == 0
+        s.set_horizon(0.0)
+        s.step(2)
+        d = s.diagnostics()
+        assert d["t"] > t_end and d["steps"] == 2
+        with pytest.raises(swe.SweError):
+            s.set_horizon(-1.0)
