@@ -22,7 +22,7 @@ _TYPES = {1: ("B", 1), 2: ("s", 1), 3: ("H", 2), 4: ("I", 4), 5: ("II", 8), 6: (
 
 TAG_WIDTH, TAG_LENGTH, TAG_BITS, TAG_COMPRESSION = 256, 257, 258, 259
 TAG_STRIP_OFFSETS, TAG_SAMPLES, TAG_ROWS_PER_STRIP, TAG_STRIP_BYTES = 273, 277, 278, 279
-TAG_PLANAR, TAG_PREDICTOR = 284, 317
+TAG_PREDICTOR = 317
 TAG_TILE_WIDTH, TAG_TILE_LENGTH, TAG_TILE_OFFSETS, TAG_TILE_BYTES = 322, 323, 324, 325
 TAG_SAMPLE_FORMAT = 339
 TAG_PIXEL_SCALE, TAG_TIEPOINT, TAG_TRANSFORM, TAG_GEOKEYS = 33550, 33922, 34264, 34735
@@ -129,10 +129,8 @@ def read_geotiff(path: str) -> Tuple[np.ndarray, float, float, float, float, np.
         return v[0]
 
     nx, ny = int(one(TAG_WIDTH)), int(one(TAG_LENGTH))
-    if int(one(TAG_SAMPLES, 1)) != 1:
+    if int(one(TAG_SAMPLES, 1)) != 1:  # (one sample per pixel: the planar configuration does not matter)
         raise ValueError("%s: one sample per pixel is read (a single-band grid)" % path)
-    if int(one(TAG_PLANAR, 1)) != 1 and int(one(TAG_SAMPLES, 1)) != 1:
-        raise ValueError("%s: unsupported planar configuration" % path)
     dt = _dtype(int(one(TAG_BITS, 1)), int(one(TAG_SAMPLE_FORMAT, 1)), bo)
     compression, predictor = int(one(TAG_COMPRESSION, 1)), int(one(TAG_PREDICTOR, 1))
     img = np.empty((ny, nx), dtype=dt.newbyteorder("="))
