@@ -72,6 +72,24 @@ def kernel_sources_sha256() -> str:
     return h.hexdigest()
 
 
+def issue_ceiling(value: float, clk):
+    """The cell-update rate at which the stage kernels would issue one warp
+    instruction per scheduler and cycle (152 SMs x 4 schedulers x 32 lanes at
+    the sampled SM clock over the captured thread instructions of the three
+    stages), and the fraction of it reached; None without valid counters."""
+    c = NCU_CAPTURE
+    try:
+        if c["sha256"] is None or kernel_sources_sha256() != c["sha256"] or not c["thread_inst_per_cell"]:
+            return None
+    except OSError:
+        return None
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    per_update = sum(c["thread_inst_per_cell"].values())
+    ceil = 152 * 4 * 32 * mhz * 1e6 / per_update
+    return {"value": ceil, "unit": "cell-updates/s", "frac": value / ceil, "sm_mhz": mhz,
+            "thread_inst_per_cell_update": per_update}
+
+
 def ncu_counters(tile: int, stage: int, cells: int):
     """The captured counters of one launch of this RK stage, DRAM bytes scaled
     to `cells` if the capture was of another size, or None if nothing was
@@ -710,6 +728,7 @@ def main():
                                  if counters else None,
                                  "issue_active_pct": counters.get("issue_active_pct") if counters else None,
                                  "source": counters.get("profile") if counters else None,
+                                 "issue_ceiling": issue_ceiling(value, clk),
                                  "note": "the kernel is bound by FP32 instruction issue, not HBM: executed thread "
                                          "instructions per cell and RK stage and the issue-active share, from ncu"}},
             "stage_ms": stage_ms,
