@@ -41,3 +41,16 @@ def test_counters_are_withheld_for_another_tile_or_changed_sources(monkeypatch):
     assert bench.ncu_counters(bench.NCU_CAPTURE["tile"], 2, cells) is None
     monkeypatch.setitem(bench.NCU_CAPTURE, "sha256", None)
     assert bench.ncu_counters(bench.NCU_CAPTURE["tile"], 2, cells) is None
+
+
+def test_issue_ceiling_from_the_captured_instructions(monkeypatch):
+    # 152 SMs x 4 schedulers x 32 lanes x clock over the thread instructions
+    # of the three stages; withheld when the kernel changed since the capture
+    monkeypatch.setitem(bench.NCU_CAPTURE, "sha256", bench.kernel_sources_sha256())
+    monkeypatch.setitem(bench.NCU_CAPTURE, "thread_inst_per_cell", {1: 500.0, 2: 600.0, 3: 700.0})
+    got = bench.issue_ceiling(1.0e10, {"sm_mhz": 2000.0})
+    assert got["thread_inst_per_cell_update"] == 1800.0
+    assert abs(got["value"] - 152 * 4 * 32 * 2.0e9 / 1800.0) <= 1e-6 * got["value"]
+    assert abs(got["frac"] - 1.0e10 / got["value"]) <= 1e-12
+    monkeypatch.setitem(bench.NCU_CAPTURE, "sha256", "0" * 64)
+    assert bench.issue_ceiling(1.0e10, {"sm_mhz": 2000.0}) is None
