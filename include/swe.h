@@ -88,7 +88,8 @@ typedef struct {
                            hydrostatic-reconstruction faces (Audusse et al. 2004) wherever a WENO
                            stencil meets a dry cell, so that lakes at rest at or below z_ref stay at
                            rest beside dry land (tile 0 or its one compiled shape: 96x32 in FP32,
-                           64x32 in FP64; also an FP32 batch option; not a strip or fused_step option) */
+                           64x32 in FP64; also a batch option, on 96x32 in FP32 and 32x32 in FP64; not
+                           a strip or fused_step option) */
   void *stream;         /* cudaStream_t to run on (e.g. torch.cuda.Stream().cuda_stream); NULL = legacy default */
 } swe_params;
 
@@ -298,8 +299,9 @@ size_t swe_batch_slot_bytes(const swe_grid *grid);
  * edge, periodic pairs) and the physical parameters are those of every slot,
  * under the rules of swe_create; precision SWE_F32 (tile 0 picks the default
  * shape) or SWE_F64 (the parity mode: its one compiled shape, 32x32, taken
- * for tile 0); shore 1 (FP32 only) runs the shoreline variant on its one
- * compiled shape, 96x32; stream as for swe_create.  SWE_EINVAL otherwise. */
+ * for tile 0); shore 1 runs the shoreline variant on the precision's one
+ * compiled shape for it (96x32 in FP32, 32x32 in FP64); stream as for
+ * swe_create.  SWE_EINVAL otherwise. */
 int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *params, swe_batch **out);
 
 /* Admit a scenario: host FP64 bathymetry and state [ny][nx] (copied), run until

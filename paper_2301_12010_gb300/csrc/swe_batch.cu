@@ -255,8 +255,8 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
   if (!valid_params(params)) return SWE_EINVAL;          // sides and physics as for one scenario
   const bool f64 = params->precision == SWE_F64;         // FP64: one compiled tile shape
   if (f64 && params->tile != 0 && params->tile != batch64_shape()) return SWE_EINVAL;
-  const bool shore = params->shore != 0;                 // the shoreline variant: FP32, one compiled shape
-  if (shore && (f64 || (params->tile != 0 && params->tile != batch_shore_shape()))) return SWE_EINVAL;
+  const bool shore = params->shore != 0;                 // the shoreline variant: one compiled shape per precision
+  if (shore && !f64 && params->tile != 0 && params->tile != batch_shore_shape()) return SWE_EINVAL;
   swe_batch *b = new (std::nothrow) swe_batch();
   if (!b) return SWE_ENOMEM;
   b->nslots = nslots;
@@ -281,7 +281,7 @@ int swe_batch_create(int32_t nslots, size_t hbm_budget_bytes, const swe_params *
   if (e == cudaSuccess) e = dev_malloc((void **)&b->d_part, sizeof(double) * (kMassBlocks + 1));
   int per_sm = 0, dev = 0, sms = 0;
   if (e == cudaSuccess)
-    e = f64 ? batch64_resident(&per_sm) : (shore ? batch_shore_resident(&per_sm) : batch_resident(b->tile, &per_sm));
+    e = f64 ? batch64_resident(shore, &per_sm) : (shore ? batch_shore_resident(&per_sm) : batch_resident(b->tile, &per_sm));
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess && (per_sm < 1 || per_sm * sms > kPartSlots)) e = cudaErrorInvalidConfiguration;
@@ -367,7 +367,8 @@ int swe_batch_run(swe_batch *b, int32_t k_steps, double cfl) {
       cudaError_t le = cudaMemsetAsync(&b->d_ctl->bar_count, 0, sizeof(unsigned), b->cap);
       if (le == cudaSuccess) {
         if (b->prec == SWE_F64)
-          le = batch64_launch((const BatchSlot<double> *)b->d_table, b->d_ctl, k_steps, b->grid, b->strided, b->cap);
+          le = batch64_launch((const BatchSlot<double> *)b->d_table, b->d_ctl, k_steps, b->grid, b->strided,
+                              b->prm.shore != 0, b->cap);
         else if (b->prm.shore)
           le = batch_shore_launch((const BatchSlot<float> *)b->d_table, b->d_ctl, k_steps, b->grid, b->strided, b->cap);
         else

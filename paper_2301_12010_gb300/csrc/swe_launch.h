@@ -131,10 +131,11 @@ int batch_shore_shape();
 cudaError_t batch_shore_resident(int *per_sm);
 cudaError_t batch_shore_launch(const BatchSlot<float> *slots, BatchCtl *ctl, int k, int grid, bool strided,
                                cudaStream_t st);
-// The FP64 batch kernel (swe_batch64_kernels.cu): one compiled tile shape.
+// The FP64 batch kernel (swe_batch64_kernels.cu): one compiled tile shape,
+// with the paper's faces or (shore) the shoreline variant's.
 int batch64_shape();
-cudaError_t batch64_resident(int *per_sm);
-cudaError_t batch64_launch(const BatchSlot<double> *slots, BatchCtl *ctl, int k, int grid, bool strided,
+cudaError_t batch64_resident(bool shore, int *per_sm);
+cudaError_t batch64_launch(const BatchSlot<double> *slots, BatchCtl *ctl, int k, int grid, bool strided, bool shore,
                            cudaStream_t st);
 // CTAs per SM of the batch kernel for a shape, and one cooperative launch
 // (small: the form with one run-time-stage copy of the stage code, for

@@ -110,7 +110,7 @@ def test_batch_arguments_rejected_without_gpu(swe):
     q = swe.Params.from_buffer_copy(p)
     q.bc[2] = swe.PERIODIC  # periodic sides come in pairs
     assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
-    for prec, tile in ((swe.F64, 0), (swe.F32, 1)):  # the shoreline batch: FP32 on its one shape
+    for prec, tile in ((swe.F64, 7), (swe.F32, 1)):  # the shoreline batch: its one shape per precision
         q = swe.Params.from_buffer_copy(p)
         q.shore, q.precision, q.tile = 1, prec, tile
         assert swe.lib.swe_batch_create(4, 1 << 30, ctypes.byref(q), ctypes.byref(b)) == swe.EINVAL
