@@ -333,6 +333,24 @@ def shore_bench(swe, W, torch, sc, steps: int = 20, warmup: int = 4, per_stage_m
     return out
 
 
+def profile_fp64_case(n: int = 2048, tile: int = 2) -> int:
+    """A few FP64 steps on the n x n coastal DEM with the FP64 path's tile
+    shape (64 x 32), for ncu; no timing."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2301_12010_gb300 as swe
+    import workloads as W
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream().cuda_stream
+    with swe.Solver(W.coastal_dem(n=n), precision=swe.F64, stream=st, tile=tile) as s:
+        s.step(3)
+        s.sync()
+    print("profile-fp64: ok")
+    return 0
+
+
 def profile_shore_case(n: int = 2048) -> int:
     """A few steps of the shoreline variant on the n x n coastal DEM, for ncu; no timing."""
     import torch
@@ -582,6 +600,8 @@ def main():
                          "single-scenario kernels: a short case for a profiler")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused-step variant's measurement")
     ap.add_argument("--no-shore", action="store_true", help="skip the shoreline variant's measurement")
+    ap.add_argument("--profile-fp64", action="store_true",
+                    help="only three FP64 steps on the --n coastal DEM (64x32 tiles): a short case for a profiler")
     ap.add_argument("--profile-shore", action="store_true",
                     help="only three steps of the shoreline variant on the --n coastal DEM: a short case for a profiler")
     ap.add_argument("--profile-fused", action="store_true",
@@ -598,6 +618,8 @@ def main():
         return profile_fused_case(args.n)
     if args.profile_shore:
         return profile_shore_case(args.n)
+    if args.profile_fp64:
+        return profile_fp64_case(args.n)
     if args.config_table:
         return config_table()
     if args.serving_sweep:
