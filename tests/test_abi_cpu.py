@@ -81,6 +81,7 @@ def test_invalid_arguments_rejected_without_gpu(swe):
     assert swe.lib.swe_create(ctypes.byref(swe.Grid(65536, 32769)), 1.0, 1.0, dp, ctypes.byref(p), ctypes.byref(h)) == swe.EINVAL
     assert not h.value
     assert swe.lib.swe_step(None, 1, 0.4) == swe.EINVAL
+    assert swe.lib.swe_set_horizon(None, 1.0) == swe.EINVAL
 
 
 def test_tile_shapes(swe):
